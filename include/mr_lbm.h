@@ -1,0 +1,185 @@
+/*
+ * mr_lbm.h -- C-ABI of the GB300 implementation of the fully adaptive
+ * multiresolution lattice-Boltzmann time step of Bellotti, Gouarin, Graille
+ * and Massot, "Multidimensional fully adaptive lattice Boltzmann methods with
+ * error control based on multiresolution analysis" (arXiv 2103.02903).
+ *
+ * One call of mr_lbm_step() runs, entirely on the GPU, the loop body of
+ * Algorithm 1 (Sec. 6.2): the multiresolution encode of the stored
+ * post-collision field (projection, Def. Projection; prediction with s = 1,
+ * Sec. 4.1; details, Def. Details; group norm, Sec. 4.4), the mesh adaptation
+ * Lambda(t+dt) = G o H_eps o T_eps (Lambda(t)) (Eq. Thresholding,
+ * Eq. AdditionNeigh, the refinement rule of Sec. 5.1, Def. Grading), the
+ * data transfer to the new leaves (Sec. 5.1), the leaf-reconstruction
+ * transport (Eq. AdaptiveAdvectionPhase evaluated with the flattened weights
+ * of Eq. PredictionWithMatrixNew plus the finer-neighbour correction of
+ * Sec. 6.1, boundaries by Eq. AdvectionOnBoundary) and the collision on the
+ * leaves (Eq. AdaptiveCollision).
+ *
+ * Conventions shared by every entry point:
+ *  - every function returns an mr_status and never aborts or throws;
+ *  - errors are sticky per handle: once a call fails, later calls on the
+ *    handle return the same status until mr_lbm_destroy();
+ *  - work is ordered on the CUDA stream given at creation; calls that move
+ *    data to host memory (on_device = 0) synchronise that stream, the others
+ *    return as soon as the work is queued; device-side failures (capacity
+ *    overflow, an inconsistent mesh, a non-finite value) are reported by the
+ *    next call that synchronises (mr_lbm_synchronize, mr_lbm_stats, any
+ *    copy to host);
+ *  - the caller owns every pointer it passes; the handle owns all device
+ *    memory it allocates (mr_lbm_create allocates, mr_lbm_destroy frees);
+ *  - on_device = 1 means the pointer is device memory of the current device,
+ *    on_device = 0 means host memory (pinned or pageable);
+ *  - cells are indexed per level by integer coordinates k with
+ *    0 <= k_a < roots[a] * 2^level (Sec. 2.1).  A key is the cell's Morton
+ *    code at its own level prefixed by its root: key = root << (d*level) |
+ *    interleave(k mod 2^level), interleave placing bit i of k_x at bit d*i,
+ *    of k_y at bit d*i+1, root = (k_x >> level) + roots[0] * (k_y >> level).
+ *    Leaves are returned sorted by (level, key).
+ *  - dense arrays of one level are row-major with x fastest.
+ */
+#ifndef MR_LBM_H
+#define MR_LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MR_OK = 0,
+  MR_EINVAL = 1,      /* invalid argument or configuration */
+  MR_ENOMEM = 2,      /* device or host allocation failed */
+  MR_ECUDA = 3,       /* a CUDA runtime call failed */
+  MR_ECAPACITY = 4,   /* more cells than the preallocated capacity */
+  MR_ENOCONV = 5,     /* reserved: a bounded iteration did not converge */
+  MR_ENONFINITE = 6,  /* a non-finite population appeared */
+  MR_ESTATE = 7,      /* call not allowed in the current state (e.g. not initialised) */
+  MR_EINTERNAL = 8    /* the mesh violated an invariant (a bug) */
+} mr_status;
+
+typedef enum {
+  MR_D1Q2_ADVECTION = 0,     /* m^eq = (u, V u), V = phys[0] */
+  MR_D1Q2_BURGERS = 1,       /* m^eq = (u, u^2/2) */
+  MR_D1Q3_SHALLOW_WATER = 2, /* m^eq = (h, q, q^2/h + g h^2/2), g = phys[0] */
+  MR_D2Q4x4_EULER = 3,       /* vectorial D2Q4^4 of Sec. 7.1.2, gamma = phys[0] */
+  MR_D2Q9_NS = 4             /* Sec. 7.2.2; accepted by the oracle only, MR_EINVAL here */
+} mr_scheme;
+
+typedef enum {
+  MR_BC_PERIODIC = 0,        /* both faces of an axis must be periodic */
+  MR_BC_COPY = 1,            /* Eq. refBoundaryConditions, copy */
+  MR_BC_BOUNCE_BACK = 2,     /* Eq. refBoundaryConditions, bounce back */
+  MR_BC_ANTI_BOUNCE_BACK = 3 /* Eq. refBoundaryConditions, anti bounce back */
+} mr_bc;
+
+typedef enum { MR_FP64 = 0 } mr_precision;
+
+typedef struct {
+  int scheme;            /* mr_scheme */
+  double lambda;         /* lattice velocity lambda = dx/dt, Eq. acousticscaling; > 0 */
+  double s[16];          /* relaxation rates in [0, 2] of the non-conserved moments:
+                            D1Q2: s[0]; D1Q3: s[0] (third moment);
+                            D2Q4^4: s[i] = s_i^q, s[4+i] = s_i^xy, i = 0..3 */
+  double phys[8];        /* scheme constants (see mr_scheme) */
+  double xmin[3], xmax[3]; /* physical domain, informational */
+  int roots[3];          /* cells per axis at level 0 (1 for the unit square) */
+  int min_level, max_level; /* J_min and J; 2 <= J_min <= J <= 15 */
+  double eps;            /* threshold epsilon >= 0, eps_j = 2^{d(j-J)} eps (Sec. 4.4) */
+  int mu_bar;            /* regularity guess of the refinement rule, >= 0 */
+  int pred_s;            /* prediction stencil half-width; only 1 is supported */
+  int bc[6];             /* mr_bc per face: -x, +x, -y, +y, -z, +z */
+  int cross_sign;        /* +1: tensor-product prediction (default, also when 0);
+                            -1: diagonal term with the sign printed in Sec. 4.1 */
+  int precision;         /* mr_precision; only MR_FP64 */
+  long long leaf_capacity; /* maximum number of leaves; 0 = all finest cells */
+} mr_lbm_config;
+
+typedef struct mr_lbm* mr_lbm_t;
+
+/* Create a solver for `cfg` on the current CUDA device.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream) on which all work is queued.
+ * Allocates every device buffer up front (capacities from cfg); *out is NULL
+ * on failure.  Does not initialise the field: call mr_lbm_init or
+ * mr_lbm_set_leaves next. */
+mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* out);
+
+/* Release all memory of the handle.  Accepts NULL. */
+mr_status mr_lbm_destroy(mr_lbm_t h);
+
+/* Algorithm 1 initialisation: the full finest mesh Lambda(0) with
+ * f = M^{-1} m^eq of the given conserved moments.  `conserved` is SoA
+ * [ncons][N_J] of doubles, N_J = prod_a roots[a] 2^J cells of level J,
+ * row-major (x fastest); ncons = 1 (D1Q2), 2 (D1Q3), 4 (D2Q4^4:
+ * rho, rho u, rho v, E). */
+mr_status mr_lbm_init(mr_lbm_t h, const double* conserved, int on_device);
+
+/* `nsteps` iterations of the loop of Algorithm 1: adapt the mesh from the
+ * details of the stored post-collision field, move the data to the new
+ * leaves, stream every leaf (Eq. AdaptiveAdvectionPhase) and collide it
+ * (Eq. AdaptiveCollision).  Asynchronous. */
+mr_status mr_lbm_step(mr_lbm_t h, int nsteps);
+
+/* Mesh adaptation and data transfer only (first two lines of the loop of
+ * Algorithm 1), without transport and collision.  Asynchronous. */
+mr_status mr_lbm_adapt(mr_lbm_t h);
+
+/* Conserved moments of the reconstructed field on the uniform level `level`
+ * (J_min <= level <= J): the average of the leaves for cells covered by finer
+ * leaves, the recursive prediction (reconstruction operator, Sec. 4.4) for
+ * cells inside coarser leaves.  `out` is SoA [ncons][N_level], row-major. */
+mr_status mr_lbm_project(mr_lbm_t h, int level, double* out, int on_device);
+
+/* Copy the leaves out, sorted by (level, key).  Call with keys = levels =
+ * f = NULL to query the count in *n_inout; otherwise *n_inout is the capacity
+ * of the buffers on entry and the number written on return (MR_EINVAL if too
+ * small).  f is SoA [Q][n] of doubles, Q = populations per cell (2, 3, 16). */
+mr_status mr_lbm_get_leaves(mr_lbm_t h, long long* n_inout, unsigned long long* keys,
+                            signed char* levels, double* f, int on_device);
+
+/* Replace the state by the given leaves (any order), which must partition the
+ * domain and form a graded tree (every state produced by mr_lbm_step does).
+ * keys/levels as in mr_lbm_get_leaves, f SoA [Q][n].  Duplicate or
+ * overlapping leaves, or leaves that do not cover the domain, give
+ * MR_EINVAL at the next synchronising call. */
+mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* keys,
+                            const signed char* levels, const double* f, int on_device);
+
+/* Mesh statistics (synchronises): leaves per level (array of J+1 entries,
+ * may be NULL), MeshOR = #leaves / #finest cells and MemOR = #cells of the
+ * complete tree / #cells of all levels J_min..J (Sec. 7.1.3). */
+mr_status mr_lbm_stats(mr_lbm_t h, long long* leaves_per_level, double* mesh_or, double* mem_or);
+
+/* Sum over all steps since creation of the number of leaves updated (device
+ * counter, synchronises), and the number of steps. */
+mr_status mr_lbm_counters(mr_lbm_t h, long long* leaf_updates, long long* steps);
+
+/* Number of kernels the handle has launched since creation (host counter). */
+long long mr_lbm_launch_count(mr_lbm_t h);
+
+/* Time every launch of the transport-collision kernel with CUDA events on the
+ * handle's stream while enabled.  mr_lbm_profile_read synchronises and
+ * returns the total milliseconds and the number of timed launches since the
+ * last enable. */
+mr_status mr_lbm_profile_enable(mr_lbm_t h, int on);
+mr_status mr_lbm_profile_read(mr_lbm_t h, double* total_ms, long long* launches);
+
+/* Wait for the handle's stream and report any deferred device-side error. */
+mr_status mr_lbm_synchronize(mr_lbm_t h);
+
+/* Human-readable name of a status. */
+const char* mr_lbm_strerror(mr_status s);
+
+/* Host-only introspection (needs no GPU): the flattened weights of
+ * Eq. PredictionWithMatrixNew used by the transport for a leaf of level
+ * `level` at position k along an axis of n_level = roots << level cells
+ * (periodic or not) when the finest level is `max_level`.  out[0..4] are the
+ * weights of f_{level,k+delta}, delta = -2..2, in (incoming - outgoing) for
+ * the velocity +1 along the axis, out[5..9] for the velocity -1 (the part
+ * entering through a non-periodic boundary is left out). */
+mr_status mr_lbm_flattened_weights(int roots, int level, int max_level, int periodic, int k,
+                                   double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MR_LBM_H */

@@ -1,0 +1,302 @@
+"""Thin ctypes binding of the C-ABI in ``include/mr_lbm.h``.
+
+Argument marshalling only: every step of the time step runs in the CUDA
+kernels of ``libmrlbm.so``.  There is no CPU fallback: if the library is
+missing or cannot be loaded, every entry point raises.  Arrays may be numpy
+arrays (host memory) or CUDA tensors (device memory, passed by pointer on
+the handle's stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmrlbm.so")
+
+MR_STATUS = {0: "MR_OK", 1: "MR_EINVAL", 2: "MR_ENOMEM", 3: "MR_ECUDA", 4: "MR_ECAPACITY",
+             5: "MR_ENOCONV", 6: "MR_ENONFINITE", 7: "MR_ESTATE", 8: "MR_EINTERNAL"}
+SCHEMES = {"d1q2_advection": 0, "d1q2_burgers": 1, "d1q3_shallow_water": 2, "d2q4x4_euler": 3,
+           "d2q9_ns": 4}
+BCS = {"periodic": 0, "copy": 1, "bounce_back": 2, "anti_bounce_back": 3}
+NCONS = {0: 1, 1: 1, 2: 2, 3: 4}
+NPOP = {0: 2, 1: 2, 2: 3, 3: 16}
+DIM = {0: 1, 1: 1, 2: 1, 3: 2}
+
+
+class MrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s failed: %s" % (where, MR_STATUS.get(status, status)))
+
+
+class MrConfig(C.Structure):
+    _fields_ = [
+        ("scheme", C.c_int),
+        ("lambda_", C.c_double),
+        ("s", C.c_double * 16),
+        ("phys", C.c_double * 8),
+        ("xmin", C.c_double * 3),
+        ("xmax", C.c_double * 3),
+        ("roots", C.c_int * 3),
+        ("min_level", C.c_int),
+        ("max_level", C.c_int),
+        ("eps", C.c_double),
+        ("mu_bar", C.c_int),
+        ("pred_s", C.c_int),
+        ("bc", C.c_int * 6),
+        ("cross_sign", C.c_int),
+        ("precision", C.c_int),
+        ("leaf_capacity", C.c_longlong),
+    ]
+
+
+_lib = None
+
+
+def library():
+    """Load libmrlbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmrlbm.so is missing: run __graft_entry__.build() "
+                               "(or python -m paper_2103_02903_gb300.build) first")
+        L = C.CDLL(LIB_PATH)
+        vp, i, ll, d = C.c_void_p, C.c_int, C.c_longlong, C.c_double
+        L.mr_lbm_create.argtypes = [C.POINTER(MrConfig), vp, C.POINTER(vp)]
+        L.mr_lbm_destroy.argtypes = [vp]
+        L.mr_lbm_init.argtypes = [vp, vp, i]
+        L.mr_lbm_step.argtypes = [vp, i]
+        L.mr_lbm_adapt.argtypes = [vp]
+        L.mr_lbm_project.argtypes = [vp, i, vp, i]
+        L.mr_lbm_get_leaves.argtypes = [vp, C.POINTER(ll), vp, vp, vp, i]
+        L.mr_lbm_set_leaves.argtypes = [vp, ll, vp, vp, vp, i]
+        L.mr_lbm_stats.argtypes = [vp, vp, C.POINTER(d), C.POINTER(d)]
+        L.mr_lbm_counters.argtypes = [vp, C.POINTER(ll), C.POINTER(ll)]
+        L.mr_lbm_launch_count.argtypes = [vp]
+        L.mr_lbm_launch_count.restype = ll
+        L.mr_lbm_profile_enable.argtypes = [vp, i]
+        L.mr_lbm_profile_read.argtypes = [vp, C.POINTER(d), C.POINTER(ll)]
+        L.mr_lbm_synchronize.argtypes = [vp]
+        L.mr_lbm_strerror.argtypes = [i]
+        L.mr_lbm_strerror.restype = C.c_char_p
+        L.mr_lbm_flattened_weights.argtypes = [i, i, i, i, i, vp]
+        for name in ("mr_lbm_create", "mr_lbm_destroy", "mr_lbm_init", "mr_lbm_step", "mr_lbm_adapt",
+                     "mr_lbm_project", "mr_lbm_get_leaves", "mr_lbm_set_leaves", "mr_lbm_stats",
+                     "mr_lbm_counters", "mr_lbm_profile_enable", "mr_lbm_profile_read",
+                     "mr_lbm_synchronize", "mr_lbm_flattened_weights"):
+            getattr(L, name).restype = i
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise MrError(status, where)
+
+
+def make_config(cfg: Dict, leaf_capacity: int = 0) -> MrConfig:
+    c = MrConfig()
+    c.scheme = SCHEMES[cfg["scheme"]]
+    c.lambda_ = float(cfg["lambda_"])
+    for k, v in enumerate(cfg["s"]):
+        c.s[k] = float(v)
+    for k, v in enumerate(cfg["phys"]):
+        c.phys[k] = float(v)
+    for a in range(3):
+        c.xmin[a] = float(cfg["xmin"][a])
+        c.xmax[a] = float(cfg["xmax"][a])
+        c.roots[a] = int(cfg["roots"][a])
+    c.min_level = int(cfg["min_level"])
+    c.max_level = int(cfg["max_level"])
+    c.eps = float(cfg["eps"])
+    c.mu_bar = int(cfg["mu_bar"])
+    c.pred_s = 1
+    for f in range(6):
+        b = cfg["bc"][f]
+        c.bc[f] = BCS[b] if isinstance(b, str) else int(b)
+    c.cross_sign = int(cfg.get("cross_sign", 1))
+    c.precision = 0
+    c.leaf_capacity = int(cfg.get("leaf_capacity", leaf_capacity))
+    return c
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy array or a CUDA tensor."""
+    if x is None:
+        return None, 0
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+    if not (isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]):
+        raise ValueError("expected a C-contiguous numpy array or a tensor")
+    return C.c_void_p(x.ctypes.data), 0
+
+
+def flattened_weights(roots: int, level: int, max_level: int, periodic: bool, k: int) -> np.ndarray:
+    out = np.zeros(10, np.float64)
+    _check(library().mr_lbm_flattened_weights(roots, level, max_level, int(periodic), k,
+                                              out.ctypes.data), "mr_lbm_flattened_weights")
+    return out
+
+
+class Solver:
+    """One adaptive MR-LBM simulation on the current CUDA device."""
+
+    def __init__(self, cfg: Dict, stream: Optional[int] = None, leaf_capacity: int = 0):
+        self.cfg = dict(cfg)
+        self._c = make_config(cfg, leaf_capacity)
+        h = C.c_void_p()
+        _check(library().mr_lbm_create(C.byref(self._c), C.c_void_p(stream or 0), C.byref(h)),
+               "mr_lbm_create")
+        self.h = h
+        sid = self._c.scheme
+        self.d, self.Q, self.ncons = DIM[sid], NPOP[sid], NCONS[sid]
+        self.J, self.Jmin = self._c.max_level, self._c.min_level
+
+    def close(self):
+        if getattr(self, "h", None):
+            library().mr_lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_cells(self, level: int) -> int:
+        n = 1
+        for a in range(self.d):
+            n *= self.cfg["roots"][a] << level
+        return n
+
+    def init(self, conserved):
+        if isinstance(conserved, np.ndarray):
+            conserved = np.ascontiguousarray(conserved, np.float64)
+        p, dev = _ptr(conserved)
+        _check(library().mr_lbm_init(self.h, p, dev), "mr_lbm_init")
+
+    def step(self, n: int = 1):
+        _check(library().mr_lbm_step(self.h, int(n)), "mr_lbm_step")
+
+    def adapt(self):
+        _check(library().mr_lbm_adapt(self.h), "mr_lbm_adapt")
+
+    def project(self, level: int, out=None):
+        if out is None:
+            out = np.zeros((self.ncons, self.level_cells(level)), np.float64)
+        p, dev = _ptr(out)
+        _check(library().mr_lbm_project(self.h, int(level), p, dev), "mr_lbm_project")
+        return out
+
+    def num_leaves(self) -> int:
+        n = C.c_longlong(0)
+        _check(library().mr_lbm_get_leaves(self.h, C.byref(n), None, None, None, 0), "mr_lbm_get_leaves")
+        return n.value
+
+    def get_leaves(self):
+        """(keys uint64, levels int8, f float64 [Q, n]) sorted by (level, key)."""
+        n = self.num_leaves()
+        keys = np.zeros(n, np.uint64)
+        lev = np.zeros(n, np.int8)
+        f = np.zeros((self.Q, n), np.float64)
+        nn = C.c_longlong(n)
+        _check(library().mr_lbm_get_leaves(self.h, C.byref(nn), keys.ctypes.data, lev.ctypes.data,
+                                           f.ctypes.data, 0), "mr_lbm_get_leaves")
+        return keys, lev, f
+
+    def get_leaves_into(self, keys, levels, f):
+        nn = C.c_longlong(int(keys.shape[0]))
+        pk, dev = _ptr(keys)
+        pl, _ = _ptr(levels)
+        pf, _ = _ptr(f)
+        _check(library().mr_lbm_get_leaves(self.h, C.byref(nn), pk, pl, pf, dev), "mr_lbm_get_leaves")
+        return nn.value
+
+    def set_leaves(self, keys, levels, f):
+        n = int(keys.shape[0])
+        if isinstance(keys, np.ndarray):
+            keys = np.ascontiguousarray(keys, np.uint64)
+            levels = np.ascontiguousarray(levels, np.int8)
+            f = np.ascontiguousarray(f, np.float64)
+        pk, dev = _ptr(keys)
+        pl, _ = _ptr(levels)
+        pf, _ = _ptr(f)
+        _check(library().mr_lbm_set_leaves(self.h, n, pk, pl, pf, dev), "mr_lbm_set_leaves")
+
+    def stats(self):
+        per = np.zeros(self.J + 1, np.int64)
+        mesh_or, mem_or = C.c_double(), C.c_double()
+        _check(library().mr_lbm_stats(self.h, per.ctypes.data, C.byref(mesh_or), C.byref(mem_or)),
+               "mr_lbm_stats")
+        return per, mesh_or.value, mem_or.value
+
+    def counters(self):
+        a, b = C.c_longlong(), C.c_longlong()
+        _check(library().mr_lbm_counters(self.h, C.byref(a), C.byref(b)), "mr_lbm_counters")
+        return a.value, b.value
+
+    def launch_count(self) -> int:
+        return int(library().mr_lbm_launch_count(self.h))
+
+    def profile_enable(self, on: bool = True):
+        _check(library().mr_lbm_profile_enable(self.h, int(on)), "mr_lbm_profile_enable")
+
+    def profile_read(self):
+        ms, n = C.c_double(), C.c_longlong()
+        _check(library().mr_lbm_profile_read(self.h, C.byref(ms), C.byref(n)), "mr_lbm_profile_read")
+        return ms.value, n.value
+
+    def synchronize(self):
+        _check(library().mr_lbm_synchronize(self.h), "mr_lbm_synchronize")
+
+
+# ---------------------------------------------------------------- keys
+def _spread(v, d):
+    v = np.asarray(v, np.uint64)
+    out = np.zeros_like(v)
+    for b in range(32):
+        out |= ((v >> np.uint64(b)) & np.uint64(1)) << np.uint64(d * b)
+    return out
+
+
+def _compact(v, d):
+    v = np.asarray(v, np.uint64)
+    out = np.zeros_like(v)
+    for b in range(32):
+        out |= ((v >> np.uint64(d * b)) & np.uint64(1)) << np.uint64(b)
+    return out
+
+
+def encode_keys(cfg: Dict, level, ix, iy=None) -> np.ndarray:
+    """Keys of the C-ABI (Morton code at the cell's own level with a root prefix)."""
+    d = DIM[SCHEMES[cfg["scheme"]]]
+    level = np.asarray(level, np.uint64)
+    ix = np.asarray(ix, np.uint64)
+    if d == 1:
+        return ix.astype(np.uint64)
+    iy = np.asarray(iy, np.uint64)
+    mask = (np.uint64(1) << level) - np.uint64(1)
+    root = (ix >> level) + np.uint64(cfg["roots"][0]) * (iy >> level)
+    local = _spread(ix & mask, 2) | (_spread(iy & mask, 2) << np.uint64(1))
+    return (root << (np.uint64(2) * level)) | local
+
+
+def decode_keys(cfg: Dict, level, keys):
+    d = DIM[SCHEMES[cfg["scheme"]]]
+    keys = np.asarray(keys, np.uint64)
+    level = np.asarray(level, np.uint64)
+    if d == 1:
+        return keys.astype(np.int64), np.zeros(keys.shape, np.int64)
+    root = keys >> (np.uint64(2) * level)
+    local = keys & ((np.uint64(1) << (np.uint64(2) * level)) - np.uint64(1))
+    rx = root % np.uint64(cfg["roots"][0])
+    ry = root // np.uint64(cfg["roots"][0])
+    x = (rx << level) | _compact(local, 2)
+    y = (ry << level) | _compact(local >> np.uint64(1), 2)
+    return x.astype(np.int64), y.astype(np.int64)

@@ -1,0 +1,662 @@
+// C-ABI of the GB300 adaptive MR-LBM library (declared in include/mr_lbm.h):
+// handle life cycle, the host-side flattened-weight tables of
+// Eq. PredictionWithMatrixNew, and the orchestration of one time step of
+// Algorithm 1 as a fixed sequence of kernels on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mr_lbm.h"
+#include "mr_internal.cuh"
+
+struct mr_lbm {
+  Geo g;
+  cudaStream_t st = nullptr;
+  int nsm = 152;
+  MeshDev mesh[2];
+  MeshCounts* cntbuf = nullptr;  // two MeshCounts
+  int cur = 0;
+  double* fstate = nullptr;
+  double* fscratch = nullptr;
+  uint8_t* flags = nullptr;
+  uint8_t* cls = nullptr;
+  int* bcounts = nullptr;
+  int32_t* inidx = nullptr;
+  unsigned long long* vol = nullptr;
+  double* W = nullptr;
+  double* dense[2] = {nullptr, nullptr};
+  size_t dense_elems = 0;
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  bool initialized = false;
+  mr_status sticky = MR_OK;
+  long long launches = 0;
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+mr_status fail(mr_lbm* h, mr_status s) {
+  if (h && h->sticky == MR_OK) h->sticky = s;
+  return s;
+}
+
+bool cuda_ok(mr_lbm* h, cudaError_t e) {
+  if (e != cudaSuccess) {
+    fail(h, MR_ECUDA);
+    return false;
+  }
+  return true;
+}
+
+template <class T>
+bool dalloc(mr_lbm* h, T** p, size_t count) {
+  void* q = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    return false;
+  }
+  h->allocs.push_back(q);
+  *p = (T*)q;
+  return true;
+}
+
+// ----------------------------------------------------------------- geometry
+bool scheme_setup(Geo& g, const mr_lbm_config* c) {
+  memset(g.eta, 0, sizeof(g.eta));
+  memset(g.consw, 0, sizeof(g.consw));
+  const double L = c->lambda;
+  switch (c->scheme) {
+    case MR_D1Q2_ADVECTION:
+    case MR_D1Q2_BURGERS:
+      g.d = 1; g.q = 2; g.m = 1; g.ncons = 1;
+      g.eta[0][0] = 1; g.eta[1][0] = -1;
+      g.opp[0] = 1; g.opp[1] = 0;
+      g.consw[0][0] = 1; g.consw[0][1] = 1;
+      break;
+    case MR_D1Q3_SHALLOW_WATER:
+      g.d = 1; g.q = 3; g.m = 1; g.ncons = 2;
+      g.eta[1][0] = 1; g.eta[2][0] = -1;
+      g.opp[0] = 0; g.opp[1] = 2; g.opp[2] = 1;
+      g.consw[0][0] = g.consw[0][1] = g.consw[0][2] = 1;
+      g.consw[1][1] = L; g.consw[1][2] = -L;
+      break;
+    case MR_D2Q4x4_EULER:
+      g.d = 2; g.q = 4; g.m = 4; g.ncons = 4;
+      g.eta[0][0] = 1; g.eta[1][1] = 1; g.eta[2][0] = -1; g.eta[3][1] = -1;
+      g.opp[0] = 2; g.opp[1] = 3; g.opp[2] = 0; g.opp[3] = 1;
+      for (int i = 0; i < 4; ++i)
+        for (int h = 0; h < 4; ++h) g.consw[i][4 * i + h] = 1;
+      break;
+    default:
+      return false;
+  }
+  g.Q = g.q * g.m;
+  return true;
+}
+
+// One-dimensional reconstruction (prediction with s = 1 applied `gap`
+// times) of a level field of N cells, constant extension or wrap outside.
+void recon1d(std::vector<double>& cur, int N, int gap, bool periodic) {
+  for (int it = 0; it < gap; ++it) {
+    std::vector<double> nxt(2 * (size_t)N);
+    for (int k = 0; k < N; ++k) {
+      auto at = [&](int i) {
+        if (periodic) return cur[((i % N) + N) % N];
+        return cur[std::min(std::max(i, 0), N - 1)];
+      };
+      const double q = -0.125 * (at(k + 1) - at(k - 1));
+      nxt[2 * k] = cur[k] + q;
+      nxt[2 * k + 1] = cur[k] - q;
+    }
+    cur.swap(nxt);
+    N *= 2;
+  }
+}
+
+// Flattened weights (Eq. PredictionWithMatrixNew) of one axis: for a cell k
+// of a level with N cells and `gap` levels above the finest, the weights of
+// f_{k+delta}, delta = -2..2, in the finest edge values R_{k-1}, R_k, L_k,
+// L_{k+1}.  out[0..4] = R_{k-1} - R_k (incoming minus outgoing for the
+// velocity +1; R_{k-1} left out at a non-periodic left boundary),
+// out[5..9] = L_{k+1} - L_k (velocity -1), out[10..14] = R_k, out[15..19] = L_k.
+bool axis_weights(int N, int gap, bool periodic, int k, double* out) {
+  int Nsim = N, ks = k;
+  if (periodic) {  // interior weights, computed away from any boundary
+    Nsim = 9;
+    ks = 4;
+  }
+  const int n = 1 << gap;
+  for (int dl = -2; dl <= 2; ++dl) {
+    const int i = ks + dl;
+    double r0 = 0, r1 = 0, l0 = 0, l1 = 0;
+    if (i >= 0 && i < Nsim) {
+      std::vector<double> f(Nsim, 0.0);
+      f[i] = 1.0;
+      recon1d(f, Nsim, gap, false);
+      if (ks >= 1) r0 = f[(size_t)n * ks - 1];
+      r1 = f[(size_t)n * (ks + 1) - 1];
+      l0 = f[(size_t)n * ks];
+      if (ks + 1 < Nsim) l1 = f[(size_t)n * (ks + 1)];
+    } else if (!periodic) {
+      // outside the domain: the kernel never reads it, the weight must be 0
+    }
+    out[dl + 2] = r0 - r1;
+    out[5 + dl + 2] = l1 - l0;
+    out[10 + dl + 2] = r1;
+    out[15 + dl + 2] = l0;
+  }
+  return true;
+}
+
+void build_tables(const Geo& g, std::vector<double>& W) {
+  W.assign((size_t)(g.J + 1) * 3 * MR_NSLOT * MR_NTAB * 5, 0.0);
+  for (int l = g.Jmin; l <= g.J; ++l)
+    for (int a = 0; a < g.d; ++a) {
+      const int N = g.n[l][a];
+      const bool per = g.periodic[a] != 0;
+      for (int s = 0; s < MR_NSLOT; ++s) {
+        int k;
+        if (per) {
+          if (s != 2) continue;
+          k = 2;
+        } else {
+          k = s < 2 ? s : (s == 2 ? 2 : N - 2 + (s - 3));
+          if (k < 0 || k >= N || mr_slot(k, N, 0) != s) continue;
+        }
+        double w[20];
+        axis_weights(N, g.J - l, per, k, w);
+        for (int t = 0; t < MR_NTAB; ++t)
+          for (int e = 0; e < 5; ++e) W[MR_WIDX(l, a, s, t) + e] = w[t * 5 + e];
+      }
+    }
+}
+
+mr_status validate(const mr_lbm_config* c) {
+  if (!c) return MR_EINVAL;
+  if (c->scheme < 0 || c->scheme > MR_D2Q4x4_EULER) return MR_EINVAL;
+  if (!(c->lambda > 0) || !(c->eps >= 0) || c->mu_bar < 0) return MR_EINVAL;
+  if (c->pred_s != 0 && c->pred_s != 1) return MR_EINVAL;
+  if (c->precision != MR_FP64) return MR_EINVAL;
+  if (c->min_level < 2 || c->max_level < c->min_level || c->max_level > 15) return MR_EINVAL;
+  for (int i = 0; i < 16; ++i)
+    if (!(c->s[i] >= 0.0 && c->s[i] <= 2.0)) return MR_EINVAL;
+  for (int f = 0; f < 6; ++f)
+    if (c->bc[f] < MR_BC_PERIODIC || c->bc[f] > MR_BC_ANTI_BOUNCE_BACK) return MR_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if ((c->bc[2 * a] == MR_BC_PERIODIC) != (c->bc[2 * a + 1] == MR_BC_PERIODIC)) return MR_EINVAL;
+  if (c->cross_sign != 0 && c->cross_sign != 1 && c->cross_sign != -1) return MR_EINVAL;
+  return MR_OK;
+}
+
+int grid_for(const mr_lbm* h, int per_sm = 4) { return h->nsm * per_sm; }
+
+void count_launch(mr_lbm* h, int n = 1) { h->launches += n; }
+
+mr_status check_launch(mr_lbm* h) {
+  if (cudaGetLastError() != cudaSuccess) return fail(h, MR_ECUDA);
+  return MR_OK;
+}
+
+mr_status read_counts(mr_lbm* h, MeshCounts* out /*[2]*/) {
+  if (!cuda_ok(h, cudaMemcpyAsync(out, h->cntbuf, 2 * sizeof(MeshCounts), cudaMemcpyDeviceToHost, h->st)))
+    return MR_ECUDA;
+  if (!cuda_ok(h, cudaStreamSynchronize(h->st))) return MR_ECUDA;
+  const int err = out[0].err | out[1].err;
+  if (err & MR_DERR_CAPACITY) return fail(h, MR_ECAPACITY);
+  if (err & MR_DERR_INPUT) return fail(h, MR_EINVAL);
+  if (err & MR_DERR_INTERNAL) return fail(h, MR_EINTERNAL);
+  if (err & MR_DERR_NONFINITE) return fail(h, MR_ENONFINITE);
+  return MR_OK;
+}
+
+// Encode of the current state: internal values, bottom-up (Def. Projection).
+void run_projection(mr_lbm* h, const MeshDev& A) {
+  for (int L = h->g.J - 1; L >= h->g.Jmin; --L) {
+    mr_launch_project(h->g, A, h->fstate, L, h->st, grid_for(h));
+    count_launch(h);
+  }
+}
+
+// Build mesh `B` from the classification in h->cls (LEAF / INT bits).
+void run_build(mr_lbm* h, MeshDev& B) {
+  mr_launch_mark_ghosts(h->g, h->cls, h->st, grid_for(h));
+  mr_launch_compact(h->g, h->cls, h->flags, h->bcounts, B, h->st);
+  count_launch(h, 4);
+}
+
+// Adaptation and data transfer; on return the new mesh is mesh[1-cur] and
+// its (pre-transport) leaf values are in h->fscratch.
+void run_adapt(mr_lbm* h) {
+  const Geo& g = h->g;
+  MeshDev& A = h->mesh[h->cur];
+  MeshDev& B = h->mesh[1 - h->cur];
+  run_projection(h, A);
+  mr_launch_details(g, A, h->fstate, h->st, grid_for(h));
+  mr_launch_flags_T(g, A, h->flags, h->st, grid_for(h));
+  mr_launch_flags_H(g, A, h->flags, h->st, grid_for(h));
+  mr_launch_grade(g, h->flags, A.cnt, h->st, grid_for(h));
+  mr_launch_classify(g, h->flags, h->cls, h->st, grid_for(h));
+  count_launch(h, g.J > g.Jmin + 1 ? 5 : 4);
+  run_build(h, B);
+  mr_launch_remesh_copy(g, A, h->fstate, B, h->fscratch, h->st, grid_for(h));
+  count_launch(h);
+  for (int l = g.Jmin + 1; l <= g.J; ++l) {
+    mr_launch_predict_level(g, B, h->fscratch, l, h->st, grid_for(h));
+    count_launch(h);
+  }
+}
+
+cudaEvent_t next_event(mr_lbm* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+void run_stream(mr_lbm* h, const MeshDev& B, int do_stream, int do_collide) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->prof_on) {
+    e0 = next_event(h);
+    e1 = next_event(h);
+    cudaEventRecord(e0, h->st);
+  }
+  mr_launch_stream_collide(h->g, B, h->fscratch, h->fstate, h->W, do_stream, do_collide, h->st,
+                           grid_for(h, 8));
+  if (h->prof_on) cudaEventRecord(e1, h->st);
+  count_launch(h);
+}
+
+mr_status ensure_staging(mr_lbm* h, size_t bytes) {
+  if (h->staging_bytes >= bytes) return MR_OK;
+  if (h->staging) cudaFree(h->staging);
+  h->staging = nullptr;
+  h->staging_bytes = 0;
+  if (cudaMalloc(&h->staging, bytes) != cudaSuccess) return fail(h, MR_ENOMEM);
+  h->staging_bytes = bytes;
+  return MR_OK;
+}
+
+}  // namespace
+
+// =================================================================== C-ABI
+
+extern "C" {
+
+const char* mr_lbm_strerror(mr_status s) {
+  switch (s) {
+    case MR_OK: return "MR_OK";
+    case MR_EINVAL: return "MR_EINVAL: invalid argument or configuration";
+    case MR_ENOMEM: return "MR_ENOMEM: allocation failed";
+    case MR_ECUDA: return "MR_ECUDA: CUDA runtime error";
+    case MR_ECAPACITY: return "MR_ECAPACITY: capacity exceeded";
+    case MR_ENOCONV: return "MR_ENOCONV: no convergence";
+    case MR_ENONFINITE: return "MR_ENONFINITE: non-finite value";
+    case MR_ESTATE: return "MR_ESTATE: invalid state for this call";
+    case MR_EINTERNAL: return "MR_EINTERNAL: mesh invariant violated";
+  }
+  return "unknown status";
+}
+
+mr_status mr_lbm_flattened_weights(int roots, int level, int max_level, int periodic, int k, double* out) {
+  if (!out || roots < 1 || level < 0 || max_level < level || max_level > 20) return MR_EINVAL;
+  const int N = roots << level;
+  if (k < 0 || k >= N) return MR_EINVAL;
+  double w[20];
+  int kk = k;
+  if (!periodic) {
+    const int s = mr_slot(k, N, 0);
+    kk = s < 2 ? s : (s == 2 ? k : N - 2 + (s - 3));
+  }
+  axis_weights(N, max_level - level, periodic != 0, kk, w);
+  for (int i = 0; i < 10; ++i) out[i] = w[i];
+  return MR_OK;
+}
+
+mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* out) {
+  if (!out) return MR_EINVAL;
+  *out = nullptr;
+  mr_status v = validate(cfg);
+  if (v != MR_OK) return v;
+  mr_lbm* h = new (std::nothrow) mr_lbm();
+  if (!h) return MR_ENOMEM;
+  Geo& g = h->g;
+  memset(&g, 0, sizeof(g));
+  g.scheme = cfg->scheme;
+  if (!scheme_setup(g, cfg)) {
+    delete h;
+    return MR_EINVAL;
+  }
+  g.Jmin = cfg->min_level;
+  g.J = cfg->max_level;
+  for (int a = 0; a < 3; ++a) g.roots[a] = a < g.d ? std::max(1, cfg->roots[a]) : 1;
+  if (g.d == 2 && (g.roots[0] * g.roots[1] > 2)) {  // root prefix must fit the 32-bit key
+    delete h;
+    return MR_EINVAL;
+  }
+  uint64_t base = 0;
+  for (int l = 0; l < MR_MAXL; ++l) {
+    for (int a = 0; a < 3; ++a) g.n[l][a] = a < g.d ? (g.roots[a] << l) : 1;
+    g.ncode[l] = (uint32_t)((uint64_t)g.n[l][0] * g.n[l][1] * g.n[l][2]);
+  }
+  for (int l = 0; l <= MR_MAXL; ++l) {
+    g.base[l] = (uint32_t)base;
+    if (l >= g.Jmin && l <= g.J) base += (g.ncode[l] + MR_DENSE_ALIGN - 1) / MR_DENSE_ALIGN * MR_DENSE_ALIGN;
+  }
+  if (base >= (1ull << 30)) {
+    delete h;
+    return MR_EINVAL;
+  }
+  for (int a = 0; a < 3; ++a) g.periodic[a] = a < g.d && cfg->bc[2 * a] == MR_BC_PERIODIC;
+  for (int f = 0; f < 6; ++f) g.bc[f] = cfg->bc[f];
+  g.lambda = cfg->lambda;
+  for (int i = 0; i < 16; ++i) g.s[i] = cfg->s[i];
+  for (int i = 0; i < 8; ++i) g.phys[i] = cfg->phys[i];
+  g.eps = cfg->eps;
+  g.mu_bar = cfg->mu_bar;
+  g.cross_sign = cfg->cross_sign == -1 ? -1 : 1;
+  long long nJ = g.ncode[g.J], nint = 0, nall = 0;
+  for (int l = g.Jmin; l <= g.J; ++l) {
+    nall += g.ncode[l];
+    if (l < g.J) nint += g.ncode[l];
+  }
+  long long capL = cfg->leaf_capacity > 0 ? std::min<long long>(cfg->leaf_capacity, nJ) : nJ;
+  g.cap[0] = (int)capL;
+  g.cap[1] = (int)std::max<long long>(nint, 1);
+  g.cap[2] = (int)nall;
+  h->st = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (h->nsm <= 0) h->nsm = 152;
+
+  const size_t dense = g.base[g.J + 1];
+  bool ok = dalloc(h, &h->cntbuf, 2) && dalloc(h, &h->flags, dense) && dalloc(h, &h->cls, dense) &&
+            dalloc(h, &h->bcounts, 3 * (dense / MR_DENSE_ALIGN + 1)) && dalloc(h, &h->inidx, dense) &&
+            dalloc(h, &h->vol, 1) && dalloc(h, &h->fstate, (size_t)g.Q * g.cap[0]) &&
+            dalloc(h, &h->fscratch, (size_t)g.Q * g.cap[0]);
+  for (int mi = 0; mi < 2 && ok; ++mi) {
+    MeshDev& M = h->mesh[mi];
+    for (int c = 0; c < 3 && ok; ++c) ok = dalloc(h, &M.code[c], g.cap[c]) && dalloc(h, &M.lvl[c], g.cap[c]);
+    ok = ok && dalloc(h, &M.map, dense) && dalloc(h, &M.IF, (size_t)g.Q * g.cap[1]) &&
+         dalloc(h, &M.GF, (size_t)g.Q * g.cap[2]) && dalloc(h, &M.G, g.cap[1]) &&
+         dalloc(h, &M.src, g.cap[0]);
+    if (ok) M.cnt = h->cntbuf + mi;
+  }
+  std::vector<double> W;
+  build_tables(g, W);
+  ok = ok && dalloc(h, &h->W, W.size());
+  if (!ok) {
+    mr_lbm_destroy(h);
+    return MR_ENOMEM;
+  }
+  bool cok = cudaMemsetAsync(h->cntbuf, 0, 2 * sizeof(MeshCounts), h->st) == cudaSuccess &&
+             cudaMemsetAsync(h->flags, 0, dense, h->st) == cudaSuccess &&
+             cudaMemsetAsync(h->cls, 0, dense, h->st) == cudaSuccess &&
+             cudaMemsetAsync(h->inidx, 0xff, dense * sizeof(int32_t), h->st) == cudaSuccess &&
+             cudaMemsetAsync(h->mesh[0].map, 0xff, dense * sizeof(int32_t), h->st) == cudaSuccess &&
+             cudaMemsetAsync(h->mesh[1].map, 0xff, dense * sizeof(int32_t), h->st) == cudaSuccess &&
+             cudaMemcpyAsync(h->W, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, h->st) ==
+                 cudaSuccess &&
+             cudaStreamSynchronize(h->st) == cudaSuccess;
+  if (!cok) {
+    mr_lbm_destroy(h);
+    return MR_ECUDA;
+  }
+  *out = h;
+  return MR_OK;
+}
+
+mr_status mr_lbm_destroy(mr_lbm_t h) {
+  if (!h) return MR_OK;
+  if (h->st || true) cudaStreamSynchronize(h->st);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->staging) cudaFree(h->staging);
+  for (int i = 0; i < 2; ++i)
+    if (h->dense[i]) cudaFree(h->dense[i]);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+  return MR_OK;
+}
+
+mr_status mr_lbm_init(mr_lbm_t h, const double* conserved, int on_device) {
+  if (!h || !conserved) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  const Geo& g = h->g;
+  const size_t bytes = (size_t)g.ncons * g.ncode[g.J] * sizeof(double);
+  const double* src = conserved;
+  if (!on_device) {
+    if (ensure_staging(h, bytes) != MR_OK) return h->sticky;
+    if (!cuda_ok(h, cudaMemcpyAsync(h->staging, conserved, bytes, cudaMemcpyHostToDevice, h->st)))
+      return MR_ECUDA;
+    src = (const double*)h->staging;
+  }
+  MeshDev& B = h->mesh[h->cur];
+  mr_launch_full_mesh(g, h->cls, h->st, grid_for(h));
+  count_launch(h);
+  run_build(h, B);
+  mr_launch_init_eq(g, B, src, h->fstate, h->st, grid_for(h));
+  count_launch(h);
+  if (check_launch(h) != MR_OK) return h->sticky;
+  if (!on_device && !cuda_ok(h, cudaStreamSynchronize(h->st))) return MR_ECUDA;
+  h->initialized = true;
+  return MR_OK;
+}
+
+mr_status mr_lbm_step(mr_lbm_t h, int nsteps) {
+  if (!h || nsteps < 0) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  if (!h->initialized) return fail(h, MR_ESTATE);
+  for (int it = 0; it < nsteps; ++it) {
+    run_adapt(h);
+    MeshDev& B = h->mesh[1 - h->cur];
+    run_stream(h, B, 1, 1);
+    mr_launch_count_updates(B.cnt, h->st);
+    count_launch(h);
+    h->cur = 1 - h->cur;
+  }
+  return check_launch(h);
+}
+
+mr_status mr_lbm_adapt(mr_lbm_t h) {
+  if (!h) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  if (!h->initialized) return fail(h, MR_ESTATE);
+  run_adapt(h);
+  std::swap(h->fstate, h->fscratch);
+  h->cur = 1 - h->cur;
+  return check_launch(h);
+}
+
+mr_status mr_lbm_project(mr_lbm_t h, int level, double* out, int on_device) {
+  if (!h || !out) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  if (!h->initialized) return fail(h, MR_ESTATE);
+  const Geo& g = h->g;
+  if (level < g.Jmin || level > g.J) return MR_EINVAL;
+  const size_t need = (size_t)g.ncons * g.ncode[g.J];
+  if (h->dense_elems < need) {
+    for (int i = 0; i < 2; ++i) {
+      if (h->dense[i]) cudaFree(h->dense[i]);
+      h->dense[i] = nullptr;
+      if (cudaMalloc(&h->dense[i], need * sizeof(double)) != cudaSuccess) return fail(h, MR_ENOMEM);
+    }
+    h->dense_elems = need;
+  }
+  const MeshDev& A = h->mesh[h->cur];
+  run_projection(h, A);
+  int pb = 0;
+  for (int l = g.Jmin; l <= level; ++l) {
+    mr_launch_project_dense(g, A, h->fstate, l, h->dense[pb], h->dense[1 - pb], h->st, grid_for(h));
+    count_launch(h);
+    pb = 1 - pb;
+  }
+  const double* res = h->dense[pb];
+  const size_t bytes = (size_t)g.ncons * g.ncode[level] * sizeof(double);
+  if (!cuda_ok(h, cudaMemcpyAsync(out, res, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  h->st)))
+    return MR_ECUDA;
+  if (check_launch(h) != MR_OK) return h->sticky;
+  if (!on_device) {
+    MeshCounts hc[2];
+    return read_counts(h, hc);
+  }
+  return MR_OK;
+}
+
+mr_status mr_lbm_get_leaves(mr_lbm_t h, long long* n_inout, unsigned long long* keys, signed char* levels,
+                            double* f, int on_device) {
+  if (!h || !n_inout) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  if (!h->initialized) return fail(h, MR_ESTATE);
+  MeshCounts hc[2];
+  mr_status s = read_counts(h, hc);
+  if (s != MR_OK) return s;
+  const long long n = hc[h->cur].total[MR_CLS_LEAF];
+  if (!keys && !levels && !f) {
+    *n_inout = n;
+    return MR_OK;
+  }
+  if (*n_inout < n) return MR_EINVAL;
+  const Geo& g = h->g;
+  const MeshDev& A = h->mesh[h->cur];
+  if (on_device) {
+    mr_launch_leaves_out(g, A, h->fstate, n, keys, levels, f, h->st, grid_for(h));
+    count_launch(h);
+  } else {
+    const size_t bk = n * sizeof(unsigned long long), bl = (n * sizeof(signed char) + 255) / 256 * 256,
+                 bf = (size_t)g.Q * n * sizeof(double);
+    if (ensure_staging(h, bk + bl + bf) != MR_OK) return h->sticky;
+    char* sp = (char*)h->staging;
+    mr_launch_leaves_out(g, A, h->fstate, n, (unsigned long long*)sp, (signed char*)(sp + bk),
+                         (double*)(sp + bk + bl), h->st, grid_for(h));
+    count_launch(h);
+    if (keys && !cuda_ok(h, cudaMemcpyAsync(keys, sp, bk, cudaMemcpyDeviceToHost, h->st))) return MR_ECUDA;
+    if (levels && !cuda_ok(h, cudaMemcpyAsync(levels, sp + bk, n, cudaMemcpyDeviceToHost, h->st)))
+      return MR_ECUDA;
+    if (f && !cuda_ok(h, cudaMemcpyAsync(f, sp + bk + bl, bf, cudaMemcpyDeviceToHost, h->st))) return MR_ECUDA;
+    if (!cuda_ok(h, cudaStreamSynchronize(h->st))) return MR_ECUDA;
+  }
+  *n_inout = n;
+  return check_launch(h);
+}
+
+mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* keys, const signed char* levels,
+                            const double* f, int on_device) {
+  if (!h || n <= 0 || !keys || !levels || !f) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  const Geo& g = h->g;
+  if (n > g.cap[0]) return fail(h, MR_ECAPACITY);
+  const unsigned long long* dk = keys;
+  const signed char* dl = levels;
+  const double* df = f;
+  if (!on_device) {
+    const size_t bk = n * sizeof(unsigned long long), bl = (n + 255) / 256 * 256, bf = (size_t)g.Q * n * sizeof(double);
+    if (ensure_staging(h, bk + bl + bf) != MR_OK) return h->sticky;
+    char* sp = (char*)h->staging;
+    if (!cuda_ok(h, cudaMemcpyAsync(sp, keys, bk, cudaMemcpyHostToDevice, h->st)) ||
+        !cuda_ok(h, cudaMemcpyAsync(sp + bk, levels, n, cudaMemcpyHostToDevice, h->st)) ||
+        !cuda_ok(h, cudaMemcpyAsync(sp + bk + bl, f, bf, cudaMemcpyHostToDevice, h->st)))
+      return MR_ECUDA;
+    dk = (const unsigned long long*)sp;
+    dl = (const signed char*)(sp + bk);
+    df = (const double*)(sp + bk + bl);
+  }
+  MeshDev& B = h->mesh[h->cur];
+  if (!cuda_ok(h, cudaMemsetAsync(h->vol, 0, sizeof(unsigned long long), h->st))) return MR_ECUDA;
+  mr_launch_leaves_in(g, n, dk, dl, h->inidx, h->cls, B.cnt, h->vol, h->st, grid_for(h));
+  mr_launch_leaves_check(g, h->cls, B.cnt, h->st, grid_for(h));
+  count_launch(h, 2);
+  unsigned long long vol = 0;
+  if (!cuda_ok(h, cudaMemcpyAsync(&vol, h->vol, sizeof(vol), cudaMemcpyDeviceToHost, h->st))) return MR_ECUDA;
+  MeshCounts hc[2];
+  mr_status s = read_counts(h, hc);
+  if (s != MR_OK) return s;
+  unsigned long long full = g.ncode[g.J];
+  if (vol != full) return fail(h, MR_EINVAL);
+  run_build(h, B);
+  mr_launch_gather_input(g, B, h->inidx, n, df, h->fstate, h->st, grid_for(h));
+  count_launch(h);
+  // reset the input index map for the next call
+  if (!cuda_ok(h, cudaMemsetAsync(h->inidx, 0xff, (size_t)g.base[g.J + 1] * sizeof(int32_t), h->st)))
+    return MR_ECUDA;
+  if (check_launch(h) != MR_OK) return h->sticky;
+  s = read_counts(h, hc);
+  if (s != MR_OK) return s;
+  h->initialized = true;
+  return MR_OK;
+}
+
+mr_status mr_lbm_stats(mr_lbm_t h, long long* leaves_per_level, double* mesh_or, double* mem_or) {
+  if (!h) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  if (!h->initialized) return fail(h, MR_ESTATE);
+  MeshCounts hc[2];
+  mr_status s = read_counts(h, hc);
+  if (s != MR_OK) return s;
+  const MeshCounts& c = hc[h->cur];
+  const Geo& g = h->g;
+  if (leaves_per_level)
+    for (int l = 0; l <= g.J; ++l)
+      leaves_per_level[l] = l < g.Jmin ? 0 : c.off[MR_CLS_LEAF][l + 1] - c.off[MR_CLS_LEAF][l];
+  double all = 0;
+  for (int l = g.Jmin; l <= g.J; ++l) all += g.ncode[l];
+  if (mesh_or) *mesh_or = (double)c.total[MR_CLS_LEAF] / (double)g.ncode[g.J];
+  if (mem_or) *mem_or = (double)(c.total[MR_CLS_LEAF] + c.total[MR_CLS_INT]) / all;
+  return MR_OK;
+}
+
+mr_status mr_lbm_counters(mr_lbm_t h, long long* leaf_updates, long long* steps) {
+  if (!h) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  MeshCounts hc[2];
+  mr_status s = read_counts(h, hc);
+  if (s != MR_OK) return s;
+  if (leaf_updates) *leaf_updates = hc[0].leaf_updates + hc[1].leaf_updates;
+  if (steps) *steps = hc[0].steps + hc[1].steps;
+  return MR_OK;
+}
+
+long long mr_lbm_launch_count(mr_lbm_t h) { return h ? h->launches : 0; }
+
+mr_status mr_lbm_profile_enable(mr_lbm_t h, int on) {
+  if (!h) return MR_EINVAL;
+  if (!cuda_ok(h, cudaStreamSynchronize(h->st))) return MR_ECUDA;
+  h->prof_on = on != 0;
+  h->ev_used = 0;
+  return MR_OK;
+}
+
+mr_status mr_lbm_profile_read(mr_lbm_t h, double* total_ms, long long* launches) {
+  if (!h) return MR_EINVAL;
+  if (!cuda_ok(h, cudaStreamSynchronize(h->st))) return MR_ECUDA;
+  double tot = 0;
+  for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[i], h->ev_pool[i + 1]) != cudaSuccess) return fail(h, MR_ECUDA);
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = (long long)(h->ev_used / 2);
+  return MR_OK;
+}
+
+mr_status mr_lbm_synchronize(mr_lbm_t h) {
+  if (!h) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  MeshCounts hc[2];
+  return read_counts(h, hc);
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Device helpers shared by the kernels: value lookup through the dense index
+// map, byte atomics, grid-stride ranges and the canonical prediction
+// operator of Sec. 4.1 (s = 1).
+#pragma once
+
+#include "mr_internal.cuh"
+
+#define MR_C1 (-0.125)  // Table 1, s = 1
+
+struct ValPtr {
+  const double* p;
+  int stride;
+};
+
+__device__ __forceinline__ ValPtr mr_resolve(const Geo& g, const MeshDev& M, const double* LF, int32_t e) {
+  uint32_t cls = ((uint32_t)e) >> 30;
+  uint32_t idx = (uint32_t)e & 0x3FFFFFFFu;
+  ValPtr r;
+  if (cls == MR_CLS_LEAF) {
+    r.p = LF + idx;
+    r.stride = g.cap[0];
+  } else if (cls == MR_CLS_INT) {
+    r.p = M.IF + idx;
+    r.stride = g.cap[1];
+  } else {
+    r.p = M.GF + idx;
+    r.stride = g.cap[2];
+  }
+  return r;
+}
+
+__device__ __forceinline__ double mr_ld(const ValPtr& v, int p) { return __ldg(v.p + (size_t)p * v.stride); }
+
+__device__ __forceinline__ uint32_t mr_atomic_or_byte(uint8_t* base, uint32_t idx, uint32_t bits) {
+  uint32_t* w = (uint32_t*)(base + (idx & ~3u));
+  uint32_t sh = (idx & 3u) * 8u;
+  uint32_t old = atomicOr(w, bits << sh);
+  return (old >> sh) & 0xFFu;
+}
+
+__device__ __forceinline__ void mr_set_err(MeshCounts* c, int bits) { atomicOr(&c->err, bits); }
+
+// level of a dense index (levels J_min..J)
+__device__ __forceinline__ int mr_level_of(const Geo& g, uint32_t gi) {
+  int l = g.Jmin;
+  while (l < g.J && gi >= g.base[l + 1]) ++l;
+  return l;
+}
+
+// Canonical s = 1 prediction of child ci from a 3^D stencil (x fastest),
+// evaluated in the order written in Sec. 4.1 with no fused multiply-add:
+// the same bits as the CPU oracle on the same inputs.
+template <int D>
+__device__ __forceinline__ double mr_predict_canonical(const double* v, int ci, int cross_sign) {
+  const double sx = (ci & 1) ? -1.0 : 1.0;
+  if (D == 1) {
+    double qx = __dmul_rn(MR_C1, __dsub_rn(v[2], v[0]));
+    return __dadd_rn(v[1], __dmul_rn(sx, qx));
+  } else {
+    const double sy = (ci & 2) ? -1.0 : 1.0;
+    double qx = __dmul_rn(MR_C1, __dsub_rn(v[5], v[3]));
+    double qy = __dmul_rn(MR_C1, __dsub_rn(v[7], v[1]));
+    double q2 = __dmul_rn(MR_C1 * MR_C1, __dadd_rn(__dsub_rn(__dsub_rn(v[8], v[6]), v[2]), v[0]));
+    double t = v[4];
+    t = __dadd_rn(t, __dmul_rn(sx, qx));
+    t = __dadd_rn(t, __dmul_rn(sy, qy));
+    t = __dadd_rn(t, __dmul_rn((double)cross_sign * sx * sy, q2));
+    return t;
+  }
+}
+
+// Same operator with contraction allowed (used off the decision path).
+template <int D>
+__device__ __forceinline__ double mr_predict_fast(const double* v, int ci, double cross_sign) {
+  const double sx = (ci & 1) ? -1.0 : 1.0;
+  if (D == 1) {
+    return v[1] + sx * (MR_C1 * (v[2] - v[0]));
+  } else {
+    const double sy = (ci & 2) ? -1.0 : 1.0;
+    double qx = MR_C1 * (v[5] - v[3]);
+    double qy = MR_C1 * (v[7] - v[1]);
+    double q2 = (MR_C1 * MR_C1) * (((v[8] - v[6]) - v[2]) + v[0]);
+    return v[4] + sx * qx + sy * qy + (cross_sign * sx * sy) * q2;
+  }
+}
+
+// Gather the 3^D stencil entries around (x, y) at level l (constant
+// extension outside a non-periodic domain, wrap on periodic axes).
+template <int D>
+__device__ __forceinline__ bool mr_stencil_entries(const Geo& g, const MeshDev& M, int l, int x, int y,
+                                                   int32_t* ent) {
+  bool ok = true;
+  const int ny3 = D == 2 ? 3 : 1;
+  for (int b = 0; b < ny3; ++b)
+    for (int a = 0; a < 3; ++a) {
+      int sx = x + a - 1, sy = D == 2 ? y + b - 1 : 0;
+      mr_nbr_stencil(g, l, sx, sy);
+      int32_t e = M.map[g.base[l] + mr_encode(g, l, sx, sy)];
+      ent[b * 3 + a] = e;
+      ok = ok && (e != MR_MAP_NONE);
+    }
+  return ok;
+}

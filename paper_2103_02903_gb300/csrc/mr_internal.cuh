@@ -1,0 +1,194 @@
+// Internal definitions of the GB300 adaptive MR-LBM library: geometry and
+// scheme constants, Morton keys with a root prefix, the dense per-level
+// index space, the device mesh layout and the kernel entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MR_MAXL 16       // levels 0..15
+#define MR_MAXQ 16       // populations per cell
+#define MR_DENSE_ALIGN 1024u
+
+// cell classes stored in the two top bits of an index-map entry
+#define MR_CLS_LEAF 0u
+#define MR_CLS_INT 1u
+#define MR_CLS_GHOST 2u
+#define MR_MAP_NONE (-1)
+
+// adaptation flags (dense byte per cell of levels J_min..J-1)
+#define MR_F_T 1u   // children kept by T_eps (with closure)
+#define MR_F_H 2u   // refined after H_eps
+#define MR_F_G 4u   // refined by the grading
+// classification (dense byte per cell of levels J_min..J)
+#define MR_C_LEAF 1u
+#define MR_C_INT 2u
+#define MR_C_GHOST 4u
+#define MR_C_INPUT 8u
+
+// device error bits
+#define MR_DERR_CAPACITY 1
+#define MR_DERR_INTERNAL 2
+#define MR_DERR_NONFINITE 4
+#define MR_DERR_INPUT 8
+
+// weight tables: [level][axis][slot][table][5], table 0: (R_{k-1} - R_k),
+// 1: (L_{k+1} - L_k), 2: R_k, 3: L_k, delta = -2..2.
+#define MR_NSLOT 5
+#define MR_NTAB 4
+#define MR_WIDX(l, a, s, t) (((((l) * 3 + (a)) * MR_NSLOT + (s)) * MR_NTAB + (t)) * 5)
+
+struct Geo {
+  int scheme, d, q, m, Q, ncons;
+  int Jmin, J;
+  int roots[3];
+  int n[MR_MAXL][3];           // cells per axis at each level
+  uint32_t ncode[MR_MAXL];     // valid codes per level (= cells)
+  uint32_t base[MR_MAXL + 1];  // dense base index of each level, aligned; base[J+1] = dense size
+  int periodic[3];
+  int bc[6];
+  double lambda;
+  double s[16];
+  double phys[8];
+  double eps;
+  int mu_bar;
+  int cross_sign;
+  int eta[9][3];
+  int opp[9];
+  int cap[3];                  // capacities: leaf, internal, ghost
+  double consw[4][MR_MAXQ];    // conserved moments as linear forms of the populations
+};
+
+// counters of one mesh, in device memory
+struct MeshCounts {
+  int total[3];                 // leaves, internal, ghosts
+  int off[3][MR_MAXL + 1];      // offsets of each level in the class arrays
+  int err;                      // device error bits
+  int pad;
+  long long leaf_updates;       // sum of leaf counts over steps
+  long long steps;
+};
+
+struct MeshDev {
+  uint32_t* code[3];   // Morton code (with root prefix) at own level
+  uint8_t* lvl[3];
+  int32_t* map;        // dense index map: (cls << 30) | idx, or -1
+  double* IF;          // internal-cell values [Q][cap_int]
+  double* GF;          // ghost values [Q][cap_ghost]
+  double* G;           // group norm per internal cell
+  int32_t* src;        // per leaf: source entry in the previous mesh, -1 if predicted
+  MeshCounts* cnt;
+};
+
+// ------------------------------------------------------------------------
+// Morton keys with root prefix
+// ------------------------------------------------------------------------
+
+__host__ __device__ inline uint32_t mr_spread2(uint32_t x) {
+  x &= 0x0000FFFFu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+__host__ __device__ inline uint32_t mr_compact2(uint32_t x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+  x = (x | (x >> 4)) & 0x00FF00FFu;
+  x = (x | (x >> 8)) & 0x0000FFFFu;
+  return x;
+}
+
+__host__ __device__ inline uint32_t mr_encode(const Geo& g, int l, int x, int y) {
+  if (g.d == 1) return (uint32_t)x;
+  uint32_t mask = (1u << l) - 1u;
+  uint32_t root = (uint32_t)(x >> l) + (uint32_t)g.roots[0] * (uint32_t)(y >> l);
+  uint32_t local = mr_spread2((uint32_t)x & mask) | (mr_spread2((uint32_t)y & mask) << 1);
+  return (root << (2 * l)) | local;
+}
+
+__host__ __device__ inline void mr_decode(const Geo& g, int l, uint32_t code, int& x, int& y) {
+  if (g.d == 1) {
+    x = (int)code;
+    y = 0;
+    return;
+  }
+  uint32_t root = code >> (2 * l);
+  uint32_t local = code & ((l > 0) ? ((1u << (2 * l)) - 1u) : 0u);
+  int rx = (int)(root % (uint32_t)g.roots[0]), ry = (int)(root / (uint32_t)g.roots[0]);
+  x = (rx << l) | (int)mr_compact2(local);
+  y = (ry << l) | (int)mr_compact2(local >> 1);
+}
+
+// neighbour for the mesh rules: periodic wrap, false outside the domain
+__host__ __device__ inline bool mr_nbr_mesh(const Geo& g, int l, int& x, int& y) {
+  int nx = g.n[l][0], ny = g.n[l][1];
+  if (x < 0 || x >= nx) {
+    if (!g.periodic[0]) return false;
+    x = ((x % nx) + nx) % nx;
+  }
+  if (g.d >= 2 && (y < 0 || y >= ny)) {
+    if (!g.periodic[1]) return false;
+    y = ((y % ny) + ny) % ny;
+  }
+  if (g.d == 1) y = 0;
+  return true;
+}
+
+// stencil cell of the prediction operator: periodic wrap, otherwise the
+// nearest cell of the same level (constant extension)
+__host__ __device__ inline void mr_nbr_stencil(const Geo& g, int l, int& x, int& y) {
+  int nx = g.n[l][0], ny = g.n[l][1];
+  if (x < 0 || x >= nx) x = g.periodic[0] ? ((x % nx) + nx) % nx : (x < 0 ? 0 : nx - 1);
+  if (g.d >= 2) {
+    if (y < 0 || y >= ny) y = g.periodic[1] ? ((y % ny) + ny) % ny : (y < 0 ? 0 : ny - 1);
+  } else {
+    y = 0;
+  }
+}
+
+__host__ __device__ inline int mr_slot(int k, int N, int periodic) {
+  if (periodic) return 2;
+  if (k < 2) return k;
+  if (k >= N - 2) return 3 + (k - (N - 2));
+  return 2;
+}
+
+// ------------------------------------------------------------------------
+// kernels (defined in mr_encode.cu, mr_mesh.cu, mr_stream.cu)
+// ------------------------------------------------------------------------
+
+void mr_launch_project(const Geo& g, const MeshDev& A, const double* LF, int level, cudaStream_t st,
+                       int grid);
+void mr_launch_details(const Geo& g, const MeshDev& A, const double* LF, cudaStream_t st, int grid);
+void mr_launch_flags_T(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid);
+void mr_launch_flags_H(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid);
+void mr_launch_grade(const Geo& g, uint8_t* flags, MeshCounts* errc, cudaStream_t st, int grid);
+void mr_launch_classify(const Geo& g, const uint8_t* flags, uint8_t* cls, cudaStream_t st, int grid);
+void mr_launch_mark_ghosts(const Geo& g, uint8_t* cls, cudaStream_t st, int grid);
+void mr_launch_compact(const Geo& g, uint8_t* cls, uint8_t* flags, int* block_counts, MeshDev& B,
+                       cudaStream_t st);
+void mr_launch_remesh_copy(const Geo& g, const MeshDev& A, const double* LF_old, const MeshDev& B,
+                           double* LF_new, cudaStream_t st, int grid);
+void mr_launch_predict_level(const Geo& g, const MeshDev& B, double* LF, int level, cudaStream_t st,
+                             int grid);
+void mr_launch_stream_collide(const Geo& g, const MeshDev& B, const double* LF_in, double* LF_out,
+                              const double* W, int do_stream, int do_collide, cudaStream_t st,
+                              int grid);
+void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, double* LF,
+                       cudaStream_t st, int grid);
+void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int grid);
+void mr_launch_leaves_in(const Geo& g, long long n, const unsigned long long* keys,
+                         const signed char* levels, int32_t* inidx, uint8_t* cls, MeshCounts* cnt,
+                         unsigned long long* vol, cudaStream_t st, int grid);
+void mr_launch_leaves_check(const Geo& g, uint8_t* cls, MeshCounts* cnt, cudaStream_t st, int grid);
+void mr_launch_gather_input(const Geo& g, const MeshDev& B, const int32_t* inidx, long long n,
+                            const double* fin, double* LF, cudaStream_t st, int grid);
+void mr_launch_leaves_out(const Geo& g, const MeshDev& B, const double* LF, long long n,
+                          unsigned long long* keys, signed char* levels, double* f,
+                          cudaStream_t st, int grid);
+void mr_launch_project_dense(const Geo& g, const MeshDev& B, const double* LF, int level,
+                             const double* prev, double* cur, cudaStream_t st, int grid);
+void mr_launch_count_updates(MeshCounts* cnt, cudaStream_t st);

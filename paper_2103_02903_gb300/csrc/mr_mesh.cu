@@ -1,0 +1,394 @@
+// Mesh adaptation on the GPU (Sec. 4.3, 4.4, 5.1): the threshold operator
+// T_eps with its tree closure, the enlargement H_eps, the grading G, the
+// classification of every cell of the new tree, the marking of the ghost
+// cells whose reconstructed values the transport reads, and the compaction
+// of leaves / internal cells / ghosts into per-level sorted Morton-key
+// arrays with a dense per-level index map.
+//
+// The tree is held as one "refined" flag per cell of levels J_min..J-1: a
+// cell belongs to R(Lambda) iff it is on level J_min or its parent is
+// refined.  Every mark is an idempotent byte OR, so races between threads
+// are benign; the closure under ancestors and the grading cascade are
+// walked by the thread that first sets a flag, which makes each of them a
+// single kernel whatever the number of levels.
+#include "mr_common.cuh"
+
+namespace {
+
+__device__ __forceinline__ double level_eps(const Geo& g, int l) { return ldexp(g.eps, g.d * (l - g.J)); }
+
+// ---------------------------------------------------------------- T_eps
+template <int D>
+__global__ void __launch_bounds__(256) k_flags_T(Geo g, MeshDev A, uint8_t* flags) {
+  const int n = A.cnt->total[MR_CLS_INT];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int L = A.lvl[MR_CLS_INT][i];
+    if (!(A.G[i] >= level_eps(g, L + 1))) continue;
+    int l = L;
+    uint32_t c = A.code[MR_CLS_INT][i];
+    for (;;) {
+      uint32_t old = mr_atomic_or_byte(flags, g.base[l] + c, MR_F_T);
+      if ((old & MR_F_T) || l == g.Jmin) break;
+      --l;
+      c >>= D;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- H_eps
+template <int D>
+__global__ void __launch_bounds__(256) k_flags_H(Geo g, MeshDev A, uint8_t* flags) {
+  const int n = A.cnt->total[MR_CLS_INT];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int L = A.lvl[MR_CLS_INT][i];
+    const uint32_t code = A.code[MR_CLS_INT][i];
+    if (!(flags[g.base[L] + code] & MR_F_T)) continue;
+    mr_atomic_or_byte(flags, g.base[L] + code, MR_F_H);
+    int x, y;
+    mr_decode(g, L, code, x, y);
+    // neighbour rule (Eq. AdditionNeigh) on the children, which are the
+    // cells of R(T_eps(Lambda)) on level L+1
+    for (int ci = 0; ci < (1 << D); ++ci) {
+      const int cx = 2 * x + (ci & 1), cy = D == 2 ? 2 * y + ((ci >> 1) & 1) : 0;
+      for (int h = 0; h < g.q; ++h) {
+        int nx = cx - g.eta[h][0], ny = D == 2 ? cy - g.eta[h][1] : 0;
+        if (!mr_nbr_mesh(g, L + 1, nx, ny)) continue;
+        mr_atomic_or_byte(flags, g.base[L] + mr_encode(g, L, nx >> 1, ny >> 1), MR_F_H);
+      }
+    }
+    // refinement rule (Sec. 5.1): J_min < L+1 < J and group norm >= 2^{mu+d} eps_{L+1}
+    if (L + 1 > g.Jmin && L + 1 < g.J && A.G[i] >= ldexp(level_eps(g, L + 1), g.mu_bar + D)) {
+      for (int ci = 0; ci < (1 << D); ++ci)
+        mr_atomic_or_byte(flags, g.base[L + 1] + ((code << D) | (uint32_t)ci), MR_F_H);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- grading
+// Every refined cell p of level L >= J_min+1 needs the 3^d stencil of its
+// children (the cells around p on level L) in the tree, i.e. the parents of
+// those cells refined on level L-1.  The thread that newly refines a cell
+// continues the cascade from it, depth first, towards J_min.
+template <int D>
+__global__ void __launch_bounds__(256) k_grade(Geo g, uint8_t* flags) {
+  const uint32_t lo = g.base[g.Jmin + 1], hi = g.base[g.J];
+  const int noff = D == 2 ? 9 : 3;
+  for (uint32_t gi = lo + blockIdx.x * blockDim.x + threadIdx.x; gi < hi; gi += gridDim.x * blockDim.x) {
+    if (!(flags[gi] & MR_F_H)) continue;
+    const int l0 = mr_level_of(g, gi);
+    const uint32_t c0 = gi - g.base[l0];
+    if (c0 >= g.ncode[l0]) continue;
+    int sl[MR_MAXL], sx[MR_MAXL], sy[MR_MAXL], sk[MR_MAXL];
+    int sp = 1;
+    sl[0] = l0;
+    mr_decode(g, l0, c0, sx[0], sy[0]);
+    sk[0] = 0;
+    while (sp > 0) {
+      const int t = sp - 1;
+      const int k = sk[t];
+      if (k == noff) {
+        --sp;
+        continue;
+      }
+      sk[t] = k + 1;
+      const int L = sl[t];
+      int nx = sx[t] + (k % 3) - 1, ny = D == 2 ? sy[t] + (k / 3) - 1 : 0;
+      if (!mr_nbr_mesh(g, L, nx, ny)) continue;
+      const int tl = L - 1;
+      const int px = nx >> 1, py = ny >> 1;
+      const uint32_t old = mr_atomic_or_byte(flags, g.base[tl] + mr_encode(g, tl, px, py), MR_F_G);
+      if (!(old & (MR_F_H | MR_F_G)) && tl > g.Jmin && sp < MR_MAXL) {
+        sl[sp] = tl;
+        sx[sp] = px;
+        sy[sp] = py;
+        sk[sp] = 0;
+        ++sp;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- classify
+template <int D>
+__global__ void __launch_bounds__(256) k_classify(Geo g, const uint8_t* __restrict__ flags,
+                                                  uint8_t* cls) {
+  const uint32_t lo = g.base[g.Jmin], hi = g.base[g.J + 1];
+  for (uint32_t gi = lo + blockIdx.x * blockDim.x + threadIdx.x; gi < hi; gi += gridDim.x * blockDim.x) {
+    const int l = mr_level_of(g, gi);
+    const uint32_t c = gi - g.base[l];
+    if (c >= g.ncode[l]) continue;
+    const bool inR = (l == g.Jmin) || (flags[g.base[l - 1] + (c >> D)] & (MR_F_H | MR_F_G));
+    const bool ref = (l < g.J) && (flags[gi] & (MR_F_H | MR_F_G));
+    cls[gi] = inR ? (ref ? MR_C_INT : MR_C_LEAF) : 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_full_mesh(Geo g, uint8_t* cls) {
+  const uint32_t lo = g.base[g.Jmin], hi = g.base[g.J + 1];
+  for (uint32_t gi = lo + blockIdx.x * blockDim.x + threadIdx.x; gi < hi; gi += gridDim.x * blockDim.x) {
+    const int l = mr_level_of(g, gi);
+    if (gi - g.base[l] >= g.ncode[l]) continue;
+    cls[gi] = l == g.J ? MR_C_LEAF : MR_C_INT;
+  }
+}
+
+// ---------------------------------------------------------------- ghosts
+// The transport of a leaf on level l reads the reconstructed values of the
+// cells at distance 1 and 2 along each axis on level l (the flattened
+// window).  Those outside R(Lambda) are ghosts: predicted from level l-1,
+// whose stencil cells outside R(Lambda) are ghosts in turn.
+template <int D>
+__global__ void __launch_bounds__(256) k_mark_ghosts(Geo g, uint8_t* cls) {
+  const uint32_t lo = g.base[g.Jmin], hi = g.base[g.J + 1];
+  const int nwin = 4 * D;
+  for (uint32_t gi = lo + blockIdx.x * blockDim.x + threadIdx.x; gi < hi; gi += gridDim.x * blockDim.x) {
+    if ((cls[gi] & 3u) != MR_C_LEAF) continue;
+    const int l = mr_level_of(g, gi);
+    const uint32_t c = gi - g.base[l];
+    if (c >= g.ncode[l]) continue;
+    int x, y;
+    mr_decode(g, l, c, x, y);
+    for (int w = 0; w < nwin; ++w) {
+      const int axis = w >> 2, k = w & 3;
+      const int off = k < 2 ? k - 2 : k - 1;  // -2, -1, +1, +2
+      int nx = x + (axis == 0 ? off : 0), ny = y + (axis == 1 ? off : 0);
+      if (!mr_nbr_mesh(g, l, nx, ny)) continue;
+      const uint32_t gw = g.base[l] + mr_encode(g, l, nx, ny);
+      if (cls[gw] & 3u) continue;
+      const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
+      if (old & MR_C_GHOST) continue;
+      // cascade: the stencil of the ghost's parent, towards coarser levels
+      int sl[MR_MAXL], sx[MR_MAXL], sy[MR_MAXL], sk[MR_MAXL];
+      int sp = 0;
+      if (l - 1 > g.Jmin - 1) {
+        sl[0] = l - 1;
+        sx[0] = nx >> 1;
+        sy[0] = ny >> 1;
+        sk[0] = 0;
+        sp = 1;
+      }
+      const int noff = D == 2 ? 9 : 3;
+      while (sp > 0) {
+        const int t = sp - 1;
+        const int kk = sk[t];
+        if (kk == noff) {
+          --sp;
+          continue;
+        }
+        sk[t] = kk + 1;
+        const int L = sl[t];
+        int ax = sx[t] + (kk % 3) - 1, ay = D == 2 ? sy[t] + (kk / 3) - 1 : 0;
+        if (!mr_nbr_mesh(g, L, ax, ay)) continue;
+        const uint32_t ga = g.base[L] + mr_encode(g, L, ax, ay);
+        if (cls[ga] & 3u) continue;
+        const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
+        if ((o2 & MR_C_GHOST) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
+        sl[sp] = L - 1;
+        sx[sp] = ax >> 1;
+        sy[sp] = ay >> 1;
+        sk[sp] = 0;
+        ++sp;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- compaction
+// Stream compaction of the dense classification, 1024 dense cells per block,
+// with ballot / popc prefixes inside each block and one scan over blocks.
+__device__ __forceinline__ int cls_of(uint8_t c) {
+  const uint32_t k = c & 3u;
+  if (k == MR_C_LEAF) return MR_CLS_LEAF;
+  if (k == MR_C_INT) return MR_CLS_INT;
+  if (c & MR_C_GHOST) return MR_CLS_GHOST;
+  return -1;
+}
+
+__global__ void __launch_bounds__(1024) k_count(const uint8_t* __restrict__ cls, int* bc) {
+  const uint32_t gi = blockIdx.x * 1024u + threadIdx.x;
+  const int k = cls_of(cls[gi]);
+  const int nl = __syncthreads_count(k == MR_CLS_LEAF);
+  const int ni = __syncthreads_count(k == MR_CLS_INT);
+  const int ng = __syncthreads_count(k == MR_CLS_GHOST);
+  if (threadIdx.x == 0) {
+    bc[blockIdx.x * 3 + 0] = nl;
+    bc[blockIdx.x * 3 + 1] = ni;
+    bc[blockIdx.x * 3 + 2] = ng;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(Geo g, int* bc, int nblocks, MeshCounts* cnt) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = 0; c < 3; ++c) {
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nblocks; b0 += 1024) {
+      const int b = b0 + threadIdx.x;
+      const int v = b < nblocks ? bc[b * 3 + c] : 0;
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) warp_sums[wid] = x;
+      __syncthreads();
+      if (wid == 0) {
+        int s = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          int y = __shfl_up_sync(0xffffffffu, s, o);
+          if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+      }
+      __syncthreads();
+      const int excl = carry + (wid > 0 ? warp_sums[wid - 1] : 0) + x - v;
+      if (b < nblocks) bc[b * 3 + c] = excl;
+      __syncthreads();
+      if (threadIdx.x == 1023) carry = excl + v;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      // counts are clamped to the capacity so that no later kernel can run
+      // past an array; the overflow itself is reported through err
+      cnt->total[c] = carry < g.cap[c] ? carry : g.cap[c];
+      if (carry > g.cap[c]) atomicOr(&cnt->err, MR_DERR_CAPACITY);
+    }
+    __syncthreads();
+  }
+  // per-level offsets: every level starts on a block boundary
+  if (threadIdx.x < 3) {
+    const int c = threadIdx.x;
+    for (int l = 0; l <= MR_MAXL; ++l) {
+      int v;
+      if (l < g.Jmin)
+        v = 0;
+      else if (l <= g.J)
+        v = bc[(g.base[l] / MR_DENSE_ALIGN) * 3 + c];
+      else
+        v = cnt->total[c];
+      cnt->off[c][l] = v < g.cap[c] ? v : g.cap[c];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scatter(Geo g, uint8_t* cls, uint8_t* flags,
+                                                  const int* __restrict__ bc, MeshDev B) {
+  __shared__ int wcount[32][3];
+  __shared__ int woff[32][3];
+  const uint32_t gi = blockIdx.x * 1024u + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int k = cls_of(cls[gi]);
+  const uint32_t lt = (1u << lane) - 1u;
+  int pre = 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const uint32_t bal = __ballot_sync(0xffffffffu, k == c);
+    if (k == c) pre = __popc(bal & lt);
+    if (lane == 0) wcount[wid][c] = __popc(bal);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    int s = 0;
+    for (int w = 0; w < 32; ++w) {
+      woff[w][threadIdx.x] = s;
+      s += wcount[w][threadIdx.x];
+    }
+  }
+  __syncthreads();
+  int32_t entry = MR_MAP_NONE;
+  if (k >= 0) {
+    const int pos = bc[blockIdx.x * 3 + k] + woff[wid][k] + pre;
+    if (pos < g.cap[k]) {
+      const int l = mr_level_of(g, gi);
+      B.code[k][pos] = gi - g.base[l];
+      B.lvl[k][pos] = (uint8_t)l;
+      entry = (int32_t)(((uint32_t)k << 30) | (uint32_t)pos);
+    }
+  }
+  B.map[gi] = entry;
+  cls[gi] = 0;
+  flags[gi] = 0;
+}
+
+// ---------------------------------------------------------------- input leaves
+template <int D>
+__global__ void __launch_bounds__(256) k_leaves_in(Geo g, long long n, const unsigned long long* keys,
+                                                   const signed char* levels, int32_t* inidx,
+                                                   uint8_t* cls, MeshCounts* cnt,
+                                                   unsigned long long* vol) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int l = levels[i];
+    const unsigned long long key = keys[i];
+    if (l < g.Jmin || l > g.J || key >= g.ncode[l]) {
+      mr_set_err(cnt, MR_DERR_INPUT);
+      continue;
+    }
+    const uint32_t c = (uint32_t)key;
+    const uint32_t old = mr_atomic_or_byte(cls, g.base[l] + c, MR_C_LEAF);
+    if (old & MR_C_LEAF) mr_set_err(cnt, MR_DERR_INPUT);
+    inidx[g.base[l] + c] = (int32_t)i;
+    atomicAdd(vol, 1ull << (D * (g.J - l)));
+    uint32_t a = c;
+    for (int la = l - 1; la >= g.Jmin; --la) {
+      a >>= D;
+      const uint32_t o = mr_atomic_or_byte(cls, g.base[la] + a, MR_C_INT);
+      if (o & MR_C_INT) break;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_leaves_check(Geo g, const uint8_t* __restrict__ cls,
+                                                      MeshCounts* cnt) {
+  const uint32_t lo = g.base[g.Jmin], hi = g.base[g.J + 1];
+  for (uint32_t gi = lo + blockIdx.x * blockDim.x + threadIdx.x; gi < hi; gi += gridDim.x * blockDim.x)
+    if ((cls[gi] & 3u) == 3u) mr_set_err(cnt, MR_DERR_INPUT);
+}
+
+}  // namespace
+
+#define MR_DISPATCH_D(KER, GRID, BLOCK, ST, ...)                 \
+  do {                                                           \
+    if (g.d == 1)                                                \
+      KER<1><<<GRID, BLOCK, 0, ST>>>(__VA_ARGS__);               \
+    else                                                         \
+      KER<2><<<GRID, BLOCK, 0, ST>>>(__VA_ARGS__);               \
+  } while (0)
+
+void mr_launch_flags_T(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid) {
+  MR_DISPATCH_D(k_flags_T, grid, 256, st, g, A, flags);
+}
+void mr_launch_flags_H(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid) {
+  MR_DISPATCH_D(k_flags_H, grid, 256, st, g, A, flags);
+}
+void mr_launch_grade(const Geo& g, uint8_t* flags, MeshCounts*, cudaStream_t st, int grid) {
+  if (g.J > g.Jmin + 1) MR_DISPATCH_D(k_grade, grid, 256, st, g, flags);
+}
+void mr_launch_classify(const Geo& g, const uint8_t* flags, uint8_t* cls, cudaStream_t st, int grid) {
+  MR_DISPATCH_D(k_classify, grid, 256, st, g, flags, cls);
+}
+void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int grid) {
+  k_full_mesh<<<grid, 256, 0, st>>>(g, cls);
+}
+void mr_launch_mark_ghosts(const Geo& g, uint8_t* cls, cudaStream_t st, int grid) {
+  MR_DISPATCH_D(k_mark_ghosts, grid, 256, st, g, cls);
+}
+void mr_launch_compact(const Geo& g, uint8_t* cls, uint8_t* flags, int* block_counts, MeshDev& B,
+                       cudaStream_t st) {
+  const int nblocks = (int)(g.base[g.J + 1] / MR_DENSE_ALIGN);
+  k_count<<<nblocks, 1024, 0, st>>>(cls, block_counts);
+  k_scan_blocks<<<1, 1024, 0, st>>>(g, block_counts, nblocks, B.cnt);
+  k_scatter<<<nblocks, 1024, 0, st>>>(g, cls, flags, block_counts, B);
+}
+void mr_launch_leaves_in(const Geo& g, long long n, const unsigned long long* keys,
+                         const signed char* levels, int32_t* inidx, uint8_t* cls, MeshCounts* cnt,
+                         unsigned long long* vol, cudaStream_t st, int grid) {
+  MR_DISPATCH_D(k_leaves_in, grid, 256, st, g, n, keys, levels, inidx, cls, cnt, vol);
+}
+void mr_launch_leaves_check(const Geo& g, uint8_t* cls, MeshCounts* cnt, cudaStream_t st, int grid) {
+  k_leaves_check<<<grid, 256, 0, st>>>(g, cls, cnt);
+}

@@ -1,0 +1,114 @@
+"""CPU checks of the C-ABI library (no GPU needed): it builds for sm_103a,
+loads, exports every function that include/mr_lbm.h declares, and its
+host-side flattened weights (Eq. PredictionWithMatrixNew) agree with the
+matrix of Eq. PredictionWithMatrix and with the CPU oracle's reconstruction.
+"""
+import ctypes
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2103_02903_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(mr_lbm_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_strerror_names(lib):
+    lib.mr_lbm_strerror.restype = ctypes.c_char_p
+    assert lib.mr_lbm_strerror(0) == b"MR_OK"
+    assert b"capacity" in lib.mr_lbm_strerror(4)
+
+
+def test_create_rejects_bad_config(lib):
+    from paper_2103_02903_gb300 import binding, workloads
+    cfg, _ = workloads.advection_1d(max_level=6)
+    cfg["eps"] = -1.0
+    c = binding.make_config(cfg)
+    h = ctypes.c_void_p()
+    assert binding.library().mr_lbm_create(ctypes.byref(c), None, ctypes.byref(h)) == 1
+    cfg, _ = workloads.advection_1d(max_level=6)
+    cfg["bc"] = ["periodic", "copy", "periodic", "periodic", "periodic", "periodic"]
+    c = binding.make_config(cfg)
+    assert binding.library().mr_lbm_create(ctypes.byref(c), None, ctypes.byref(h)) == 1
+
+
+def _paper_matrix():
+    rows = []
+    with open(os.path.join(ROOT, "tests", "golden", "flattening_matrix_1d.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(Fraction(v)) for v in line.split()])
+    return np.array(rows)
+
+
+@pytest.mark.parametrize("gap", [1, 2, 3, 5])
+def test_flattened_weights_match_paper_matrix(lib, gap):
+    """Interior weights: R_{k-1} is row 2 (index 1) of M^gap applied to
+    f_{k-2..k+1}; R_k is the same row shifted by one cell."""
+    from paper_2103_02903_gb300.binding import flattened_weights
+    P = np.linalg.matrix_power(_paper_matrix(), gap)
+    w = flattened_weights(1, 6, 6 + gap, True, 10)
+    r_km1 = np.zeros(5)
+    r_km1[0:4] = P[1]            # fine cell 2^g k - 1 from f_{k-2..k+1}
+    r_k = np.zeros(5)
+    r_k[1:5] = P[1]              # fine cell 2^g (k+1) - 1 from f_{k-1..k+2}
+    np.testing.assert_allclose(w[0:5], r_km1 - r_k, rtol=0, atol=1e-15)
+    l_k = np.zeros(5)
+    l_k[0:4] = P[2]              # fine cell 2^g k from f_{k-2..k+1}
+    l_kp1 = np.zeros(5)
+    l_kp1[1:5] = P[2]
+    np.testing.assert_allclose(w[5:10], l_kp1 - l_k, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 13, 14, 15])
+@pytest.mark.parametrize("gap", [1, 3])
+def test_flattened_weights_match_oracle_near_boundaries(lib, k, gap):
+    """With constant extension outside the domain, the weights at the
+    boundary slots reproduce the oracle's reconstruction of a uniform level."""
+    from oracle import Oracle
+    from paper_2103_02903_gb300 import workloads
+    from paper_2103_02903_gb300.binding import flattened_weights
+    cfg, _ = workloads.burgers_1d(max_level=4 + gap, min_level=2)
+    level = 4
+    n = 1 << level
+    rng = np.random.default_rng(k + 100 * gap)
+    f = rng.standard_normal(n)
+    o = Oracle(cfg)
+    z = np.zeros(n, np.int32)
+    o.set_leaves(np.full(n, level, np.int32), np.arange(n, dtype=np.int32), z, z, np.stack([f, f]))
+    fine = o.reconstruct(cfg["max_level"])[0]
+    w = flattened_weights(1, level, cfg["max_level"], False, k)
+    win = np.array([f[k + d] if 0 <= k + d < n else 0.0 for d in range(-2, 3)])
+    m = 1 << gap
+    r_km1 = fine[m * k - 1] if k > 0 else 0.0
+    r_k = fine[m * (k + 1) - 1]
+    l_k = fine[m * k]
+    l_kp1 = fine[m * (k + 1)] if k + 1 < n else 0.0
+    assert abs(w[0:5] @ win - (r_km1 - r_k)) < 1e-13
+    assert abs(w[5:10] @ win - (l_kp1 - l_k)) < 1e-13

@@ -1,0 +1,253 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Leaf sets must match exactly; populations within 1e-12 of the max norm of
+each population field (the FP64 tolerance of the spec: fields to 1e-12
+relative).  When the two runs evolve independently for several steps, a keep
+/ refine decision can only differ if a group norm lies within rounding of a
+threshold; the oracle logs the smallest relative decision margin, and such
+steps are reported instead of silently accepted.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2103_02903_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def _morton2(x, y, l, roots_x):
+    """Key of the C-ABI written out bit by bit (independent of the library)."""
+    x = int(x)
+    y = int(y)
+    root = (x >> l) + roots_x * (y >> l)
+    code = 0
+    for b in range(l):
+        code |= ((x >> b) & 1) << (2 * b)
+        code |= ((y >> b) & 1) << (2 * b + 1)
+    return (root << (2 * l)) | code
+
+
+def _unmorton2(key, l, roots_x):
+    key = int(key)
+    root = key >> (2 * l)
+    x = y = 0
+    for b in range(l):
+        x |= ((key >> (2 * b)) & 1) << b
+        y |= ((key >> (2 * b + 1)) & 1) << b
+    return ((root % roots_x) << l) | x, ((root // roots_x) << l) | y
+
+
+def gpu_leaves(solver, cfg):
+    keys, lev, f = solver.get_leaves()
+    d = 1 if cfg["scheme"].startswith("d1") else 2
+    if d == 1:
+        xs = keys.astype(np.int64)
+        ys = np.zeros_like(xs)
+    else:
+        xy = [_unmorton2(k, l, cfg["roots"][0]) for k, l in zip(keys.tolist(), lev.tolist())]
+        xs = np.array([p[0] for p in xy], np.int64)
+        ys = np.array([p[1] for p in xy], np.int64)
+    order = np.lexsort((xs, ys, lev))
+    return lev[order].astype(np.int64), xs[order], ys[order], f[:, order]
+
+
+def load_oracle_state(solver, ref, cfg):
+    lev, ix, iy, iz, f = ref.leaves()
+    d = 1 if cfg["scheme"].startswith("d1") else 2
+    if d == 1:
+        keys = ix.astype(np.uint64)
+    else:
+        keys = np.array([_morton2(x, y, l, cfg["roots"][0]) for x, y, l in zip(ix, iy, lev)], np.uint64)
+    solver.set_leaves(keys, lev.astype(np.int8), f)
+
+
+def compare(solver, ref, cfg, what=""):
+    glev, gx, gy, gf = gpu_leaves(solver, cfg)
+    lev, ix, iy, iz, f = ref.leaves()
+    same = (len(glev) == len(lev) and (glev == lev).all() and (gx == ix).all() and (gy == iy).all())
+    if not same:
+        pytest.fail("%s: leaf sets differ (gpu %d, oracle %d leaves, oracle margin %.3e)"
+                    % (what, len(glev), len(lev), ref.margin()))
+    scale = np.maximum(np.abs(f).max(axis=1, keepdims=True), 1e-300)
+    err = float((np.abs(gf - f) / scale).max())
+    assert err <= TOL, "%s: populations differ by %.3e (max-norm relative)" % (what, err)
+    return err
+
+
+def _solver(cfg, **kw):
+    from paper_2103_02903_gb300.binding import Solver
+    return Solver(cfg, **kw)
+
+
+CASES = [
+    ("advection_1d", dict(max_level=9), 35),
+    ("burgers_1d", dict(max_level=10), 30),
+    ("shallow_water_1d", dict(max_level=10), 30),
+    ("euler_2d", dict(max_level=7), 20),
+]
+
+
+@pytest.mark.parametrize("name,kw,steps", CASES)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_per_step_from_identical_state(name, kw, steps, seed):
+    """Each step starts both sides from the oracle's state: the leaf sets
+    must then agree bit for bit (details are computed in the same order)."""
+    cfg, u = W.WORKLOADS[name](seed=seed, **kw)
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    for it in range(min(steps, 12)):
+        load_oracle_state(gpu, ref, cfg)
+        gpu.step(1)
+        ref.step(1)
+        compare(gpu, ref, cfg, "%s seed %d step %d" % (name, seed, it))
+
+
+@pytest.mark.parametrize("name,kw,steps", CASES)
+def test_trajectory(name, kw, steps):
+    cfg, u = W.WORKLOADS[name](seed=2, **kw)
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    for it in range(steps):
+        gpu.step(1)
+        ref.step(1)
+        compare(gpu, ref, cfg, "%s step %d" % (name, it))
+
+
+def test_euler_full_size_first_steps():
+    """D2Q4^4 Euler at the benchmark size (J = 10, 1024^2 finest cells)."""
+    cfg, u = W.euler_2d(seed=0, max_level=10)
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    for it in range(3):
+        gpu.step(1)
+        ref.step(1)
+        compare(gpu, ref, cfg, "euler J10 step %d" % it)
+
+
+@pytest.mark.parametrize("name,kw", [("advection_1d", dict(max_level=8)), ("euler_2d", dict(max_level=6)),
+                                     ("shallow_water_1d", dict(max_level=8))])
+def test_epsilon_zero_full_mesh(name, kw):
+    cfg, u = W.WORKLOADS[name](seed=5, **kw)
+    cfg["eps"] = 0.0
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    gpu.step(6)
+    ref.step(6)
+    compare(gpu, ref, cfg, "eps=0")
+    assert gpu.num_leaves() == ref.num_leaves() == int(np.prod(ref.level_shape(cfg["max_level"])))
+
+
+def test_huge_epsilon_coarsest_mesh():
+    cfg, u = W.euler_2d(seed=6, max_level=6)
+    cfg["eps"] = 1e30
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    gpu.step(3)
+    ref.step(3)
+    compare(gpu, ref, cfg, "eps=inf")
+    per, _, _ = gpu.stats()
+    assert per[cfg["min_level"]] == gpu.num_leaves()
+
+
+def test_printed_cross_sign_variant():
+    cfg, u = W.euler_2d(seed=3, max_level=6)
+    cfg["cross_sign"] = -1
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    for it in range(6):
+        load_oracle_state(gpu, ref, cfg)
+        gpu.step(1)
+        ref.step(1)
+        compare(gpu, ref, cfg, "cross=-1 step %d" % it)
+
+
+def test_periodic_euler_and_mu_bar():
+    cfg, u = W.euler_2d(seed=4, max_level=6, mu_bar=1)
+    cfg["bc"] = ["periodic"] * 6
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    for it in range(8):
+        load_oracle_state(gpu, ref, cfg)
+        gpu.step(1)
+        ref.step(1)
+        compare(gpu, ref, cfg, "periodic step %d" % it)
+
+
+@pytest.mark.parametrize("name,kw", [("advection_1d", dict(max_level=9)), ("euler_2d", dict(max_level=7))])
+def test_adapt_and_project(name, kw):
+    cfg, u = W.WORKLOADS[name](seed=7, **kw)
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    gpu.step(4)
+    ref.step(4)
+    gpu.adapt()
+    ref.adapt()
+    compare(gpu, ref, cfg, "adapt")
+    for level in (cfg["min_level"], cfg["min_level"] + 1, cfg["max_level"]):
+        a = gpu.project(level)
+        b = ref.project(level)
+        scale = np.abs(b).max(axis=1, keepdims=True)
+        assert (np.abs(a - b) / scale).max() <= TOL
+
+
+def test_capacity_overflow_is_reported():
+    from paper_2103_02903_gb300.binding import MrError
+    cfg, u = W.euler_2d(seed=0, max_level=6)
+    gpu = _solver(cfg, leaf_capacity=16 * 16)
+    with pytest.raises(MrError) as ei:
+        gpu.init(u)
+        gpu.synchronize()
+    assert ei.value.status == 4  # MR_ECAPACITY
+
+
+def test_invalid_leaves_rejected():
+    from paper_2103_02903_gb300.binding import MrError
+    cfg, u = W.advection_1d(seed=0, max_level=5)
+    gpu = _solver(cfg)
+    keys = np.array([0, 1, 2, 3, 3], np.uint64)  # duplicate, does not cover the domain
+    lev = np.full(5, 2, np.int8)
+    f = np.zeros((2, 5))
+    with pytest.raises(MrError):
+        gpu.set_leaves(keys, lev, f)
+
+
+def test_mass_conservation_periodic():
+    cfg, u = W.euler_2d(seed=8, max_level=7)
+    cfg["bc"] = ["periodic"] * 6
+    gpu = _solver(cfg)
+    gpu.init(u)
+    J = cfg["max_level"]
+    m0 = gpu.project(J).sum(axis=1)
+    gpu.step(25)
+    m1 = gpu.project(J).sum(axis=1)
+    np.testing.assert_allclose(m1, m0, rtol=1e-12, atol=1e-12 * np.abs(m0).max())
+
+
+def test_counters_and_launches():
+    cfg, u = W.euler_2d(seed=0, max_level=6)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    n0 = gpu.launch_count()
+    gpu.step(3)
+    upd, steps = gpu.counters()
+    assert steps == 3 and upd > 0
+    assert gpu.launch_count() > n0
