@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Throughput of the fully adaptive MR-LBM time step on GB300.
+
+Workload: the D2Q4^4 compressible-Euler four-quadrant Riemann problem on
+[0, 1]^2 (gamma = 1.4, lambda = 5, s^q = 1.9/1.75, s^xy = 1, copy
+boundaries), min level 2, max level 10 (1024^2 finest cells), epsilon = 1e-3,
+mu_bar = 0, seeded quadrant states; FP64 plain form.  One step = one pass of
+Algorithm 1's loop (encode, T/H/G adaptation, compaction, data transfer,
+ghost prediction, transport, collision) through the C-ABI.  Metric: leaf
+updates per second (sum over timed steps of the leaves of the new mesh,
+divided by the event-timed duration of those steps).
+
+Runs on N GPUs as N independent replicas (the single-instance step does not
+shard).  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "adaptive leaf updates/s per MR-LBM step"
+UNIT = "leaf updates/s"
+WORKLOAD = "d2q4x4_euler_riemann_J10"
+
+# Algorithmic work of the transport + collision kernel per leaf (FP64 form,
+# D2Q4^4): reads and writes the 16 populations of the leaf and reads its key
+# and level (2 * 16 * 8 + 4 + 1 bytes); 320 FP64 flops (16 populations x 11
+# for the flattened row weights and update, 141 for the collision, see
+# the design doc).  Window values of neighbours are L2 reuse, not algorithmic.
+ALG_BYTES_PER_LEAF = 2 * 16 * 8 + 5
+ALG_FLOPS_PER_LEAF = 320.0
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--max-level", type=int, default=10)
+    p.add_argument("--e2e-steps", type=int, default=30)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--profile-groups", action="store_true",
+                   help="also time every kernel group once (extra steps, not part of value)")
+    return p.parse_args()
+
+
+def _workload(args):
+    from paper_2103_02903_gb300 import workloads
+    return workloads.euler_2d(seed=args.seed, max_level=args.max_level)
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        exe = shutil.which("nvidia-smi")
+        if exe:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen([exe, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-i", str(gpu_index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _fp64_peak_tflops(torch):
+    """FP64 throughput measured with a cuBLAS DGEMM (2 N^3 flops), best of 3."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def _oracle_sample(cfg, u, seconds, max_steps=None):
+    """Time oracle steps of the workload from its initial condition until
+    `seconds` of CPU time have elapsed (single thread)."""
+    from oracle import Oracle
+    o = Oracle(cfg)
+    o.init(u)
+    leaves, steps, t = 0, 0, 0.0
+    while t < seconds and (max_steps is None or steps < max_steps):
+        t0 = time.perf_counter()
+        o.step(1)
+        t += time.perf_counter() - t0
+        leaves += o.num_leaves()
+        steps += 1
+    return leaves, steps, t
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    cfg, u = _workload(args)
+    from oracle import Oracle
+    o = Oracle(cfg)
+    o.init(u)
+    budget = 150.0
+    # warm-up: at most min(W, 2) oracle steps
+    for _ in range(min(args.warmup, 2)):
+        o.step(1)
+    leaves, steps, t = 0, 0, 0.0
+    while steps < args.steps and t < budget:
+        t0 = time.perf_counter()
+        o.step(1)
+        t += time.perf_counter() - t0
+        leaves += o.num_leaves()
+        steps += 1
+    value = leaves / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": min(args.warmup, 2), "ms_per_step": 1e3 * t / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "max_level": cfg["max_level"],
+                                        "min_level": cfg["min_level"], "eps": cfg["eps"], "seed": args.seed},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "oracle steps %d..%d of the workload from its initial condition "
+                                   "(capped at %.0f s of CPU time)" % (min(args.warmup, 2) + 1,
+                                                                       min(args.warmup, 2) + steps, budget)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    from paper_2103_02903_gb300.binding import Solver
+
+    cfg, u = _workload(args)
+    stream = torch.cuda.current_stream()
+    solver = Solver(cfg, stream=stream.cuda_stream)
+    solver.init(u)
+    solver.step(args.warmup)
+    solver.synchronize()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    upd0, _ = solver.counters()
+    launches0 = solver.launch_count()
+    solver.profile_enable(1)  # events around the transport + collision kernel
+    clk = ClockSampler(local)
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        solver.step(1)
+        ev[k][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = clk.stop()
+    launches = solver.launch_count() - launches0
+    kern_ms, kern_n = solver.profile_read()
+    solver.profile_enable(0)
+    upd1, _ = solver.counters()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    leaf_updates = upd1 - upd0
+
+    # whole-job aggregate: updates summed over ranks, time = max over ranks
+    if dist is not None:
+        t = torch.tensor([float(leaf_updates), total_s], dtype=torch.float64, device="cuda")
+        s = t.clone()
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        m = t.clone()
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        leaf_updates_all, total_s_max = s[0].item(), m[1].item()
+    else:
+        leaf_updates_all, total_s_max = float(leaf_updates), total_s
+    value = leaf_updates_all / total_s_max
+    per_step_leaves = leaf_updates / args.steps
+
+    # roofline of the transport + collision kernel, timed live above
+    peaks, peak_kind = _peaks()
+    kern_avg_s = kern_ms / 1e3 / max(kern_n, 1)
+    fp64_tflops = _fp64_peak_tflops(torch)
+    achieved_tflops = ALG_FLOPS_PER_LEAF * per_step_leaves / kern_avg_s / 1e12
+    achieved_gbs = ALG_BYTES_PER_LEAF * per_step_leaves / kern_avg_s / 1e9
+    roofline = {
+        "kernel": "k_stream_collide<3> (transport + collision)",
+        "bound": "alu", "achieved": achieved_tflops, "peak": fp64_tflops, "unit": "TFLOP/s",
+        "frac": achieved_tflops / fp64_tflops,
+        "peak_kind": "FP64 measured with cuBLAS DGEMM in this run",
+        "traffic": None,
+        "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved_gbs / peaks["hbm_gbs"], "peak_kind": peak_kind},
+        "kernel_ms_avg": 1e3 * kern_avg_s, "kernel_share_of_step": kern_ms / 1e3 / total_s,
+        "alg_flops_per_leaf": ALG_FLOPS_PER_LEAF, "alg_bytes_per_leaf": ALG_BYTES_PER_LEAF,
+    }
+
+    groups = None
+    if args.profile_groups:
+        groups = {}
+        names = {1: "transport+collision", 2: "details", 3: "projection", 4: "prediction",
+                 5: "mesh adaptation+compaction", 6: "data transfer"}
+        for gid, name in names.items():
+            solver.profile_enable(gid)
+            solver.step(20)
+            ms, n = solver.profile_read()
+            groups[name] = {"ms_per_step": ms / 20.0, "launches_per_step": n / 20.0}
+        solver.profile_enable(0)
+
+    # end to end through the C-ABI with host buffers: upload the state,
+    # one step, download the state
+    e2e = None
+    if args.e2e_steps > 0:
+        n = solver.num_leaves()
+        cap = int(n * 1.5) + 1024
+        keys = torch.empty(cap, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+        levs = torch.empty(cap, dtype=torch.int8, pin_memory=True).numpy()
+        f = torch.empty(16 * cap, dtype=torch.float64, pin_memory=True).numpy()
+        nn = solver.get_leaves_into(keys[:cap], levs[:cap], f[:16 * cap])
+        h2d = d2h = 0
+        e2e_leaves = 0
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            fk = f[:16 * nn]
+            solver.set_leaves(keys[:nn], levs[:nn], fk.reshape(16, nn))
+            h2d += nn * (8 + 1 + 16 * 8)
+            solver.step(1)
+            nn = solver.get_leaves_into(keys[:cap], levs[:cap], f[:16 * cap])
+            d2h += nn * (8 + 1 + 16 * 8)
+            e2e_leaves += nn
+        barrier()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": e2e_leaves / t_e2e * world, "unit": UNIT,
+               "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
+               "steps": args.e2e_steps,
+               "call": "mr_lbm_set_leaves(host) + mr_lbm_step(1) + mr_lbm_get_leaves(host), pinned buffers"}
+
+    per_level, mesh_or, mem_or = solver.stats()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        lv, st, t = _oracle_sample(cfg, u, args.cpu_seconds)
+        cpu = {"value": lv / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "oracle (single thread) steps 1..%d of the same workload from its initial "
+                         "condition, %.1f s" % (st, t)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "scheme": "D2Q4^4 Euler", "max_level": cfg["max_level"],
+                       "min_level": cfg["min_level"], "eps": cfg["eps"], "mu_bar": cfg["mu_bar"],
+                       "seed": args.seed, "steps_timed": "%d..%d" % (args.warmup + 1, args.warmup + args.steps),
+                       "l2": "256 MiB write between timed steps, outside the step events",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "leaves_per_step_avg": per_step_leaves, "mesh_or_final": mesh_or, "mem_or_final": mem_or,
+            "wall_s_timed_region": t_wall,
+            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks,
+        }
+        if groups is not None:
+            line["kernel_groups"] = groups
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -156,10 +156,12 @@ mr_status mr_lbm_counters(mr_lbm_t h, long long* leaf_updates, long long* steps)
 /* Number of kernels the handle has launched since creation (host counter). */
 long long mr_lbm_launch_count(mr_lbm_t h);
 
-/* Time every launch of the transport-collision kernel with CUDA events on the
- * handle's stream while enabled.  mr_lbm_profile_read synchronises and
- * returns the total milliseconds and the number of timed launches since the
- * last enable. */
+/* Time every launch of one kernel group with a pair of CUDA events on the
+ * handle's stream: on = 1 transport+collision, 2 details, 3 projection,
+ * 4 ghost / new-leaf prediction, 5 mesh adaptation and compaction,
+ * 6 data transfer; 0 disables.  mr_lbm_profile_read synchronises and returns
+ * the total milliseconds and the number of timed launches since the last
+ * mr_lbm_profile_enable. */
 mr_status mr_lbm_profile_enable(mr_lbm_t h, int on);
 mr_status mr_lbm_profile_read(mr_lbm_t h, double* total_ms, long long* launches);
 

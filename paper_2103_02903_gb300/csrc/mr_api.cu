@@ -36,7 +36,7 @@ struct mr_lbm {
   bool initialized = false;
   mr_status sticky = MR_OK;
   long long launches = 0;
-  bool prof_on = false;
+  int prof_group = 0;  // 0 = off, else the kernel group timed with events
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<void*> allocs;
@@ -219,10 +219,31 @@ mr_status read_counts(mr_lbm* h, MeshCounts* out /*[2]*/) {
   return MR_OK;
 }
 
+cudaEvent_t next_event(mr_lbm* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// Kernel groups that mr_lbm_profile_enable can time.
+enum { PG_STREAM = 1, PG_DETAILS = 2, PG_PROJECT = 3, PG_PREDICT = 4, PG_MESH = 5, PG_REMESH = 6 };
+
+inline void prof_begin(mr_lbm* h, int group) {
+  if (h->prof_group == group) cudaEventRecord(next_event(h), h->st);
+}
+inline void prof_end(mr_lbm* h, int group) {
+  if (h->prof_group == group) cudaEventRecord(next_event(h), h->st);
+}
+
 // Encode of the current state: internal values, bottom-up (Def. Projection).
 void run_projection(mr_lbm* h, const MeshDev& A) {
   for (int L = h->g.J - 1; L >= h->g.Jmin; --L) {
+    prof_begin(h, PG_PROJECT);
     mr_launch_project(h->g, A, h->fstate, L, h->st, grid_for(h));
+    prof_end(h, PG_PROJECT);
     count_launch(h);
   }
 }
@@ -241,40 +262,34 @@ void run_adapt(mr_lbm* h) {
   MeshDev& A = h->mesh[h->cur];
   MeshDev& B = h->mesh[1 - h->cur];
   run_projection(h, A);
+  prof_begin(h, PG_DETAILS);
   mr_launch_details(g, A, h->fstate, h->st, grid_for(h));
+  prof_end(h, PG_DETAILS);
+  prof_begin(h, PG_MESH);
   mr_launch_flags_T(g, A, h->flags, h->st, grid_for(h));
   mr_launch_flags_H(g, A, h->flags, h->st, grid_for(h));
   mr_launch_grade(g, h->flags, A.cnt, h->st, grid_for(h));
   mr_launch_classify(g, h->flags, h->cls, h->st, grid_for(h));
   count_launch(h, g.J > g.Jmin + 1 ? 5 : 4);
   run_build(h, B);
+  prof_end(h, PG_MESH);
+  prof_begin(h, PG_REMESH);
   mr_launch_remesh_copy(g, A, h->fstate, B, h->fscratch, h->st, grid_for(h));
+  prof_end(h, PG_REMESH);
   count_launch(h);
   for (int l = g.Jmin + 1; l <= g.J; ++l) {
+    prof_begin(h, PG_PREDICT);
     mr_launch_predict_level(g, B, h->fscratch, l, h->st, grid_for(h));
+    prof_end(h, PG_PREDICT);
     count_launch(h);
   }
 }
 
-cudaEvent_t next_event(mr_lbm* h) {
-  if (h->ev_used == h->ev_pool.size()) {
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    h->ev_pool.push_back(e);
-  }
-  return h->ev_pool[h->ev_used++];
-}
-
 void run_stream(mr_lbm* h, const MeshDev& B, int do_stream, int do_collide) {
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (h->prof_on) {
-    e0 = next_event(h);
-    e1 = next_event(h);
-    cudaEventRecord(e0, h->st);
-  }
+  prof_begin(h, PG_STREAM);
   mr_launch_stream_collide(h->g, B, h->fscratch, h->fstate, h->W, do_stream, do_collide, h->st,
                            grid_for(h, 8));
-  if (h->prof_on) cudaEventRecord(e1, h->st);
+  prof_end(h, PG_STREAM);
   count_launch(h);
 }
 
@@ -631,9 +646,9 @@ mr_status mr_lbm_counters(mr_lbm_t h, long long* leaf_updates, long long* steps)
 long long mr_lbm_launch_count(mr_lbm_t h) { return h ? h->launches : 0; }
 
 mr_status mr_lbm_profile_enable(mr_lbm_t h, int on) {
-  if (!h) return MR_EINVAL;
+  if (!h || on < 0 || on > 6) return MR_EINVAL;
   if (!cuda_ok(h, cudaStreamSynchronize(h->st))) return MR_ECUDA;
-  h->prof_on = on != 0;
+  h->prof_group = on;
   h->ev_used = 0;
   return MR_OK;
 }
