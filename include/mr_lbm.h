@@ -129,6 +129,24 @@ mr_status mr_lbm_adapt(mr_lbm_t h);
  * cells inside coarser leaves.  `out` is SoA [ncons][N_level], row-major. */
 mr_status mr_lbm_project(mr_lbm_t h, int level, double* out, int on_device);
 
+/* Same result as mr_lbm_project, for callers that must not allocate memory
+ * during the call (the paper has no counterpart: this is a deployment aid).
+ * mr_lbm_project allocates its two dense level buffers on first use; a caller
+ * that is queueing work while a stream is captured into a CUDA graph, or
+ * whose device memory belongs to another allocator with a fixed budget,
+ * cannot let that happen.  This variant calls no cudaMalloc, cudaFree or
+ * allocating library routine: its level buffers live in one file-scope
+ * device array of 2^21 doubles (16 MiB) that each GPU loading the library
+ * holds until the process exits.  Limit: ncons * N_level <= 2^20 (e.g. the
+ * D2Q4^4 Euler scheme up to level 9); larger levels return MR_ECAPACITY
+ * without touching the handle, which stays usable.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make it before any stream capture.  All calls on a
+ * device share the array and its leftover contents (nothing in it has to
+ * start at zero); calls whose GPU work overlaps race on it, so serialise
+ * them.  Arguments, layout and synchronisation as in mr_lbm_project. */
+mr_status mr_lbm_project_noalloc(mr_lbm_t h, int level, double* out, int on_device);
+
 /* Copy the leaves out, sorted by (level, key).  Call with keys = levels =
  * f = NULL to query the count in *n_inout; otherwise *n_inout is the capacity
  * of the buffers on entry and the number written on return (MR_EINVAL if too

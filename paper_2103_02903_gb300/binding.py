@@ -72,6 +72,7 @@ def library():
         L.mr_lbm_step.argtypes = [vp, i]
         L.mr_lbm_adapt.argtypes = [vp]
         L.mr_lbm_project.argtypes = [vp, i, vp, i]
+        L.mr_lbm_project_noalloc.argtypes = [vp, i, vp, i]
         L.mr_lbm_get_leaves.argtypes = [vp, C.POINTER(ll), vp, vp, vp, i]
         L.mr_lbm_set_leaves.argtypes = [vp, ll, vp, vp, vp, i]
         L.mr_lbm_stats.argtypes = [vp, vp, C.POINTER(d), C.POINTER(d)]
@@ -85,7 +86,7 @@ def library():
         L.mr_lbm_strerror.restype = C.c_char_p
         L.mr_lbm_flattened_weights.argtypes = [i, i, i, i, i, vp]
         for name in ("mr_lbm_create", "mr_lbm_destroy", "mr_lbm_init", "mr_lbm_step", "mr_lbm_adapt",
-                     "mr_lbm_project", "mr_lbm_get_leaves", "mr_lbm_set_leaves", "mr_lbm_stats",
+                     "mr_lbm_project", "mr_lbm_project_noalloc", "mr_lbm_get_leaves", "mr_lbm_set_leaves", "mr_lbm_stats",
                      "mr_lbm_counters", "mr_lbm_profile_enable", "mr_lbm_profile_read",
                      "mr_lbm_synchronize", "mr_lbm_flattened_weights"):
             getattr(L, name).restype = i
@@ -192,6 +193,14 @@ class Solver:
             out = np.zeros((self.ncons, self.level_cells(level)), np.float64)
         p, dev = _ptr(out)
         _check(library().mr_lbm_project(self.h, int(level), p, dev), "mr_lbm_project")
+        return out
+
+    def project_noalloc(self, level: int, out=None):
+        """mr_lbm_project without allocation (fixed 16 MiB device scratch)."""
+        if out is None:
+            out = np.zeros((self.ncons, self.level_cells(level)), np.float64)
+        p, dev = _ptr(out)
+        _check(library().mr_lbm_project_noalloc(self.h, int(level), p, dev), "mr_lbm_project_noalloc")
         return out
 
     def num_leaves(self) -> int:

@@ -11,36 +11,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/mr_lbm.h"
-#include "mr_internal.cuh"
-
-struct mr_lbm {
-  Geo g;
-  cudaStream_t st = nullptr;
-  int nsm = 152;
-  MeshDev mesh[2];
-  MeshCounts* cntbuf = nullptr;  // two MeshCounts
-  int cur = 0;
-  double* fstate = nullptr;
-  double* fscratch = nullptr;
-  uint8_t* flags = nullptr;
-  uint8_t* cls = nullptr;
-  int* bcounts = nullptr;
-  int32_t* inidx = nullptr;
-  unsigned long long* vol = nullptr;
-  double* W = nullptr;
-  double* dense[2] = {nullptr, nullptr};
-  size_t dense_elems = 0;
-  void* staging = nullptr;
-  size_t staging_bytes = 0;
-  bool initialized = false;
-  mr_status sticky = MR_OK;
-  long long launches = 0;
-  int prof_group = 0;  // 0 = off, else the kernel group timed with events
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_used = 0;
-  std::vector<void*> allocs;
-};
+#include "mr_handle.cuh"
 
 namespace {
 
@@ -304,6 +275,10 @@ mr_status ensure_staging(mr_lbm* h, size_t bytes) {
 }
 
 }  // namespace
+
+mr_status mr_handle_fail(mr_lbm* h, mr_status s) { return fail(h, s); }
+void mr_handle_projection(mr_lbm* h) { run_projection(h, h->mesh[h->cur]); }
+mr_status mr_handle_read_counts(mr_lbm* h, MeshCounts* out) { return read_counts(h, out); }
 
 // =================================================================== C-ABI
 

@@ -1,0 +1,47 @@
+// Handle of the C-ABI (private to the library's translation units) and the
+// host-side helpers that more than one of them uses.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/mr_lbm.h"
+#include "mr_internal.cuh"
+
+struct mr_lbm {
+  Geo g;
+  cudaStream_t st = nullptr;
+  int nsm = 152;
+  MeshDev mesh[2];
+  MeshCounts* cntbuf = nullptr;  // two MeshCounts
+  int cur = 0;
+  double* fstate = nullptr;
+  double* fscratch = nullptr;
+  uint8_t* flags = nullptr;
+  uint8_t* cls = nullptr;
+  int* bcounts = nullptr;
+  int32_t* inidx = nullptr;
+  unsigned long long* vol = nullptr;
+  double* W = nullptr;
+  double* dense[2] = {nullptr, nullptr};
+  size_t dense_elems = 0;
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  bool initialized = false;
+  mr_status sticky = MR_OK;
+  long long launches = 0;
+  int prof_group = 0;  // 0 = off, else the kernel group timed with events
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<void*> allocs;
+};
+
+// Record a sticky failure on the handle and return it.
+mr_status mr_handle_fail(mr_lbm* h, mr_status s);
+// Queue the bottom-up projection of the current state into the internal
+// cells of the current mesh (no allocation).
+void mr_handle_projection(mr_lbm* h);
+// Copy both meshes' counters to the host, synchronise, and turn device error
+// bits into a status (no allocation).
+mr_status mr_handle_read_counts(mr_lbm* h, MeshCounts* out /*[2]*/);
