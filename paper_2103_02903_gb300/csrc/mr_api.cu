@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -264,6 +265,98 @@ void run_stream(mr_lbm* h, const MeshDev& B, int do_stream, int do_collide) {
   count_launch(h);
 }
 
+// One iteration of the loop of Algorithm 1 on the current stream.
+void run_step(mr_lbm* h) {
+  run_adapt(h);
+  MeshDev& B = h->mesh[1 - h->cur];
+  run_stream(h, B, 1, 1);
+  mr_launch_count_updates(B.cnt, h->st);
+  count_launch(h);
+}
+
+void drop_graphs(mr_lbm* h) {
+  for (auto& G : h->graphs) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G.exec = nullptr;
+    G.graph = nullptr;
+    G.prof = -1;
+    G.ev_nodes.clear();
+  }
+}
+
+// Capture run_step() for the current mesh parity into h->graphs[h->cur].
+bool capture_step(mr_lbm* h) {
+  mr_lbm::StepGraph& G = h->graphs[h->cur];
+  if (!h->cap_st && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) return false;
+  while (h->ev_pool.size() < h->ev_used + 64) {  // events are created outside the capture
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return false;
+    h->ev_pool.push_back(e);
+  }
+  const size_t ev0 = h->ev_used;
+  const long long l0 = h->launches;
+  cudaStream_t orig = h->st;
+  h->st = h->cap_st;
+  if (cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    h->st = orig;
+    return false;
+  }
+  run_step(h);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->cap_st, &graph);
+  h->st = orig;
+  std::vector<cudaEvent_t> cap_events(h->ev_pool.begin() + ev0, h->ev_pool.begin() + h->ev_used);
+  h->ev_used = ev0;
+  G.launches = h->launches - l0;
+  h->launches = l0;
+  if (e != cudaSuccess || !graph) return false;
+  size_t n = 0;
+  cudaGraphGetNodes(graph, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) cudaGraphGetNodes(graph, nodes.data(), &n);
+  G.ev_nodes.assign(cap_events.size(), nullptr);
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t ev;
+    if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+    for (size_t i = 0; i < cap_events.size(); ++i)
+      if (cap_events[i] == ev) G.ev_nodes[i] = nd;
+  }
+  for (cudaGraphNode_t nd : G.ev_nodes)
+    if (!nd) {
+      cudaGraphDestroy(graph);
+      return false;
+    }
+  if (cudaGraphInstantiate(&G.exec, graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    G.exec = nullptr;
+    return false;
+  }
+  G.graph = graph;
+  G.prof = h->prof_group;
+  return true;
+}
+
+// One step by graph replay (captured on first use for this parity and
+// profiling mode); false if graphs cannot be used, and nothing was queued.
+bool graph_step(mr_lbm* h) {
+  mr_lbm::StepGraph& G = h->graphs[h->cur];
+  if (G.exec && G.prof != h->prof_group) {
+    cudaGraphExecDestroy(G.exec);
+    cudaGraphDestroy(G.graph);
+    G.exec = nullptr;
+    G.graph = nullptr;
+  }
+  if (!G.exec && !capture_step(h)) return false;
+  for (cudaGraphNode_t nd : G.ev_nodes)
+    if (cudaGraphExecEventRecordNodeSetEvent(G.exec, nd, next_event(h)) != cudaSuccess) return false;
+  if (cudaGraphLaunch(G.exec, h->st) != cudaSuccess) return false;
+  h->launches += G.launches;
+  return true;
+}
+
 mr_status ensure_staging(mr_lbm* h, size_t bytes) {
   if (h->staging_bytes >= bytes) return MR_OK;
   if (h->staging) cudaFree(h->staging);
@@ -351,6 +444,7 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   for (int a = 0; a < 3; ++a) g.periodic[a] = a < g.d && cfg->bc[2 * a] == MR_BC_PERIODIC;
   for (int f = 0; f < 6; ++f) g.bc[f] = cfg->bc[f];
   g.lambda = cfg->lambda;
+  g.inv_lambda = 1.0 / cfg->lambda;
   for (int i = 0; i < 16; ++i) g.s[i] = cfg->s[i];
   for (int i = 0; i < 8; ++i) g.phys[i] = cfg->phys[i];
   g.eps = cfg->eps;
@@ -366,6 +460,10 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   g.cap[1] = (int)std::max<long long>(nint, 1);
   g.cap[2] = (int)nall;
   h->st = (cudaStream_t)cuda_stream;
+  {
+    const char* env = getenv("MR_LBM_GRAPHS");  // "0" launches every kernel directly
+    h->use_graph = !(env && env[0] == '0');
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -410,7 +508,9 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
 
 mr_status mr_lbm_destroy(mr_lbm_t h) {
   if (!h) return MR_OK;
-  if (h->st || true) cudaStreamSynchronize(h->st);
+  cudaStreamSynchronize(h->st);
+  drop_graphs(h);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   for (void* p : h->allocs) cudaFree(p);
   if (h->staging) cudaFree(h->staging);
   for (int i = 0; i < 2; ++i)
@@ -449,11 +549,10 @@ mr_status mr_lbm_step(mr_lbm_t h, int nsteps) {
   if (h->sticky != MR_OK) return h->sticky;
   if (!h->initialized) return fail(h, MR_ESTATE);
   for (int it = 0; it < nsteps; ++it) {
-    run_adapt(h);
-    MeshDev& B = h->mesh[1 - h->cur];
-    run_stream(h, B, 1, 1);
-    mr_launch_count_updates(B.cnt, h->st);
-    count_launch(h);
+    if (!(h->use_graph && graph_step(h))) {
+      h->use_graph = false;  // graphs unavailable: launch the kernels directly from now on
+      run_step(h);
+    }
     h->cur = 1 - h->cur;
   }
   return check_launch(h);
@@ -465,6 +564,7 @@ mr_status mr_lbm_adapt(mr_lbm_t h) {
   if (!h->initialized) return fail(h, MR_ESTATE);
   run_adapt(h);
   std::swap(h->fstate, h->fscratch);
+  drop_graphs(h);  // captured steps refer to the swapped buffers
   h->cur = 1 - h->cur;
   return check_launch(h);
 }

@@ -35,6 +35,18 @@ struct mr_lbm {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<void*> allocs;
+  // One time step captured as a CUDA graph per mesh parity (the two meshes
+  // alternate), replayed by mr_lbm_step; the event-record nodes of a
+  // profiled kernel group are pointed at fresh events before each replay.
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    int prof = -1;
+    long long launches = 0;
+    std::vector<cudaGraphNode_t> ev_nodes;
+    cudaGraph_t graph = nullptr;
+  } graphs[2];
+  bool use_graph = true;
+  cudaStream_t cap_st = nullptr;
 };
 
 // Record a sticky failure on the handle and return it.

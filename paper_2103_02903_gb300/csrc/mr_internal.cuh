@@ -48,6 +48,7 @@ struct Geo {
   int periodic[3];
   int bc[6];
   double lambda;
+  double inv_lambda;
   double s[16];
   double phys[8];
   double eps;

@@ -100,13 +100,14 @@ struct Scheme<3> {
   __device__ static int opp(int p) { return (p & ~3) | ((p + 2) & 3); }
   __device__ static void fluxes(const Geo& g, const double* u, double* fx, double* fy) {
     const double rho = u[0], mx = u[1], my = u[2], E = u[3], gam = g.phys[0];
-    const double vx = mx / rho, vy = my / rho;
+    const double irho = 1.0 / rho;  // one FP64 division per cell
+    const double vx = mx * irho, vy = my * irho;
     const double pr = (gam - 1.0) * (E - 0.5 * (mx * vx + my * vy));
     fx[0] = mx; fx[1] = mx * vx + pr; fx[2] = my * vx; fx[3] = vx * (E + pr);
     fy[0] = my; fy[1] = mx * vy; fy[2] = my * vy + pr; fy[3] = vy * (E + pr);
   }
   __device__ static void from_moments(const Geo& g, double m0, double m1, double m2, double m3, double* f) {
-    const double il = 1.0 / g.lambda, il2 = il * il;
+    const double il = g.inv_lambda, il2 = il * il;
     const double a = 0.25 * m0, b = 0.5 * m1 * il, c = 0.5 * m2 * il, e = 0.25 * m3 * il2;
     f[0] = a + b + e;
     f[1] = a + c - e;
