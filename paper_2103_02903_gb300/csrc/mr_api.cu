@@ -214,7 +214,7 @@ inline void prof_end(mr_lbm* h, int group) {
 void run_projection(mr_lbm* h, const MeshDev& A) {
   for (int L = h->g.J - 1; L >= h->g.Jmin; --L) {
     prof_begin(h, PG_PROJECT);
-    mr_launch_project(h->g, A, h->fstate, L, h->st, grid_for(h));
+    mr_launch_project(h->g, A, h->fstate, L, h->st, grid_for(h, 8));
     prof_end(h, PG_PROJECT);
     count_launch(h);
   }
@@ -235,7 +235,7 @@ void run_adapt(mr_lbm* h) {
   MeshDev& B = h->mesh[1 - h->cur];
   run_projection(h, A);
   prof_begin(h, PG_DETAILS);
-  mr_launch_details(g, A, h->fstate, h->st, grid_for(h));
+  mr_launch_details(g, A, h->fstate, h->st, grid_for(h, 8));
   prof_end(h, PG_DETAILS);
   prof_begin(h, PG_MESH);
   mr_launch_flags_T(g, A, h->flags, h->st, grid_for(h));
@@ -246,12 +246,12 @@ void run_adapt(mr_lbm* h) {
   run_build(h, B);
   prof_end(h, PG_MESH);
   prof_begin(h, PG_REMESH);
-  mr_launch_remesh_copy(g, A, h->fstate, B, h->fscratch, h->st, grid_for(h));
+  mr_launch_remesh_copy(g, A, h->fstate, B, h->fscratch, h->st, grid_for(h, 8));
   prof_end(h, PG_REMESH);
   count_launch(h);
   for (int l = g.Jmin + 1; l <= g.J; ++l) {
     prof_begin(h, PG_PREDICT);
-    mr_launch_predict_level(g, B, h->fscratch, l, h->st, grid_for(h));
+    mr_launch_predict_level(g, B, h->fscratch, l, h->st, grid_for(h, 8));
     prof_end(h, PG_PREDICT);
     count_launch(h);
   }

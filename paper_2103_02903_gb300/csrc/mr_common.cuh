@@ -47,6 +47,23 @@ __device__ __forceinline__ int mr_level_of(const Geo& g, uint32_t gi) {
   return l;
 }
 
+// Dense kernels run one block of 256 threads per 1024-cell chunk of the dense
+// index space, starting at chunk `chunk0`.  Every level starts on a chunk
+// boundary, so a block finds its level once; the body sees the level L, the
+// code C and the dense index GI of each valid cell of the chunk.
+#define MR_DENSE_CHUNK_BEGIN(g, chunk0, L, C, GI)                              \
+  {                                                                           \
+    const uint32_t mr_chunk_ = (chunk0) + blockIdx.x;                         \
+    const int L = mr_level_of(g, mr_chunk_ * MR_DENSE_ALIGN);                 \
+    const uint32_t mr_cb_ = mr_chunk_ * MR_DENSE_ALIGN - (g).base[L];         \
+    for (int mr_k_ = 0; mr_k_ < (int)(MR_DENSE_ALIGN / 256u); ++mr_k_) {      \
+      const uint32_t C = mr_cb_ + (uint32_t)mr_k_ * 256u + threadIdx.x;       \
+      if (C >= (g).ncode[L]) break;                                           \
+      const uint32_t GI = (g).base[L] + C;
+#define MR_DENSE_CHUNK_END \
+  }                        \
+  }
+
 // Canonical s = 1 prediction of child ci from a 3^D stencil (x fastest),
 // evaluated in the order written in Sec. 4.1 with no fused multiply-add:
 // the same bits as the CPU oracle on the same inputs.

@@ -12,12 +12,22 @@
 
 namespace {
 
+// Thread layout of the encode kernels: a block is 32 cells (threadIdx.x) by
+// up to 8 populations (threadIdx.y), so a warp handles one population of 32
+// consecutive cells: its loads are independent of its stores and coalesce
+// where the cells' children are consecutive.
+template <int Q>
+struct PopRows {
+  static constexpr int value = Q < 8 ? Q : 8;
+};
+
 template <int D, int Q>
 __global__ void __launch_bounds__(256) k_project(Geo g, MeshDev A, const double* __restrict__ LF,
                                                  int level) {
+  constexpr int PY = PopRows<Q>::value;
   const int begin = A.cnt->off[MR_CLS_INT][level], end = A.cnt->off[MR_CLS_INT][level + 1];
   const double scale = D == 1 ? 0.5 : 0.25;
-  for (int i = begin + blockIdx.x * blockDim.x + threadIdx.x; i < end; i += gridDim.x * blockDim.x) {
+  for (int i = begin + blockIdx.x * 32 + threadIdx.x; i < end; i += gridDim.x * 32) {
     const uint32_t code = A.code[MR_CLS_INT][i];
     ValPtr ch[1 << D];
     bool ok = true;
@@ -28,11 +38,11 @@ __global__ void __launch_bounds__(256) k_project(Geo g, MeshDev A, const double*
       ch[ci] = mr_resolve(g, A, LF, e);
     }
     if (!ok) {
-      mr_set_err(A.cnt, MR_DERR_INTERNAL);
+      if (threadIdx.y == 0) mr_set_err(A.cnt, MR_DERR_INTERNAL);
       continue;
     }
-#pragma unroll 4
-    for (int p = 0; p < Q; ++p) {
+#pragma unroll
+    for (int p = threadIdx.y; p < Q; p += PY) {
       double acc = 0.0;
 #pragma unroll
       for (int ci = 0; ci < (1 << D); ++ci) acc = __dadd_rn(acc, mr_ld(ch[ci], p));
@@ -43,54 +53,71 @@ __global__ void __launch_bounds__(256) k_project(Geo g, MeshDev A, const double*
 
 template <int D, int Q>
 __global__ void __launch_bounds__(256) k_details(Geo g, MeshDev A, const double* __restrict__ LF) {
+  constexpr int PY = PopRows<Q>::value;
+  __shared__ double red[PY][32];
   const int n = A.cnt->total[MR_CLS_INT];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int L = A.lvl[MR_CLS_INT][i];
-    const uint32_t code = A.code[MR_CLS_INT][i];
-    int x, y;
-    mr_decode(g, L, code, x, y);
-    int32_t st[9];
-    bool ok = mr_stencil_entries<D>(g, A, L, x, y, st);
-    ValPtr sv[D == 2 ? 9 : 3], cv[1 << D];
-#pragma unroll
-    for (int k = 0; k < (D == 2 ? 9 : 3); ++k) {
-      ok = ok && (((uint32_t)st[k]) >> 30) <= MR_CLS_INT;
-      sv[k] = mr_resolve(g, A, LF, st[k]);
-    }
-#pragma unroll
-    for (int ci = 0; ci < (1 << D); ++ci) {
-      int32_t e = A.map[g.base[L + 1] + ((code << D) | (uint32_t)ci)];
-      ok = ok && e != MR_MAP_NONE && (((uint32_t)e) >> 30) <= MR_CLS_INT;
-      cv[ci] = mr_resolve(g, A, LF, e);
-    }
-    if (!ok) {
-      mr_set_err(A.cnt, MR_DERR_INTERNAL);
-      A.G[i] = 0.0;
-      continue;
-    }
+  for (int i0 = blockIdx.x * 32; i0 < n; i0 += gridDim.x * 32) {  // uniform over the block
+    const int i = i0 + threadIdx.x;
     double gmax = 0.0;
-    for (int p = 0; p < Q; ++p) {
-      double v[D == 2 ? 9 : 3];
+    if (i < n) {
+      const int L = A.lvl[MR_CLS_INT][i];
+      const uint32_t code = A.code[MR_CLS_INT][i];
+      int x, y;
+      mr_decode(g, L, code, x, y);
+      int32_t st[9];
+      bool ok = mr_stencil_entries<D>(g, A, L, x, y, st);
+      ValPtr sv[D == 2 ? 9 : 3], cv[1 << D];
 #pragma unroll
-      for (int k = 0; k < (D == 2 ? 9 : 3); ++k) v[k] = mr_ld(sv[k], p);
+      for (int k = 0; k < (D == 2 ? 9 : 3); ++k) {
+        ok = ok && (((uint32_t)st[k]) >> 30) <= MR_CLS_INT;
+        sv[k] = mr_resolve(g, A, LF, st[k]);
+      }
 #pragma unroll
       for (int ci = 0; ci < (1 << D); ++ci) {
-        double det = __dsub_rn(mr_ld(cv[ci], p), mr_predict_canonical<D>(v, ci, g.cross_sign));
-        gmax = fmax(gmax, fabs(det));
+        int32_t e = A.map[g.base[L + 1] + ((code << D) | (uint32_t)ci)];
+        ok = ok && e != MR_MAP_NONE && (((uint32_t)e) >> 30) <= MR_CLS_INT;
+        cv[ci] = mr_resolve(g, A, LF, e);
+      }
+      if (!ok) {
+        if (threadIdx.y == 0) mr_set_err(A.cnt, MR_DERR_INTERNAL);
+      } else {
+#pragma unroll
+        for (int p = threadIdx.y; p < Q; p += PY) {
+          double v[D == 2 ? 9 : 3], c[1 << D];
+#pragma unroll
+          for (int k = 0; k < (D == 2 ? 9 : 3); ++k) v[k] = mr_ld(sv[k], p);
+#pragma unroll
+          for (int ci = 0; ci < (1 << D); ++ci) c[ci] = mr_ld(cv[ci], p);
+#pragma unroll
+          for (int ci = 0; ci < (1 << D); ++ci) {
+            double det = __dsub_rn(c[ci], mr_predict_canonical<D>(v, ci, g.cross_sign));
+            gmax = fmax(gmax, fabs(det));
+          }
+        }
       }
     }
-    A.G[i] = gmax;
+    red[threadIdx.y][threadIdx.x] = gmax;
+    __syncthreads();
+    if (threadIdx.y == 0 && i < n) {
+      double m = red[0][threadIdx.x];
+#pragma unroll
+      for (int k = 1; k < PY; ++k) m = fmax(m, red[k][threadIdx.x]);
+      A.G[i] = m;
+    }
+    __syncthreads();
   }
 }
 
+// `grid` is the maximum number of blocks; a block covers 32 cells.
 template <int D, int Q>
 void launch_project_t(const Geo& g, const MeshDev& A, const double* LF, int level, cudaStream_t st,
                       int grid) {
-  k_project<D, Q><<<grid, 256, 0, st>>>(g, A, LF, level);
+  const int need = (int)((g.ncode[level] + 31) / 32);
+  k_project<D, Q><<<need < grid ? need : grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LF, level);
 }
 template <int D, int Q>
 void launch_details_t(const Geo& g, const MeshDev& A, const double* LF, cudaStream_t st, int grid) {
-  k_details<D, Q><<<grid, 256, 0, st>>>(g, A, LF);
+  k_details<D, Q><<<grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LF);
 }
 
 }  // namespace

@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(256) k_flags_H(Geo g, MeshDev A, uint8_t* flag
 // continues the cascade from it, depth first, towards J_min.
 template <int D>
 __global__ void __launch_bounds__(256) k_grade(Geo g, uint8_t* flags) {
+  // grid-stride (not one block per chunk): refined cells cluster, and
+  // interleaving spreads their cascades over all blocks
   const uint32_t lo = g.base[g.Jmin + 1], hi = g.base[g.J];
   const int noff = D == 2 ? 9 : 3;
   for (uint32_t gi = lo + blockIdx.x * blockDim.x + threadIdx.x; gi < hi; gi += gridDim.x * blockDim.x) {
@@ -112,24 +114,18 @@ __global__ void __launch_bounds__(256) k_grade(Geo g, uint8_t* flags) {
 template <int D>
 __global__ void __launch_bounds__(256) k_classify(Geo g, const uint8_t* __restrict__ flags,
                                                   uint8_t* cls) {
-  const uint32_t lo = g.base[g.Jmin], hi = g.base[g.J + 1];
-  for (uint32_t gi = lo + blockIdx.x * blockDim.x + threadIdx.x; gi < hi; gi += gridDim.x * blockDim.x) {
-    const int l = mr_level_of(g, gi);
-    const uint32_t c = gi - g.base[l];
-    if (c >= g.ncode[l]) continue;
+  MR_DENSE_CHUNK_BEGIN(g, 0u, l, c, gi)
     const bool inR = (l == g.Jmin) || (flags[g.base[l - 1] + (c >> D)] & (MR_F_H | MR_F_G));
     const bool ref = (l < g.J) && (flags[gi] & (MR_F_H | MR_F_G));
     cls[gi] = inR ? (ref ? MR_C_INT : MR_C_LEAF) : 0;
-  }
+  MR_DENSE_CHUNK_END
 }
 
 __global__ void __launch_bounds__(256) k_full_mesh(Geo g, uint8_t* cls) {
-  const uint32_t lo = g.base[g.Jmin], hi = g.base[g.J + 1];
-  for (uint32_t gi = lo + blockIdx.x * blockDim.x + threadIdx.x; gi < hi; gi += gridDim.x * blockDim.x) {
-    const int l = mr_level_of(g, gi);
-    if (gi - g.base[l] >= g.ncode[l]) continue;
+  MR_DENSE_CHUNK_BEGIN(g, 0u, l, c, gi)
+    (void)c;
     cls[gi] = l == g.J ? MR_C_LEAF : MR_C_INT;
-  }
+  MR_DENSE_CHUNK_END
 }
 
 // ---------------------------------------------------------------- ghosts
@@ -139,13 +135,9 @@ __global__ void __launch_bounds__(256) k_full_mesh(Geo g, uint8_t* cls) {
 // whose stencil cells outside R(Lambda) are ghosts in turn.
 template <int D>
 __global__ void __launch_bounds__(256) k_mark_ghosts(Geo g, uint8_t* cls) {
-  const uint32_t lo = g.base[g.Jmin], hi = g.base[g.J + 1];
   const int nwin = 4 * D;
-  for (uint32_t gi = lo + blockIdx.x * blockDim.x + threadIdx.x; gi < hi; gi += gridDim.x * blockDim.x) {
+  MR_DENSE_CHUNK_BEGIN(g, 0u, l, c, gi)
     if ((cls[gi] & 3u) != MR_C_LEAF) continue;
-    const int l = mr_level_of(g, gi);
-    const uint32_t c = gi - g.base[l];
-    if (c >= g.ncode[l]) continue;
     int x, y;
     mr_decode(g, l, c, x, y);
     for (int w = 0; w < nwin; ++w) {
@@ -190,7 +182,7 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(Geo g, uint8_t* cls) {
         ++sp;
       }
     }
-  }
+  MR_DENSE_CHUNK_END
 }
 
 // ---------------------------------------------------------------- compaction
@@ -365,17 +357,21 @@ void mr_launch_flags_T(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStrea
 void mr_launch_flags_H(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid) {
   MR_DISPATCH_D(k_flags_H, grid, 256, st, g, A, flags);
 }
+// dense kernels: one block per 1024-cell chunk (the `grid` argument is unused)
+static int dense_chunks(const Geo& g, int lo_level, int hi_level_excl) {
+  return (int)((g.base[hi_level_excl] - g.base[lo_level]) / MR_DENSE_ALIGN);
+}
 void mr_launch_grade(const Geo& g, uint8_t* flags, MeshCounts*, cudaStream_t st, int grid) {
   if (g.J > g.Jmin + 1) MR_DISPATCH_D(k_grade, grid, 256, st, g, flags);
 }
-void mr_launch_classify(const Geo& g, const uint8_t* flags, uint8_t* cls, cudaStream_t st, int grid) {
-  MR_DISPATCH_D(k_classify, grid, 256, st, g, flags, cls);
+void mr_launch_classify(const Geo& g, const uint8_t* flags, uint8_t* cls, cudaStream_t st, int) {
+  MR_DISPATCH_D(k_classify, dense_chunks(g, g.Jmin, g.J + 1), 256, st, g, flags, cls);
 }
-void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int grid) {
-  k_full_mesh<<<grid, 256, 0, st>>>(g, cls);
+void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int) {
+  k_full_mesh<<<dense_chunks(g, g.Jmin, g.J + 1), 256, 0, st>>>(g, cls);
 }
-void mr_launch_mark_ghosts(const Geo& g, uint8_t* cls, cudaStream_t st, int grid) {
-  MR_DISPATCH_D(k_mark_ghosts, grid, 256, st, g, cls);
+void mr_launch_mark_ghosts(const Geo& g, uint8_t* cls, cudaStream_t st, int) {
+  MR_DISPATCH_D(k_mark_ghosts, dense_chunks(g, g.Jmin, g.J + 1), 256, st, g, cls);
 }
 void mr_launch_compact(const Geo& g, uint8_t* cls, uint8_t* flags, int* block_counts, MeshDev& B,
                        cudaStream_t st) {

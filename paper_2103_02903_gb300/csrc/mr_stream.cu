@@ -154,11 +154,19 @@ __device__ __forceinline__ double bc_value(int kind, const double* f, int p, int
 }
 
 // ------------------------------------------------------------------ transfer
+// Thread layout of the transfer kernels: 32 cells (threadIdx.x) by up to 8
+// populations (threadIdx.y), one population per warp.
+template <int Q>
+struct PopRows {
+  static constexpr int value = Q < 8 ? Q : 8;
+};
+
 template <int Q>
 __global__ void __launch_bounds__(256) k_remesh_copy(Geo g, MeshDev A, const double* __restrict__ LFold,
                                                      MeshDev B, double* LFnew) {
+  constexpr int PY = PopRows<Q>::value;
   const int nL = B.cnt->total[MR_CLS_LEAF], nI = B.cnt->total[MR_CLS_INT];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nL + nI; t += gridDim.x * blockDim.x) {
+  for (int t = blockIdx.x * 32 + threadIdx.x; t < nL + nI; t += gridDim.x * 32) {
     const bool leaf = t < nL;
     const int i = leaf ? t : t - nL;
     const int k = leaf ? MR_CLS_LEAF : MR_CLS_INT;
@@ -168,13 +176,14 @@ __global__ void __launch_bounds__(256) k_remesh_copy(Geo g, MeshDev A, const dou
       const ValPtr s = mr_resolve(g, A, LFold, e);
       double* dst = leaf ? LFnew + i : B.IF + i;
       const size_t ds = leaf ? g.cap[0] : g.cap[1];
-#pragma unroll 4
-      for (int p = 0; p < Q; ++p) dst[(size_t)p * ds] = mr_ld(s, p);
-      if (leaf) B.src[i] = e;
-    } else if (leaf) {
-      B.src[i] = -1;
-    } else {
-      mr_set_err(B.cnt, MR_DERR_INTERNAL);
+#pragma unroll
+      for (int p = threadIdx.y; p < Q; p += PY) dst[(size_t)p * ds] = mr_ld(s, p);
+      if (leaf && threadIdx.y == 0) B.src[i] = e;
+    } else if (threadIdx.y == 0) {
+      if (leaf)
+        B.src[i] = -1;
+      else
+        mr_set_err(B.cnt, MR_DERR_INTERNAL);
     }
   }
 }
@@ -183,11 +192,12 @@ __global__ void __launch_bounds__(256) k_remesh_copy(Geo g, MeshDev A, const dou
 // applied to level-1 values of the new mesh (all present by construction).
 template <int D, int Q>
 __global__ void __launch_bounds__(256) k_predict_level(Geo g, MeshDev B, double* LF, int level) {
+  constexpr int PY = PopRows<Q>::value;
   const int gb = B.cnt->off[MR_CLS_GHOST][level], ge = B.cnt->off[MR_CLS_GHOST][level + 1];
   const int lb = B.cnt->off[MR_CLS_LEAF][level], le = B.cnt->off[MR_CLS_LEAF][level + 1];
   const int ng = ge - gb, total = ng + (le - lb);
   const double cs = (double)g.cross_sign;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+  for (int t = blockIdx.x * 32 + threadIdx.x; t < total; t += gridDim.x * 32) {
     uint32_t code;
     double* out;
     size_t ostride;
@@ -207,15 +217,15 @@ __global__ void __launch_bounds__(256) k_predict_level(Geo g, MeshDev B, double*
     mr_decode(g, level - 1, code >> D, px, py);
     int32_t st[9];
     if (!mr_stencil_entries<D>(g, B, level - 1, px, py, st)) {
-      mr_set_err(B.cnt, MR_DERR_INTERNAL);
+      if (threadIdx.y == 0) mr_set_err(B.cnt, MR_DERR_INTERNAL);
       continue;
     }
     ValPtr sv[D == 2 ? 9 : 3];
 #pragma unroll
     for (int k = 0; k < (D == 2 ? 9 : 3); ++k) sv[k] = mr_resolve(g, B, LF, st[k]);
     const int ci = (int)(code & ((1u << D) - 1u));
-#pragma unroll 4
-    for (int p = 0; p < Q; ++p) {
+#pragma unroll
+    for (int p = threadIdx.y; p < Q; p += PY) {
       double v[D == 2 ? 9 : 3];
 #pragma unroll
       for (int k = 0; k < (D == 2 ? 9 : 3); ++k) v[k] = mr_ld(sv[k], p);
@@ -452,11 +462,13 @@ __global__ void k_count_updates(MeshCounts* cnt) {
 template <int Q>
 void launch_remesh_t(const Geo& g, const MeshDev& A, const double* LFo, const MeshDev& B, double* LFn,
                      cudaStream_t st, int grid) {
-  k_remesh_copy<Q><<<grid, 256, 0, st>>>(g, A, LFo, B, LFn);
+  k_remesh_copy<Q><<<grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LFo, B, LFn);
 }
 template <int D, int Q>
 void launch_predict_t(const Geo& g, const MeshDev& B, double* LF, int level, cudaStream_t st, int grid) {
-  k_predict_level<D, Q><<<grid, 256, 0, st>>>(g, B, LF, level);
+  // `grid` is the maximum number of blocks; a block covers 32 cells
+  const int need = (int)((2u * g.ncode[level] + 31) / 32);
+  k_predict_level<D, Q><<<need < grid ? need : grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, B, LF, level);
 }
 
 }  // namespace
