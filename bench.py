@@ -40,6 +40,8 @@ WORKLOAD = "d2q4x4_euler_riemann_J10"
 # the design doc).  Window values of neighbours are L2 reuse, not algorithmic.
 ALG_BYTES_PER_LEAF = 2 * 16 * 8 + 5
 ALG_FLOPS_PER_LEAF = 320.0
+FORM_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+FORM_DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}
 
 
 def _args():
@@ -55,6 +57,9 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--profile-groups", action="store_true",
                    help="also time every kernel group once (extra steps, not part of value)")
+    p.add_argument("--form", default="fp64", choices=["fp64", "fp32", "fp16", "bf16"],
+                   help="storage / arithmetic form of the timed run")
+    p.add_argument("--all-forms", action="store_true", help="also time every form (extra runs)")
     return p.parse_args()
 
 
@@ -208,34 +213,53 @@ def run_ours(args):
 
     cfg, u = _workload(args)
     stream = torch.cuda.current_stream()
-    solver = Solver(cfg, stream=stream.cuda_stream)
-    solver.init(u)
-    solver.step(args.warmup)
-    solver.synchronize()
-
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    upd0, _ = solver.counters()
-    launches0 = solver.launch_count()
-    solver.profile_enable(1)  # events around the transport + collision kernel
-    clk = ClockSampler(local)
-    barrier()
-    t_wall = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
-        ev[k][0].record(stream)
-        solver.step(1)
-        ev[k][1].record(stream)
-    barrier()
-    t_wall = time.perf_counter() - t_wall
-    clocks = clk.stop()
-    launches = solver.launch_count() - launches0
-    kern_ms, kern_n = solver.profile_read()
-    solver.profile_enable(0)
-    upd1, _ = solver.counters()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    leaf_updates = upd1 - upd0
+
+    def timed_run(form, clocks_too=False):
+        """W untimed steps, then K steps timed one by one with CUDA events
+        (L2 flushed between them, outside the events)."""
+        s = Solver(dict(cfg, precision=form), stream=stream.cuda_stream)
+        s.init(u)
+        s.step(args.warmup)
+        s.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        upd0, _ = s.counters()
+        l0 = s.launch_count()
+        s.profile_enable(1)  # events around the transport + collision kernel
+        clk = ClockSampler(local) if clocks_too else None
+        barrier()
+        tw = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            s.step(1)
+            ev[k][1].record(stream)
+        barrier()
+        tw = time.perf_counter() - tw
+        clocks = clk.stop() if clk else None
+        kms, kn = s.profile_read()
+        s.profile_enable(0)
+        upd1, _ = s.counters()
+        tot = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        return s, dict(updates=upd1 - upd0, total_s=tot, wall_s=tw, launches=s.launch_count() - l0,
+                       kern_ms=kms, kern_n=kn, clocks=clocks)
+
+    solver, r = timed_run(args.form, clocks_too=True)
+    clocks, launches, kern_ms, kern_n = r["clocks"], r["launches"], r["kern_ms"], r["kern_n"]
+    total_s, t_wall, leaf_updates = r["total_s"], r["wall_s"], r["updates"]
+    forms = None
+    if args.all_forms:
+        forms = {}
+        for fm in ("fp64", "fp32", "fp16", "bf16"):
+            s2, r2 = timed_run(fm)
+            lv = r2["updates"] / args.steps
+            ksec = r2["kern_ms"] / 1e3 / max(r2["kern_n"], 1)
+            bpl = 2 * 16 * FORM_BYTES[fm] + 5
+            forms[fm] = {"value": r2["updates"] / r2["total_s"], "ms_per_step": 1e3 * r2["total_s"] / args.steps,
+                         "leaves_per_step_avg": lv, "transport_kernel_ms": 1e3 * ksec,
+                         "transport_hbm_gbs_alg": bpl * lv / ksec / 1e9}
+            s2.close()
 
     # whole-job aggregate: updates summed over ranks, time = max over ranks
     if dist is not None:
@@ -253,20 +277,24 @@ def run_ours(args):
     # roofline of the transport + collision kernel, timed live above
     peaks, peak_kind = _peaks()
     kern_avg_s = kern_ms / 1e3 / max(kern_n, 1)
-    fp64_tflops = _fp64_peak_tflops(torch)
-    achieved_tflops = ALG_FLOPS_PER_LEAF * per_step_leaves / kern_avg_s / 1e12
-    achieved_gbs = ALG_BYTES_PER_LEAF * per_step_leaves / kern_avg_s / 1e9
-    roofline = {
-        "kernel": "k_stream_collide<3> (transport + collision)",
-        "bound": "alu", "achieved": achieved_tflops, "peak": fp64_tflops, "unit": "TFLOP/s",
-        "frac": achieved_tflops / fp64_tflops,
-        "peak_kind": "FP64 measured with cuBLAS DGEMM in this run",
-        "traffic": None,
-        "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved_gbs / peaks["hbm_gbs"], "peak_kind": peak_kind},
-        "kernel_ms_avg": 1e3 * kern_avg_s, "kernel_share_of_step": kern_ms / 1e3 / total_s,
-        "alg_flops_per_leaf": ALG_FLOPS_PER_LEAF, "alg_bytes_per_leaf": ALG_BYTES_PER_LEAF,
-    }
+    bytes_per_leaf = 2 * 16 * FORM_BYTES[args.form] + 5
+    achieved_gbs = bytes_per_leaf * per_step_leaves / kern_avg_s / 1e9
+    hbm = {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": achieved_gbs / peaks["hbm_gbs"], "peak_kind": peak_kind}
+    if args.form == "fp64":
+        fp64_tflops = _fp64_peak_tflops(torch)
+        achieved_tflops = ALG_FLOPS_PER_LEAF * per_step_leaves / kern_avg_s / 1e12
+        roofline = {
+            "kernel": "k_stream_collide<3> (transport + collision)",
+            "bound": "alu", "achieved": achieved_tflops, "peak": fp64_tflops, "unit": "TFLOP/s",
+            "frac": achieved_tflops / fp64_tflops,
+            "peak_kind": "FP64 measured with cuBLAS DGEMM in this run",
+            "traffic": None, "hbm": hbm,
+        }
+    else:
+        roofline = dict(hbm, kernel="k_stream_collide<3> (transport + collision)", bound="hbm", traffic=None)
+    roofline.update({"kernel_ms_avg": 1e3 * kern_avg_s, "kernel_share_of_step": kern_ms / 1e3 / total_s,
+                     "alg_flops_per_leaf": ALG_FLOPS_PER_LEAF, "alg_bytes_per_leaf": bytes_per_leaf})
 
     groups = None
     if args.profile_groups:
@@ -321,9 +349,10 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPE[args.form],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "scheme": "D2Q4^4 Euler", "max_level": cfg["max_level"],
+                       "form": args.form,
                        "min_level": cfg["min_level"], "eps": cfg["eps"], "mu_bar": cfg["mu_bar"],
                        "seed": args.seed, "steps_timed": "%d..%d" % (args.warmup + 1, args.warmup + args.steps),
                        "l2": "256 MiB write between timed steps, outside the step events",
@@ -335,6 +364,8 @@ def run_ours(args):
         }
         if groups is not None:
             line["kernel_groups"] = groups
+        if forms is not None:
+            line["forms"] = forms
         print(json.dumps(line), flush=True)
     solver.close()
     if dist is not None:

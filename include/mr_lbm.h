@@ -72,7 +72,15 @@ typedef enum {
   MR_BC_ANTI_BOUNCE_BACK = 3 /* Eq. refBoundaryConditions, anti bounce back */
 } mr_bc;
 
-typedef enum { MR_FP64 = 0 } mr_precision;
+/* Storage and arithmetic of the populations.  The details that decide the
+ * mesh (Def. Details, Eq. Thresholding, the refinement rule) are evaluated
+ * in FP64 in every form, on the stored values. */
+typedef enum {
+  MR_FP64 = 0,           /* plain: FP64 storage and arithmetic */
+  MR_FP32 = 1,           /* FP32 storage, FP32 transport and collision */
+  MR_FP32_FP16STORE = 2, /* FP16 storage of f - f^eq(mean initial state), FP32 arithmetic */
+  MR_FP32_BF16STORE = 3  /* BF16 storage of f - f^eq(mean initial state), FP32 arithmetic */
+} mr_precision;
 
 typedef struct {
   int scheme;            /* mr_scheme */
@@ -90,7 +98,7 @@ typedef struct {
   int bc[6];             /* mr_bc per face: -x, +x, -y, +y, -z, +z */
   int cross_sign;        /* +1: tensor-product prediction (default, also when 0);
                             -1: diagonal term with the sign printed in Sec. 4.1 */
-  int precision;         /* mr_precision; only MR_FP64 */
+  int precision;         /* mr_precision */
   long long leaf_capacity; /* maximum number of leaves; 0 = all finest cells */
 } mr_lbm_config;
 

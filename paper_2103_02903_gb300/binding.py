@@ -22,6 +22,7 @@ MR_STATUS = {0: "MR_OK", 1: "MR_EINVAL", 2: "MR_ENOMEM", 3: "MR_ECUDA", 4: "MR_E
 SCHEMES = {"d1q2_advection": 0, "d1q2_burgers": 1, "d1q3_shallow_water": 2, "d2q4x4_euler": 3,
            "d2q9_ns": 4}
 BCS = {"periodic": 0, "copy": 1, "bounce_back": 2, "anti_bounce_back": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 NCONS = {0: 1, 1: 1, 2: 2, 3: 4}
 NPOP = {0: 2, 1: 2, 2: 3, 3: 16}
 DIM = {0: 1, 1: 1, 2: 1, 3: 2}
@@ -120,7 +121,8 @@ def make_config(cfg: Dict, leaf_capacity: int = 0) -> MrConfig:
         b = cfg["bc"][f]
         c.bc[f] = BCS[b] if isinstance(b, str) else int(b)
     c.cross_sign = int(cfg.get("cross_sign", 1))
-    c.precision = 0
+    prec = cfg.get("precision", 0)
+    c.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     c.leaf_capacity = int(cfg.get("leaf_capacity", leaf_capacity))
     return c
 

@@ -153,12 +153,49 @@ void build_tables(const Geo& g, std::vector<double>& W) {
     }
 }
 
+// Equilibrium populations M^{-1} m^eq(u) of each scheme on the host (used for
+// the storage offsets of the 16-bit forms).
+void host_equilibrium(const Geo& g, const double* u, double* f) {
+  const double L = g.lambda;
+  switch (g.scheme) {
+    case MR_D1Q2_ADVECTION:
+    case MR_D1Q2_BURGERS: {
+      const double m1 = g.scheme == MR_D1Q2_ADVECTION ? g.phys[0] * u[0] : 0.5 * u[0] * u[0];
+      f[0] = 0.5 * (u[0] + m1 / L);
+      f[1] = 0.5 * (u[0] - m1 / L);
+      break;
+    }
+    case MR_D1Q3_SHALLOW_WATER: {
+      const double t = (u[1] * u[1] / u[0] + 0.5 * g.phys[0] * u[0] * u[0]) / (L * L);
+      f[0] = u[0] - t;
+      f[1] = 0.5 * (t + u[1] / L);
+      f[2] = 0.5 * (t - u[1] / L);
+      break;
+    }
+    case MR_D2Q4x4_EULER: {
+      const double rho = u[0], mx = u[1], my = u[2], E = u[3];
+      const double vx = mx / rho, vy = my / rho;
+      const double pr = (g.phys[0] - 1.0) * (E - 0.5 * (mx * vx + my * vy));
+      const double fx[4] = {mx, mx * vx + pr, my * vx, vx * (E + pr)};
+      const double fy[4] = {my, mx * vy, my * vy + pr, vy * (E + pr)};
+      for (int i = 0; i < 4; ++i) {
+        const double a = 0.25 * u[i], b = 0.5 * fx[i] / L, c = 0.5 * fy[i] / L;
+        f[4 * i + 0] = a + b;
+        f[4 * i + 1] = a + c;
+        f[4 * i + 2] = a - b;
+        f[4 * i + 3] = a - c;
+      }
+      break;
+    }
+  }
+}
+
 mr_status validate(const mr_lbm_config* c) {
   if (!c) return MR_EINVAL;
   if (c->scheme < 0 || c->scheme > MR_D2Q4x4_EULER) return MR_EINVAL;
   if (!(c->lambda > 0) || !(c->eps >= 0) || c->mu_bar < 0) return MR_EINVAL;
   if (c->pred_s != 0 && c->pred_s != 1) return MR_EINVAL;
-  if (c->precision != MR_FP64) return MR_EINVAL;
+  if (c->precision < MR_FP64 || c->precision > MR_FP32_BF16STORE) return MR_EINVAL;
   if (c->min_level < 2 || c->max_level < c->min_level || c->max_level > 15) return MR_EINVAL;
   for (int i = 0; i < 16; ++i)
     if (!(c->s[i] >= 0.0 && c->s[i] <= 2.0)) return MR_EINVAL;
@@ -450,6 +487,8 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   g.eps = cfg->eps;
   g.mu_bar = cfg->mu_bar;
   g.cross_sign = cfg->cross_sign == -1 ? -1 : 1;
+  g.form = cfg->precision;  // MR_FP64 .. MR_FP32_BF16STORE map onto MR_FORM_F64 .. MR_FORM_F32_BF16
+  for (int p = 0; p < MR_MAXQ; ++p) g.off[p] = 0.0;
   long long nJ = g.ncode[g.J], nint = 0, nall = 0;
   for (int l = g.Jmin; l <= g.J; ++l) {
     nall += g.ncode[l];
@@ -470,16 +509,21 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   if (h->nsm <= 0) h->nsm = 152;
 
   const size_t dense = g.base[g.J + 1];
+  const size_t eb = mr_form_bytes(g.form);  // bytes per stored population value
+  char *fs = nullptr, *fsc = nullptr;
   bool ok = dalloc(h, &h->cntbuf, 2) && dalloc(h, &h->flags, dense) && dalloc(h, &h->cls, dense) &&
             dalloc(h, &h->bcounts, 3 * (dense / MR_DENSE_ALIGN + 1)) && dalloc(h, &h->inidx, dense) &&
-            dalloc(h, &h->vol, 1) && dalloc(h, &h->fstate, (size_t)g.Q * g.cap[0]) &&
-            dalloc(h, &h->fscratch, (size_t)g.Q * g.cap[0]);
+            dalloc(h, &h->vol, 1) && dalloc(h, &fs, eb * g.Q * g.cap[0]) && dalloc(h, &fsc, eb * g.Q * g.cap[0]);
+  h->fstate = fs;
+  h->fscratch = fsc;
   for (int mi = 0; mi < 2 && ok; ++mi) {
     MeshDev& M = h->mesh[mi];
     for (int c = 0; c < 3 && ok; ++c) ok = dalloc(h, &M.code[c], g.cap[c]) && dalloc(h, &M.lvl[c], g.cap[c]);
-    ok = ok && dalloc(h, &M.map, dense) && dalloc(h, &M.IF, (size_t)g.Q * g.cap[1]) &&
-         dalloc(h, &M.GF, (size_t)g.Q * g.cap[2]) && dalloc(h, &M.G, g.cap[1]) &&
-         dalloc(h, &M.src, g.cap[0]);
+    char *ifp = nullptr, *gfp = nullptr;
+    ok = ok && dalloc(h, &M.map, dense) && dalloc(h, &ifp, eb * g.Q * g.cap[1]) &&
+         dalloc(h, &gfp, eb * g.Q * g.cap[2]) && dalloc(h, &M.G, g.cap[1]) && dalloc(h, &M.src, g.cap[0]);
+    M.IF = ifp;
+    M.GF = gfp;
     if (ok) M.cnt = h->cntbuf + mi;
   }
   std::vector<double> W;
@@ -526,6 +570,26 @@ mr_status mr_lbm_init(mr_lbm_t h, const double* conserved, int on_device) {
   const Geo& g = h->g;
   const size_t bytes = (size_t)g.ncons * g.ncode[g.J] * sizeof(double);
   const double* src = conserved;
+  if (g.form == MR_FORM_F32_F16 || g.form == MR_FORM_F32_BF16) {
+    // 16-bit storage keeps populations as offsets from the equilibrium of
+    // the mean initial state
+    std::vector<double> hc;
+    const double* cp = conserved;
+    if (on_device) {
+      hc.resize(bytes / sizeof(double));
+      if (!cuda_ok(h, cudaMemcpy(hc.data(), conserved, bytes, cudaMemcpyDeviceToHost))) return MR_ECUDA;
+      cp = hc.data();
+    }
+    const long long N = g.ncode[g.J];
+    double u[4] = {0, 0, 0, 0};
+    for (int k = 0; k < g.ncons; ++k) {
+      double s = 0;
+      for (long long c = 0; c < N; ++c) s += cp[k * N + c];
+      u[k] = s / (double)N;
+    }
+    host_equilibrium(h->g, u, h->g.off);
+    drop_graphs(h);
+  }
   if (!on_device) {
     if (ensure_staging(h, bytes) != MR_OK) return h->sticky;
     if (!cuda_ok(h, cudaMemcpyAsync(h->staging, conserved, bytes, cudaMemcpyHostToDevice, h->st)))
@@ -648,6 +712,23 @@ mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* k
   if (h->sticky != MR_OK) return h->sticky;
   const Geo& g = h->g;
   if (n > g.cap[0]) return fail(h, MR_ECAPACITY);
+  if (!h->initialized && (g.form == MR_FORM_F32_F16 || g.form == MR_FORM_F32_BF16)) {
+    // first state of the handle: 16-bit storage offsets = mean populations
+    std::vector<double> hf;
+    const double* fp = f;
+    if (on_device) {
+      hf.resize((size_t)g.Q * n);
+      if (!cuda_ok(h, cudaMemcpy(hf.data(), f, hf.size() * sizeof(double), cudaMemcpyDeviceToHost)))
+        return MR_ECUDA;
+      fp = hf.data();
+    }
+    for (int p = 0; p < g.Q; ++p) {
+      double s = 0;
+      for (long long i = 0; i < n; ++i) s += fp[(size_t)p * n + i];
+      h->g.off[p] = s / (double)n;
+    }
+    drop_graphs(h);
+  }
   const unsigned long long* dk = keys;
   const signed char* dl = levels;
   const double* df = f;

@@ -3,33 +3,100 @@
 // operator of Sec. 4.1 (s = 1).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "mr_internal.cuh"
 
 #define MR_C1 (-0.125)  // Table 1, s = 1
 
+// ------------------------------------------------------------------ forms
+// S: storage type of the populations, C: arithmetic of transport and
+// collision, offs: stored value = population - g.off[p].
+template <int F>
+struct FormT;
+template <>
+struct FormT<MR_FORM_F64> {
+  using S = double;
+  using C = double;
+  static constexpr bool offs = false;
+};
+template <>
+struct FormT<MR_FORM_F32> {
+  using S = float;
+  using C = float;
+  static constexpr bool offs = false;
+};
+template <>
+struct FormT<MR_FORM_F32_F16> {
+  using S = __half;
+  using C = float;
+  static constexpr bool offs = true;
+};
+template <>
+struct FormT<MR_FORM_F32_BF16> {
+  using S = __nv_bfloat16;
+  using C = float;
+  static constexpr bool offs = true;
+};
+
+__device__ __forceinline__ double mr_cvt_d(double v) { return v; }
+__device__ __forceinline__ double mr_cvt_d(float v) { return (double)v; }
+__device__ __forceinline__ double mr_cvt_d(__half v) { return (double)__half2float(v); }
+__device__ __forceinline__ double mr_cvt_d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+template <class S>
+__device__ __forceinline__ S mr_from_d(double v);
+template <>
+__device__ __forceinline__ double mr_from_d<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float mr_from_d<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ __half mr_from_d<__half>(double v) { return __double2half(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 mr_from_d<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+template <class S>
+__device__ __forceinline__ S mr_from_f(float v);
+template <>
+__device__ __forceinline__ double mr_from_f<double>(float v) { return (double)v; }
+template <>
+__device__ __forceinline__ float mr_from_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half mr_from_f<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 mr_from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// A cell's population array: element p is at p[p * stride].
+template <class S = double>
 struct ValPtr {
-  const double* p;
+  const S* p;
   int stride;
 };
 
-__device__ __forceinline__ ValPtr mr_resolve(const Geo& g, const MeshDev& M, const double* LF, int32_t e) {
+template <class S = double>
+__device__ __forceinline__ ValPtr<S> mr_resolve(const Geo& g, const MeshDev& M, const void* LF, int32_t e) {
   uint32_t cls = ((uint32_t)e) >> 30;
   uint32_t idx = (uint32_t)e & 0x3FFFFFFFu;
-  ValPtr r;
+  ValPtr<S> r;
   if (cls == MR_CLS_LEAF) {
-    r.p = LF + idx;
+    r.p = (const S*)LF + idx;
     r.stride = g.cap[0];
   } else if (cls == MR_CLS_INT) {
-    r.p = M.IF + idx;
+    r.p = (const S*)M.IF + idx;
     r.stride = g.cap[1];
   } else {
-    r.p = M.GF + idx;
+    r.p = (const S*)M.GF + idx;
     r.stride = g.cap[2];
   }
   return r;
 }
 
-__device__ __forceinline__ double mr_ld(const ValPtr& v, int p) { return __ldg(v.p + (size_t)p * v.stride); }
+// stored value of population p as double (no offset added)
+template <class S>
+__device__ __forceinline__ double mr_ld(const ValPtr<S>& v, int p) {
+  return mr_cvt_d(__ldg(v.p + (size_t)p * v.stride));
+}
 
 __device__ __forceinline__ uint32_t mr_atomic_or_byte(uint8_t* base, uint32_t idx, uint32_t bits) {
   uint32_t* w = (uint32_t*)(base + (idx & ~3u));

@@ -4,10 +4,12 @@
 // reduced to one max-norm per sibling group and over all populations
 // (Def. Details and the group norm of Sec. 4.4).
 //
-// Both kernels evaluate their arithmetic in a fixed order with
+// Both kernels evaluate their arithmetic in FP64, in a fixed order with
 // __dadd_rn/__dmul_rn (never contracted into FMA), so that the details, and
 // hence every keep / refine decision, carry the same bits as the CPU oracle
-// on the same leaf values.
+// on the same stored values, whatever the storage type of the form.  Both
+// act on stored values directly: the projection and the details are linear
+// and exact on constants, so the offset of the 16-bit forms cancels.
 #include "mr_common.cuh"
 
 namespace {
@@ -21,21 +23,22 @@ struct PopRows {
   static constexpr int value = Q < 8 ? Q : 8;
 };
 
-template <int D, int Q>
-__global__ void __launch_bounds__(256) k_project(Geo g, MeshDev A, const double* __restrict__ LF,
-                                                 int level) {
+template <int D, int Q, int F>
+__global__ void __launch_bounds__(256) k_project(Geo g, MeshDev A, const void* __restrict__ LF, int level) {
+  using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   const int begin = A.cnt->off[MR_CLS_INT][level], end = A.cnt->off[MR_CLS_INT][level + 1];
   const double scale = D == 1 ? 0.5 : 0.25;
+  S* IF = (S*)A.IF;
   for (int i = begin + blockIdx.x * 32 + threadIdx.x; i < end; i += gridDim.x * 32) {
     const uint32_t code = A.code[MR_CLS_INT][i];
-    ValPtr ch[1 << D];
+    ValPtr<S> ch[1 << D];
     bool ok = true;
 #pragma unroll
     for (int ci = 0; ci < (1 << D); ++ci) {
       int32_t e = A.map[g.base[level + 1] + ((code << D) | (uint32_t)ci)];
       ok = ok && e != MR_MAP_NONE && (((uint32_t)e) >> 30) <= MR_CLS_INT;
-      ch[ci] = mr_resolve(g, A, LF, e);
+      ch[ci] = mr_resolve<S>(g, A, LF, e);
     }
     if (!ok) {
       if (threadIdx.y == 0) mr_set_err(A.cnt, MR_DERR_INTERNAL);
@@ -46,13 +49,14 @@ __global__ void __launch_bounds__(256) k_project(Geo g, MeshDev A, const double*
       double acc = 0.0;
 #pragma unroll
       for (int ci = 0; ci < (1 << D); ++ci) acc = __dadd_rn(acc, mr_ld(ch[ci], p));
-      A.IF[(size_t)p * g.cap[1] + i] = __dmul_rn(acc, scale);
+      IF[(size_t)p * g.cap[1] + i] = mr_from_d<S>(__dmul_rn(acc, scale));
     }
   }
 }
 
-template <int D, int Q>
-__global__ void __launch_bounds__(256) k_details(Geo g, MeshDev A, const double* __restrict__ LF) {
+template <int D, int Q, int F>
+__global__ void __launch_bounds__(256) k_details(Geo g, MeshDev A, const void* __restrict__ LF) {
+  using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   __shared__ double red[PY][32];
   const int n = A.cnt->total[MR_CLS_INT];
@@ -66,17 +70,17 @@ __global__ void __launch_bounds__(256) k_details(Geo g, MeshDev A, const double*
       mr_decode(g, L, code, x, y);
       int32_t st[9];
       bool ok = mr_stencil_entries<D>(g, A, L, x, y, st);
-      ValPtr sv[D == 2 ? 9 : 3], cv[1 << D];
+      ValPtr<S> sv[D == 2 ? 9 : 3], cv[1 << D];
 #pragma unroll
       for (int k = 0; k < (D == 2 ? 9 : 3); ++k) {
         ok = ok && (((uint32_t)st[k]) >> 30) <= MR_CLS_INT;
-        sv[k] = mr_resolve(g, A, LF, st[k]);
+        sv[k] = mr_resolve<S>(g, A, LF, st[k]);
       }
 #pragma unroll
       for (int ci = 0; ci < (1 << D); ++ci) {
         int32_t e = A.map[g.base[L + 1] + ((code << D) | (uint32_t)ci)];
         ok = ok && e != MR_MAP_NONE && (((uint32_t)e) >> 30) <= MR_CLS_INT;
-        cv[ci] = mr_resolve(g, A, LF, e);
+        cv[ci] = mr_resolve<S>(g, A, LF, e);
       }
       if (!ok) {
         if (threadIdx.y == 0) mr_set_err(A.cnt, MR_DERR_INTERNAL);
@@ -109,33 +113,38 @@ __global__ void __launch_bounds__(256) k_details(Geo g, MeshDev A, const double*
 }
 
 // `grid` is the maximum number of blocks; a block covers 32 cells.
-template <int D, int Q>
-void launch_project_t(const Geo& g, const MeshDev& A, const double* LF, int level, cudaStream_t st,
-                      int grid) {
+template <int D, int Q, int F>
+void launch_project_t(const Geo& g, const MeshDev& A, const void* LF, int level, cudaStream_t st, int grid) {
   const int need = (int)((g.ncode[level] + 31) / 32);
-  k_project<D, Q><<<need < grid ? need : grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LF, level);
+  k_project<D, Q, F><<<need < grid ? need : grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LF, level);
 }
-template <int D, int Q>
-void launch_details_t(const Geo& g, const MeshDev& A, const double* LF, cudaStream_t st, int grid) {
-  k_details<D, Q><<<grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LF);
+template <int D, int Q, int F>
+void launch_details_t(const Geo& g, const MeshDev& A, const void* LF, cudaStream_t st, int grid) {
+  k_details<D, Q, F><<<grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LF);
 }
 
 }  // namespace
 
-#define MR_DISPATCH_DQ(FN, ...)                                  \
-  switch (g.d * 100 + g.Q) {                                     \
-    case 102: FN<1, 2>(__VA_ARGS__); break;                      \
-    case 103: FN<1, 3>(__VA_ARGS__); break;                      \
-    case 216: FN<2, 16>(__VA_ARGS__); break;                     \
-    case 209: FN<2, 9>(__VA_ARGS__); break;                      \
-    default: break;                                              \
+#define MR_DISPATCH_F(FN, D, Q, ...)                       \
+  switch (g.form) {                                        \
+    case MR_FORM_F64: FN<D, Q, MR_FORM_F64>(__VA_ARGS__); break;       \
+    case MR_FORM_F32: FN<D, Q, MR_FORM_F32>(__VA_ARGS__); break;       \
+    case MR_FORM_F32_F16: FN<D, Q, MR_FORM_F32_F16>(__VA_ARGS__); break; \
+    case MR_FORM_F32_BF16: FN<D, Q, MR_FORM_F32_BF16>(__VA_ARGS__); break; \
   }
 
-void mr_launch_project(const Geo& g, const MeshDev& A, const double* LF, int level, cudaStream_t st,
-                       int grid) {
-  MR_DISPATCH_DQ(launch_project_t, g, A, LF, level, st, grid);
+#define MR_DISPATCH_DQF(FN, ...)                                  \
+  switch (g.d * 100 + g.Q) {                                      \
+    case 102: MR_DISPATCH_F(FN, 1, 2, __VA_ARGS__); break;        \
+    case 103: MR_DISPATCH_F(FN, 1, 3, __VA_ARGS__); break;        \
+    case 216: MR_DISPATCH_F(FN, 2, 16, __VA_ARGS__); break;       \
+    default: break;                                               \
+  }
+
+void mr_launch_project(const Geo& g, const MeshDev& A, const void* LF, int level, cudaStream_t st, int grid) {
+  MR_DISPATCH_DQF(launch_project_t, g, A, LF, level, st, grid);
 }
 
-void mr_launch_details(const Geo& g, const MeshDev& A, const double* LF, cudaStream_t st, int grid) {
-  MR_DISPATCH_DQ(launch_details_t, g, A, LF, st, grid);
+void mr_launch_details(const Geo& g, const MeshDev& A, const void* LF, cudaStream_t st, int grid) {
+  MR_DISPATCH_DQF(launch_details_t, g, A, LF, st, grid);
 }

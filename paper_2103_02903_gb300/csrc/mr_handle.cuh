@@ -16,8 +16,8 @@ struct mr_lbm {
   MeshDev mesh[2];
   MeshCounts* cntbuf = nullptr;  // two MeshCounts
   int cur = 0;
-  double* fstate = nullptr;
-  double* fscratch = nullptr;
+  void* fstate = nullptr;    // leaf populations [Q][cap_leaf], storage type of the form
+  void* fscratch = nullptr;  // pre-transport leaf populations, same layout
   uint8_t* flags = nullptr;
   uint8_t* cls = nullptr;
   int* bcounts = nullptr;

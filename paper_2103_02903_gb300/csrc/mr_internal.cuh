@@ -58,7 +58,16 @@ struct Geo {
   int opp[9];
   int cap[3];                  // capacities: leaf, internal, ghost
   double consw[4][MR_MAXQ];    // conserved moments as linear forms of the populations
+  int form;                    // storage / compute form, see MR_FORM_*
+  double off[MR_MAXQ];         // stored value = population - off[p] (0 unless 16-bit storage)
 };
+
+// Storage / compute forms: populations are stored as S and transported and
+// collided in C; details (the mesh decisions) are always evaluated in FP64.
+#define MR_FORM_F64 0        // S = double, C = double (plain)
+#define MR_FORM_F32 1        // S = float,  C = float
+#define MR_FORM_F32_F16 2    // S = half (offset from the rest equilibrium), C = float
+#define MR_FORM_F32_BF16 3   // S = bfloat16 (offset from the rest equilibrium), C = float
 
 // counters of one mesh, in device memory
 struct MeshCounts {
@@ -74,8 +83,8 @@ struct MeshDev {
   uint32_t* code[3];   // Morton code (with root prefix) at own level
   uint8_t* lvl[3];
   int32_t* map;        // dense index map: (cls << 30) | idx, or -1
-  double* IF;          // internal-cell values [Q][cap_int]
-  double* GF;          // ghost values [Q][cap_ghost]
+  void* IF;            // internal-cell values [Q][cap_int], storage type of the form
+  void* GF;            // ghost values [Q][cap_ghost], storage type of the form
   double* G;           // group norm per internal cell
   int32_t* src;        // per leaf: source entry in the previous mesh, -1 if predicted
   MeshCounts* cnt;
@@ -161,9 +170,11 @@ __host__ __device__ inline int mr_slot(int k, int N, int periodic) {
 // kernels (defined in mr_encode.cu, mr_mesh.cu, mr_stream.cu)
 // ------------------------------------------------------------------------
 
-void mr_launch_project(const Geo& g, const MeshDev& A, const double* LF, int level, cudaStream_t st,
+// Leaf-value arrays (LF) are passed as void*: their element type is the
+// storage type of g.form.
+void mr_launch_project(const Geo& g, const MeshDev& A, const void* LF, int level, cudaStream_t st,
                        int grid);
-void mr_launch_details(const Geo& g, const MeshDev& A, const double* LF, cudaStream_t st, int grid);
+void mr_launch_details(const Geo& g, const MeshDev& A, const void* LF, cudaStream_t st, int grid);
 void mr_launch_flags_T(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid);
 void mr_launch_flags_H(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid);
 void mr_launch_grade(const Geo& g, uint8_t* flags, MeshCounts* errc, cudaStream_t st, int grid);
@@ -171,14 +182,14 @@ void mr_launch_classify(const Geo& g, const uint8_t* flags, uint8_t* cls, cudaSt
 void mr_launch_mark_ghosts(const Geo& g, uint8_t* cls, cudaStream_t st, int grid);
 void mr_launch_compact(const Geo& g, uint8_t* cls, uint8_t* flags, int* block_counts, MeshDev& B,
                        cudaStream_t st);
-void mr_launch_remesh_copy(const Geo& g, const MeshDev& A, const double* LF_old, const MeshDev& B,
-                           double* LF_new, cudaStream_t st, int grid);
-void mr_launch_predict_level(const Geo& g, const MeshDev& B, double* LF, int level, cudaStream_t st,
+void mr_launch_remesh_copy(const Geo& g, const MeshDev& A, const void* LF_old, const MeshDev& B,
+                           void* LF_new, cudaStream_t st, int grid);
+void mr_launch_predict_level(const Geo& g, const MeshDev& B, void* LF, int level, cudaStream_t st,
                              int grid);
-void mr_launch_stream_collide(const Geo& g, const MeshDev& B, const double* LF_in, double* LF_out,
+void mr_launch_stream_collide(const Geo& g, const MeshDev& B, const void* LF_in, void* LF_out,
                               const double* W, int do_stream, int do_collide, cudaStream_t st,
                               int grid);
-void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, double* LF,
+void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, void* LF,
                        cudaStream_t st, int grid);
 void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int grid);
 void mr_launch_leaves_in(const Geo& g, long long n, const unsigned long long* keys,
@@ -186,10 +197,11 @@ void mr_launch_leaves_in(const Geo& g, long long n, const unsigned long long* ke
                          unsigned long long* vol, cudaStream_t st, int grid);
 void mr_launch_leaves_check(const Geo& g, uint8_t* cls, MeshCounts* cnt, cudaStream_t st, int grid);
 void mr_launch_gather_input(const Geo& g, const MeshDev& B, const int32_t* inidx, long long n,
-                            const double* fin, double* LF, cudaStream_t st, int grid);
-void mr_launch_leaves_out(const Geo& g, const MeshDev& B, const double* LF, long long n,
+                            const double* fin, void* LF, cudaStream_t st, int grid);
+void mr_launch_leaves_out(const Geo& g, const MeshDev& B, const void* LF, long long n,
                           unsigned long long* keys, signed char* levels, double* f,
                           cudaStream_t st, int grid);
-void mr_launch_project_dense(const Geo& g, const MeshDev& B, const double* LF, int level,
+void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int level,
                              const double* prev, double* cur, cudaStream_t st, int grid);
+size_t mr_form_bytes(int form);  // bytes per stored population value
 void mr_launch_count_updates(MeshCounts* cnt, cudaStream_t st);

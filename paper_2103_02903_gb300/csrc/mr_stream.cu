@@ -14,6 +14,12 @@
 // leaves, or predicted ghosts).  Where a neighbour k-1 or k+1 is refined,
 // the details of its children (the critical case of Sec. 6.1) are added
 // through the level-(j+1) weights; grading makes deeper corrections vanish.
+//
+// Every kernel is instantiated per storage / compute form (FormT): values
+// are stored as FormT::S and transported / collided in FormT::C.  The
+// transfer and the ghost prediction are linear and exact on constants and
+// act on stored values; transport, collision and input / output add the
+// offset of the 16-bit forms back.
 #include "mr_common.cuh"
 
 namespace {
@@ -29,17 +35,19 @@ struct Scheme<0> {
   __device__ static int axis(int p) { return 0; }
   __device__ static int sign(int p) { return p == 0 ? 1 : -1; }
   __device__ static int opp(int p) { return 1 - p; }
-  __device__ static double meq1(const Geo& g, double m0) { return g.phys[0] * m0; }
-  __device__ static void collide(const Geo& g, double* f) {
-    const double L = g.lambda, s = g.s[0];
-    const double m0 = f[0] + f[1];
-    double m1 = L * (f[0] - f[1]);
-    m1 = (1.0 - s) * m1 + s * meq1(g, m0);
-    f[0] = 0.5 * (m0 + m1 / L);
-    f[1] = 0.5 * (m0 - m1 / L);
+  template <class C>
+  __device__ static C meq1(const Geo& g, C m0) { return (C)g.phys[0] * m0; }
+  template <class C>
+  __device__ static void collide(const Geo& g, C* f) {
+    const C L = (C)g.lambda, s = (C)g.s[0];
+    const C m0 = f[0] + f[1];
+    C m1 = L * (f[0] - f[1]);
+    m1 = ((C)1 - s) * m1 + s * meq1<C>(g, m0);
+    f[0] = (C)0.5 * (m0 + m1 / L);
+    f[1] = (C)0.5 * (m0 - m1 / L);
   }
   __device__ static void equilibrium(const Geo& g, const double* u, double* f) {
-    const double m1 = meq1(g, u[0]);
+    const double m1 = meq1<double>(g, u[0]);
     f[0] = 0.5 * (u[0] + m1 / g.lambda);
     f[1] = 0.5 * (u[0] - m1 / g.lambda);
   }
@@ -48,17 +56,19 @@ struct Scheme<0> {
 // D1Q2 Burgers: m^eq_1 = u^2 / 2
 template <>
 struct Scheme<1> : Scheme<0> {
-  __device__ static double meq1(const Geo&, double m0) { return 0.5 * m0 * m0; }
-  __device__ static void collide(const Geo& g, double* f) {
-    const double L = g.lambda, s = g.s[0];
-    const double m0 = f[0] + f[1];
-    double m1 = L * (f[0] - f[1]);
-    m1 = (1.0 - s) * m1 + s * meq1(g, m0);
-    f[0] = 0.5 * (m0 + m1 / L);
-    f[1] = 0.5 * (m0 - m1 / L);
+  template <class C>
+  __device__ static C meq1(const Geo&, C m0) { return (C)0.5 * m0 * m0; }
+  template <class C>
+  __device__ static void collide(const Geo& g, C* f) {
+    const C L = (C)g.lambda, s = (C)g.s[0];
+    const C m0 = f[0] + f[1];
+    C m1 = L * (f[0] - f[1]);
+    m1 = ((C)1 - s) * m1 + s * meq1<C>(g, m0);
+    f[0] = (C)0.5 * (m0 + m1 / L);
+    f[1] = (C)0.5 * (m0 - m1 / L);
   }
   __device__ static void equilibrium(const Geo& g, const double* u, double* f) {
-    const double m1 = meq1(g, u[0]);
+    const double m1 = meq1<double>(g, u[0]);
     f[0] = 0.5 * (u[0] + m1 / g.lambda);
     f[1] = 0.5 * (u[0] - m1 / g.lambda);
   }
@@ -71,16 +81,17 @@ struct Scheme<2> {
   __device__ static int axis(int p) { return p == 0 ? -1 : 0; }
   __device__ static int sign(int p) { return p == 1 ? 1 : -1; }
   __device__ static int opp(int p) { return p == 0 ? 0 : 3 - p; }
-  __device__ static void collide(const Geo& g, double* f) {
-    const double L = g.lambda, s = g.s[0], gr = g.phys[0];
-    const double m0 = f[0] + f[1] + f[2];
-    const double m1 = L * (f[1] - f[2]);
-    double m2 = L * L * (f[1] + f[2]);
-    m2 = (1.0 - s) * m2 + s * (m1 * m1 / m0 + 0.5 * gr * m0 * m0);
-    const double t = m2 / (L * L);
+  template <class C>
+  __device__ static void collide(const Geo& g, C* f) {
+    const C L = (C)g.lambda, s = (C)g.s[0], gr = (C)g.phys[0];
+    const C m0 = f[0] + f[1] + f[2];
+    const C m1 = L * (f[1] - f[2]);
+    C m2 = L * L * (f[1] + f[2]);
+    m2 = ((C)1 - s) * m2 + s * (m1 * m1 / m0 + (C)0.5 * gr * m0 * m0);
+    const C t = m2 / (L * L);
     f[0] = m0 - t;
-    f[1] = 0.5 * (t + m1 / L);
-    f[2] = 0.5 * (t - m1 / L);
+    f[1] = (C)0.5 * (t + m1 / L);
+    f[2] = (C)0.5 * (t - m1 / L);
   }
   __device__ static void equilibrium(const Geo& g, const double* u, double* f) {
     const double L = g.lambda;
@@ -98,72 +109,110 @@ struct Scheme<3> {
   __device__ static int axis(int p) { return (p & 3) & 1; }
   __device__ static int sign(int p) { return (p & 3) < 2 ? 1 : -1; }
   __device__ static int opp(int p) { return (p & ~3) | ((p + 2) & 3); }
-  __device__ static void fluxes(const Geo& g, const double* u, double* fx, double* fy) {
-    const double rho = u[0], mx = u[1], my = u[2], E = u[3], gam = g.phys[0];
-    const double irho = 1.0 / rho;  // one FP64 division per cell
-    const double vx = mx * irho, vy = my * irho;
-    const double pr = (gam - 1.0) * (E - 0.5 * (mx * vx + my * vy));
+  template <class C>
+  __device__ static void fluxes(const Geo& g, const C* u, C* fx, C* fy) {
+    const C rho = u[0], mx = u[1], my = u[2], E = u[3], gam = (C)g.phys[0];
+    const C irho = (C)1 / rho;  // one division per cell
+    const C vx = mx * irho, vy = my * irho;
+    const C pr = (gam - (C)1) * (E - (C)0.5 * (mx * vx + my * vy));
     fx[0] = mx; fx[1] = mx * vx + pr; fx[2] = my * vx; fx[3] = vx * (E + pr);
     fy[0] = my; fy[1] = mx * vy; fy[2] = my * vy + pr; fy[3] = vy * (E + pr);
   }
-  __device__ static void from_moments(const Geo& g, double m0, double m1, double m2, double m3, double* f) {
-    const double il = g.inv_lambda, il2 = il * il;
-    const double a = 0.25 * m0, b = 0.5 * m1 * il, c = 0.5 * m2 * il, e = 0.25 * m3 * il2;
+  template <class C>
+  __device__ static void from_moments(const Geo& g, C m0, C m1, C m2, C m3, C* f) {
+    const C il = (C)g.inv_lambda, il2 = il * il;
+    const C a = (C)0.25 * m0, b = (C)0.5 * m1 * il, c = (C)0.5 * m2 * il, e = (C)0.25 * m3 * il2;
     f[0] = a + b + e;
     f[1] = a + c - e;
     f[2] = a - b + e;
     f[3] = a - c - e;
   }
-  __device__ static void collide(const Geo& g, double* f) {
-    const double L = g.lambda;
-    double m[4][4], u[4], fx[4], fy[4];
+  template <class C>
+  __device__ static void collide(const Geo& g, C* f) {
+    const C L = (C)g.lambda;
+    C m[4][4], u[4], fx[4], fy[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const double* fi = f + 4 * i;
+      const C* fi = f + 4 * i;
       m[i][0] = fi[0] + fi[1] + fi[2] + fi[3];
       m[i][1] = L * (fi[0] - fi[2]);
       m[i][2] = L * (fi[1] - fi[3]);
       m[i][3] = L * L * (fi[0] - fi[1] + fi[2] - fi[3]);
       u[i] = m[i][0];
     }
-    fluxes(g, u, fx, fy);
+    fluxes<C>(g, u, fx, fy);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const double sq = g.s[i], sxy = g.s[4 + i];
-      const double m1 = (1.0 - sq) * m[i][1] + sq * fx[i];
-      const double m2 = (1.0 - sq) * m[i][2] + sq * fy[i];
-      const double m3 = (1.0 - sxy) * m[i][3];
-      from_moments(g, m[i][0], m1, m2, m3, f + 4 * i);
+      const C sq = (C)g.s[i], sxy = (C)g.s[4 + i];
+      const C m1 = ((C)1 - sq) * m[i][1] + sq * fx[i];
+      const C m2 = ((C)1 - sq) * m[i][2] + sq * fy[i];
+      const C m3 = ((C)1 - sxy) * m[i][3];
+      from_moments<C>(g, m[i][0], m1, m2, m3, f + 4 * i);
     }
   }
   __device__ static void equilibrium(const Geo& g, const double* u, double* f) {
     double fx[4], fy[4];
-    fluxes(g, u, fx, fy);
+    fluxes<double>(g, u, fx, fy);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) from_moments(g, u[i], fx[i], fy[i], 0.0, f + 4 * i);
+    for (int i = 0; i < 4; ++i) from_moments<double>(g, u[i], fx[i], fy[i], 0.0, f + 4 * i);
   }
 };
 
-__device__ __forceinline__ double bc_value(int kind, const double* f, int p, int pd) {
+template <class C>
+__device__ __forceinline__ C bc_value(int kind, const C* f, int p, int pd) {
   switch (kind) {
-    case 1: return f[p];     // copy
-    case 2: return f[pd];    // bounce back
-    case 3: return -f[pd];   // anti bounce back
-    default: return 0.0;
+    case 1: return f[p];    // copy
+    case 2: return f[pd];   // bounce back
+    case 3: return -f[pd];  // anti bounce back
+    default: return (C)0;
   }
 }
 
-// ------------------------------------------------------------------ transfer
-// Thread layout of the transfer kernels: 32 cells (threadIdx.x) by up to 8
-// populations (threadIdx.y), one population per warp.
+// s = 1 prediction in arithmetic C (contraction allowed; off the decision path)
+template <int D, class C>
+__device__ __forceinline__ C predict_c(const C* v, int ci, C cross_sign) {
+  const C sx = (ci & 1) ? (C)-1 : (C)1;
+  const C c1 = (C)MR_C1;
+  if (D == 1) {
+    return v[1] + sx * (c1 * (v[2] - v[0]));
+  } else {
+    const C sy = (ci & 2) ? (C)-1 : (C)1;
+    const C qx = c1 * (v[5] - v[3]);
+    const C qy = c1 * (v[7] - v[1]);
+    const C q2 = (c1 * c1) * (((v[8] - v[6]) - v[2]) + v[0]);
+    return v[4] + sx * qx + sy * qy + (cross_sign * sx * sy) * q2;
+  }
+}
+
+template <class C, class S>
+__device__ __forceinline__ C ld_c(const ValPtr<S>& v, int p) {
+  return (C)mr_cvt_d(__ldg(v.p + (size_t)p * v.stride));
+}
+template <>
+__device__ __forceinline__ float ld_c<float, float>(const ValPtr<float>& v, int p) {
+  return __ldg(v.p + (size_t)p * v.stride);
+}
+template <>
+__device__ __forceinline__ float ld_c<float, __half>(const ValPtr<__half>& v, int p) {
+  return __half2float(__ldg(v.p + (size_t)p * v.stride));
+}
+template <>
+__device__ __forceinline__ float ld_c<float, __nv_bfloat16>(const ValPtr<__nv_bfloat16>& v, int p) {
+  return __bfloat162float(__ldg(v.p + (size_t)p * v.stride));
+}
+
 template <int Q>
 struct PopRows {
   static constexpr int value = Q < 8 ? Q : 8;
 };
 
-template <int Q>
-__global__ void __launch_bounds__(256) k_remesh_copy(Geo g, MeshDev A, const double* __restrict__ LFold,
-                                                     MeshDev B, double* LFnew) {
+// ------------------------------------------------------------------ transfer
+// Thread layout of the transfer kernels: 32 cells (threadIdx.x) by up to 8
+// populations (threadIdx.y), one population per warp.
+template <int Q, int F>
+__global__ void __launch_bounds__(256) k_remesh_copy(Geo g, MeshDev A, const void* __restrict__ LFold, MeshDev B,
+                                                     void* LFnew) {
+  using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   const int nL = B.cnt->total[MR_CLS_LEAF], nI = B.cnt->total[MR_CLS_INT];
   for (int t = blockIdx.x * 32 + threadIdx.x; t < nL + nI; t += gridDim.x * 32) {
@@ -173,11 +222,11 @@ __global__ void __launch_bounds__(256) k_remesh_copy(Geo g, MeshDev A, const dou
     const int l = B.lvl[k][i];
     const int32_t e = A.map[g.base[l] + B.code[k][i]];
     if (e != MR_MAP_NONE && (((uint32_t)e) >> 30) <= MR_CLS_INT) {
-      const ValPtr s = mr_resolve(g, A, LFold, e);
-      double* dst = leaf ? LFnew + i : B.IF + i;
+      const ValPtr<S> s = mr_resolve<S>(g, A, LFold, e);
+      S* dst = leaf ? (S*)LFnew + i : (S*)B.IF + i;
       const size_t ds = leaf ? g.cap[0] : g.cap[1];
 #pragma unroll
-      for (int p = threadIdx.y; p < Q; p += PY) dst[(size_t)p * ds] = mr_ld(s, p);
+      for (int p = threadIdx.y; p < Q; p += PY) dst[(size_t)p * ds] = __ldg(s.p + (size_t)p * s.stride);
       if (leaf && threadIdx.y == 0) B.src[i] = e;
     } else if (threadIdx.y == 0) {
       if (leaf)
@@ -190,27 +239,29 @@ __global__ void __launch_bounds__(256) k_remesh_copy(Geo g, MeshDev A, const dou
 
 // Ghosts and newly created leaves of one level: the prediction operator
 // applied to level-1 values of the new mesh (all present by construction).
-template <int D, int Q>
-__global__ void __launch_bounds__(256) k_predict_level(Geo g, MeshDev B, double* LF, int level) {
+template <int D, int Q, int F>
+__global__ void __launch_bounds__(256) k_predict_level(Geo g, MeshDev B, void* LF, int level) {
+  using S = typename FormT<F>::S;
+  using C = typename FormT<F>::C;
   constexpr int PY = PopRows<Q>::value;
   const int gb = B.cnt->off[MR_CLS_GHOST][level], ge = B.cnt->off[MR_CLS_GHOST][level + 1];
   const int lb = B.cnt->off[MR_CLS_LEAF][level], le = B.cnt->off[MR_CLS_LEAF][level + 1];
   const int ng = ge - gb, total = ng + (le - lb);
-  const double cs = (double)g.cross_sign;
+  const C cs = (C)g.cross_sign;
   for (int t = blockIdx.x * 32 + threadIdx.x; t < total; t += gridDim.x * 32) {
     uint32_t code;
-    double* out;
+    S* out;
     size_t ostride;
     if (t < ng) {
       const int i = gb + t;
       code = B.code[MR_CLS_GHOST][i];
-      out = B.GF + i;
+      out = (S*)B.GF + i;
       ostride = g.cap[2];
     } else {
       const int i = lb + (t - ng);
       if (B.src[i] >= 0) continue;
       code = B.code[MR_CLS_LEAF][i];
-      out = LF + i;
+      out = (S*)LF + i;
       ostride = g.cap[0];
     }
     int px, py;
@@ -220,43 +271,49 @@ __global__ void __launch_bounds__(256) k_predict_level(Geo g, MeshDev B, double*
       if (threadIdx.y == 0) mr_set_err(B.cnt, MR_DERR_INTERNAL);
       continue;
     }
-    ValPtr sv[D == 2 ? 9 : 3];
+    ValPtr<S> sv[D == 2 ? 9 : 3];
 #pragma unroll
-    for (int k = 0; k < (D == 2 ? 9 : 3); ++k) sv[k] = mr_resolve(g, B, LF, st[k]);
+    for (int k = 0; k < (D == 2 ? 9 : 3); ++k) sv[k] = mr_resolve<S>(g, B, LF, st[k]);
     const int ci = (int)(code & ((1u << D) - 1u));
 #pragma unroll
     for (int p = threadIdx.y; p < Q; p += PY) {
-      double v[D == 2 ? 9 : 3];
+      C v[D == 2 ? 9 : 3];
 #pragma unroll
-      for (int k = 0; k < (D == 2 ? 9 : 3); ++k) v[k] = mr_ld(sv[k], p);
-      out[(size_t)p * ostride] = mr_predict_fast<D>(v, ci, cs);
+      for (int k = 0; k < (D == 2 ? 9 : 3); ++k) v[k] = ld_c<C>(sv[k], p);
+      out[(size_t)p * ostride] = mr_from_d<S>((double)predict_c<D, C>(v, ci, cs));
     }
   }
 }
 
 // ------------------------------------------------------------------ transport + collision
-template <int S>
-__global__ void __launch_bounds__(128) k_stream_collide(Geo g, MeshDev B, const double* __restrict__ LFin,
-                                                        double* __restrict__ LFout,
-                                                        const double* __restrict__ W, int do_stream,
-                                                        int do_collide) {
-  using Sc = Scheme<S>;
+template <int SC, int F>
+__global__ void __launch_bounds__(128) k_stream_collide(Geo g, MeshDev B, const void* __restrict__ LFin_,
+                                                        void* __restrict__ LFout_, const double* __restrict__ W,
+                                                        int do_stream, int do_collide) {
+  using Sc = Scheme<SC>;
+  using S = typename FormT<F>::S;
+  using C = typename FormT<F>::C;
+  constexpr bool OFFS = FormT<F>::offs;
   constexpr int D = Sc::D, Q = Sc::Q;
+  const S* LFin = (const S*)LFin_;
+  S* LFout = (S*)LFout_;
   const int n = B.cnt->total[MR_CLS_LEAF];
-  const double cs = (double)g.cross_sign;
+  const C cs = (C)g.cross_sign;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int l = B.lvl[MR_CLS_LEAF][i];
     const uint32_t code = B.code[MR_CLS_LEAF][i];
-    double f[Q], out[Q];
+    C f[Q], out[Q], offv[Q];
 #pragma unroll
     for (int p = 0; p < Q; ++p) {
-      f[p] = __ldg(LFin + (size_t)p * g.cap[0] + i);
+      offv[p] = OFFS ? (C)g.off[p] : (C)0;
+      ValPtr<S> me{LFin + i, g.cap[0]};
+      f[p] = ld_c<C>(me, p) + offv[p];
       out[p] = f[p];
     }
     if (do_stream) {
       int x, y;
       mr_decode(g, l, code, x, y);
-      const double scale = ldexp(1.0, l - g.J);
+      const C scale = (C)ldexp(1.0, l - g.J);
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         const int k = a == 0 ? x : y;
@@ -266,7 +323,7 @@ __global__ void __launch_bounds__(128) k_stream_collide(Geo g, MeshDev B, const 
         const double* wP = W + MR_WIDX(l, a, slot, 0);
         const double* wM = W + MR_WIDX(l, a, slot, 1);
         // window: delta = -2, -1, +1, +2 along a
-        ValPtr vp[4];
+        ValPtr<S> vp[4];
         bool has[4];
         int32_t ent[4];
 #pragma unroll
@@ -279,20 +336,20 @@ __global__ void __launch_bounds__(128) k_stream_collide(Geo g, MeshDev B, const 
             mr_set_err(B.cnt, MR_DERR_INTERNAL);
             has[w] = false;
           }
-          vp[w] = mr_resolve(g, B, LFin, has[w] ? ent[w] : 0);
+          vp[w] = mr_resolve<S>(g, B, LFin, has[w] ? ent[w] : 0);
         }
 #pragma unroll
         for (int p = 0; p < Q; ++p) {
           if (Sc::axis(p) != a) continue;
           const int sgn = Sc::sign(p);
           const double* w = sgn > 0 ? wP : wM;
-          double acc = w[2] * f[p];
+          C acc = (C)w[2] * f[p];
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            if (has[q]) acc += w[q < 2 ? q : q + 1] * mr_ld(vp[q], p);
+            if (has[q]) acc += (C)w[q < 2 ? q : q + 1] * (ld_c<C>(vp[q], p) + offv[p]);
           if (!per) {
-            if (sgn > 0 && k == 0) acc += bc_value(g.bc[2 * a], f, p, Sc::opp(p));
-            if (sgn < 0 && k == N - 1) acc += bc_value(g.bc[2 * a + 1], f, p, Sc::opp(p));
+            if (sgn > 0 && k == 0) acc += bc_value<C>(g.bc[2 * a], f, p, Sc::opp(p));
+            if (sgn < 0 && k == N - 1) acc += bc_value<C>(g.bc[2 * a + 1], f, p, Sc::opp(p));
           }
           out[p] += scale * acc;
         }
@@ -308,16 +365,16 @@ __global__ void __launch_bounds__(128) k_stream_collide(Geo g, MeshDev B, const 
             mr_set_err(B.cnt, MR_DERR_INTERNAL);
             continue;
           }
-          ValPtr sv[D == 2 ? 9 : 3], cv[1 << D];
+          ValPtr<S> sv[D == 2 ? 9 : 3], cv[1 << D];
 #pragma unroll
-          for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) sv[kk] = mr_resolve(g, B, LFin, st[kk]);
+          for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) sv[kk] = mr_resolve<S>(g, B, LFin, st[kk]);
           const uint32_t ncode = mr_encode(g, l, nx, ny);
           bool ok = true;
 #pragma unroll
           for (int ci = 0; ci < (1 << D); ++ci) {
             const int32_t e = B.map[g.base[l + 1] + ((ncode << D) | (uint32_t)ci)];
             ok = ok && e != MR_MAP_NONE;
-            cv[ci] = mr_resolve(g, B, LFin, e);
+            cv[ci] = mr_resolve<S>(g, B, LFin, e);
           }
           if (!ok) {
             mr_set_err(B.cnt, MR_DERR_INTERNAL);
@@ -338,40 +395,42 @@ __global__ void __launch_bounds__(128) k_stream_collide(Geo g, MeshDev B, const 
               c = side > 0 ? 2 * k + 2 : 2 * k;
             const int cslot = mr_slot(per ? 2 : c, N1, per);
             const double* wt = W + MR_WIDX(l + 1, a, cslot, sgn > 0 ? 2 : 3);
-            double v[D == 2 ? 9 : 3];
+            // details are exact on constants: stored values suffice
+            C v[D == 2 ? 9 : 3];
 #pragma unroll
-            for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) v[kk] = mr_ld(sv[kk], p);
-            double corr = 0.0;
+            for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) v[kk] = ld_c<C>(sv[kk], p);
+            C corr = (C)0;
 #pragma unroll
             for (int ci = 0; ci < (1 << D); ++ci) {
               const int sa = (ci >> a) & 1;
               const int delta = 2 * (k + side) + sa - c;
               if (delta < -2 || delta > 2) continue;
-              const double det = mr_ld(cv[ci], p) - mr_predict_fast<D>(v, ci, cs);
-              corr += wt[delta + 2] * det;
+              const C det = ld_c<C>(cv[ci], p) - predict_c<D, C>(v, ci, cs);
+              corr += (C)wt[delta + 2] * det;
             }
-            corr *= (D == 2 ? 0.5 : 1.0);
+            corr *= (D == 2 ? (C)0.5 : (C)1);
             out[p] += scale * (incoming ? corr : -corr);
           }
         }
       }
     }
-    if (do_collide) Sc::collide(g, out);
+    if (do_collide) Sc::template collide<C>(g, out);
     bool finite = true;
 #pragma unroll
     for (int p = 0; p < Q; ++p) {
       finite = finite && isfinite(out[p]);
-      LFout[(size_t)p * g.cap[0] + i] = out[p];
+      LFout[(size_t)p * g.cap[0] + i] = mr_from_d<S>((double)(out[p] - offv[p]));
     }
     if (!finite) mr_set_err(B.cnt, MR_DERR_NONFINITE);
   }
 }
 
 // ------------------------------------------------------------------ input / output
-template <int S>
-__global__ void __launch_bounds__(256) k_init_eq(Geo g, MeshDev B, const double* __restrict__ cons,
-                                                 double* LF) {
-  using Sc = Scheme<S>;
+template <int SC, int F>
+__global__ void __launch_bounds__(256) k_init_eq(Geo g, MeshDev B, const double* __restrict__ cons, void* LF_) {
+  using Sc = Scheme<SC>;
+  using S = typename FormT<F>::S;
+  S* LF = (S*)LF_;
   const int n = B.cnt->total[MR_CLS_LEAF];
   const long long NJ = (long long)g.n[g.J][0] * (Sc::D == 2 ? g.n[g.J][1] : 1);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -382,13 +441,16 @@ __global__ void __launch_bounds__(256) k_init_eq(Geo g, MeshDev B, const double*
     for (int k = 0; k < g.ncons; ++k) u[k] = cons[k * NJ + r];
     Sc::equilibrium(g, u, f);
 #pragma unroll
-    for (int p = 0; p < Sc::Q; ++p) LF[(size_t)p * g.cap[0] + i] = f[p];
+    for (int p = 0; p < Sc::Q; ++p)
+      LF[(size_t)p * g.cap[0] + i] = mr_from_d<S>(FormT<F>::offs ? f[p] - g.off[p] : f[p]);
   }
 }
 
+template <int F>
 __global__ void __launch_bounds__(256) k_gather_input(Geo g, MeshDev B, const int32_t* __restrict__ inidx,
-                                                      long long nin, const double* __restrict__ fin,
-                                                      double* LF) {
+                                                      long long nin, const double* __restrict__ fin, void* LF_) {
+  using S = typename FormT<F>::S;
+  S* LF = (S*)LF_;
   const int n = B.cnt->total[MR_CLS_LEAF];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int l = B.lvl[MR_CLS_LEAF][i];
@@ -397,28 +459,36 @@ __global__ void __launch_bounds__(256) k_gather_input(Geo g, MeshDev B, const in
       mr_set_err(B.cnt, MR_DERR_INPUT);
       continue;
     }
-    for (int p = 0; p < g.Q; ++p) LF[(size_t)p * g.cap[0] + i] = fin[(size_t)p * nin + j];
+    for (int p = 0; p < g.Q; ++p) {
+      const double v = fin[(size_t)p * nin + j];
+      LF[(size_t)p * g.cap[0] + i] = mr_from_d<S>(FormT<F>::offs ? v - g.off[p] : v);
+    }
   }
 }
 
-__global__ void __launch_bounds__(256) k_leaves_out(Geo g, MeshDev B, const double* __restrict__ LF,
-                                                    long long n, unsigned long long* keys,
-                                                    signed char* levels, double* f) {
+template <int F>
+__global__ void __launch_bounds__(256) k_leaves_out(Geo g, MeshDev B, const void* __restrict__ LF_, long long n,
+                                                    unsigned long long* keys, signed char* levels, double* f) {
+  using S = typename FormT<F>::S;
+  const S* LF = (const S*)LF_;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     if (keys) keys[i] = B.code[MR_CLS_LEAF][i];
     if (levels) levels[i] = (signed char)B.lvl[MR_CLS_LEAF][i];
     if (f)
-      for (int p = 0; p < g.Q; ++p) f[(size_t)p * n + i] = LF[(size_t)p * g.cap[0] + i];
+      for (int p = 0; p < g.Q; ++p) {
+        const double v = mr_cvt_d(LF[(size_t)p * g.cap[0] + i]);
+        f[(size_t)p * n + i] = FormT<F>::offs ? v + g.off[p] : v;
+      }
   }
 }
 
 // Conserved moments on the uniform level `level`, row-major: values of the
 // complete tree where present, the prediction of the level above otherwise.
-template <int D>
-__global__ void __launch_bounds__(256) k_project_dense(Geo g, MeshDev B, const double* __restrict__ LF,
-                                                       int level, const double* __restrict__ prev,
-                                                       double* cur) {
+template <int D, int F>
+__global__ void __launch_bounds__(256) k_project_dense(Geo g, MeshDev B, const void* __restrict__ LF, int level,
+                                                       const double* __restrict__ prev, double* cur) {
+  using S = typename FormT<F>::S;
   const int nx = g.n[level][0], ny = D == 2 ? g.n[level][1] : 1;
   const long long N = (long long)nx * ny;
   const int pnx = level > g.Jmin ? g.n[level - 1][0] : 1;
@@ -429,10 +499,11 @@ __global__ void __launch_bounds__(256) k_project_dense(Geo g, MeshDev B, const d
     const int x = (int)(r % nx), y = (int)(r / nx);
     const int32_t e = B.map[g.base[level] + mr_encode(g, level, x, y)];
     if (e != MR_MAP_NONE && (((uint32_t)e) >> 30) <= MR_CLS_INT) {
-      const ValPtr v = mr_resolve(g, B, LF, e);
+      const ValPtr<S> v = mr_resolve<S>(g, B, LF, e);
       for (int k = 0; k < g.ncons; ++k) {
         double acc = 0.0;
-        for (int p = 0; p < g.Q; ++p) acc += g.consw[k][p] * mr_ld(v, p);
+        for (int p = 0; p < g.Q; ++p)
+          acc += g.consw[k][p] * (mr_ld(v, p) + (FormT<F>::offs ? g.off[p] : 0.0));
         cur[k * N + r] = acc;
       }
     } else if (level > g.Jmin) {
@@ -459,78 +530,127 @@ __global__ void k_count_updates(MeshCounts* cnt) {
   cnt->steps += 1;
 }
 
-template <int Q>
-void launch_remesh_t(const Geo& g, const MeshDev& A, const double* LFo, const MeshDev& B, double* LFn,
-                     cudaStream_t st, int grid) {
-  k_remesh_copy<Q><<<grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LFo, B, LFn);
+template <int Q, int F>
+void launch_remesh_t(const Geo& g, const MeshDev& A, const void* LFo, const MeshDev& B, void* LFn, cudaStream_t st,
+                     int grid) {
+  k_remesh_copy<Q, F><<<grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LFo, B, LFn);
 }
-template <int D, int Q>
-void launch_predict_t(const Geo& g, const MeshDev& B, double* LF, int level, cudaStream_t st, int grid) {
+template <int D, int Q, int F>
+void launch_predict_t(const Geo& g, const MeshDev& B, void* LF, int level, cudaStream_t st, int grid) {
   // `grid` is the maximum number of blocks; a block covers 32 cells
   const int need = (int)((2u * g.ncode[level] + 31) / 32);
-  k_predict_level<D, Q><<<need < grid ? need : grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, B, LF, level);
+  k_predict_level<D, Q, F><<<need < grid ? need : grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, B, LF, level);
+}
+template <int SC, int F>
+void launch_stream_t(const Geo& g, const MeshDev& B, const void* in, void* out, const double* W, int ds, int dc,
+                     cudaStream_t st, int grid) {
+  k_stream_collide<SC, F><<<grid, 128, 0, st>>>(g, B, in, out, W, ds, dc);
+}
+template <int SC, int F>
+void launch_init_t(const Geo& g, const MeshDev& B, const double* cons, void* LF, cudaStream_t st, int grid) {
+  k_init_eq<SC, F><<<grid, 256, 0, st>>>(g, B, cons, LF);
 }
 
 }  // namespace
 
-void mr_launch_remesh_copy(const Geo& g, const MeshDev& A, const double* LF_old, const MeshDev& B,
-                           double* LF_new, cudaStream_t st, int grid) {
+#define MR_FORMS(FN, ...)                                          \
+  switch (g.form) {                                                \
+    case MR_FORM_F64: FN<MR_FORM_F64>(__VA_ARGS__); break;         \
+    case MR_FORM_F32: FN<MR_FORM_F32>(__VA_ARGS__); break;         \
+    case MR_FORM_F32_F16: FN<MR_FORM_F32_F16>(__VA_ARGS__); break; \
+    case MR_FORM_F32_BF16: FN<MR_FORM_F32_BF16>(__VA_ARGS__); break; \
+  }
+#define MR_FORMS2(FN, A1, ...)                                         \
+  switch (g.form) {                                                    \
+    case MR_FORM_F64: FN<A1, MR_FORM_F64>(__VA_ARGS__); break;         \
+    case MR_FORM_F32: FN<A1, MR_FORM_F32>(__VA_ARGS__); break;         \
+    case MR_FORM_F32_F16: FN<A1, MR_FORM_F32_F16>(__VA_ARGS__); break; \
+    case MR_FORM_F32_BF16: FN<A1, MR_FORM_F32_BF16>(__VA_ARGS__); break; \
+  }
+#define MR_FORMS3(FN, A1, A2, ...)                                         \
+  switch (g.form) {                                                        \
+    case MR_FORM_F64: FN<A1, A2, MR_FORM_F64>(__VA_ARGS__); break;         \
+    case MR_FORM_F32: FN<A1, A2, MR_FORM_F32>(__VA_ARGS__); break;         \
+    case MR_FORM_F32_F16: FN<A1, A2, MR_FORM_F32_F16>(__VA_ARGS__); break; \
+    case MR_FORM_F32_BF16: FN<A1, A2, MR_FORM_F32_BF16>(__VA_ARGS__); break; \
+  }
+
+size_t mr_form_bytes(int form) {
+  switch (form) {
+    case MR_FORM_F64: return 8;
+    case MR_FORM_F32: return 4;
+    default: return 2;
+  }
+}
+
+void mr_launch_remesh_copy(const Geo& g, const MeshDev& A, const void* LF_old, const MeshDev& B, void* LF_new,
+                           cudaStream_t st, int grid) {
   switch (g.Q) {
-    case 2: launch_remesh_t<2>(g, A, LF_old, B, LF_new, st, grid); break;
-    case 3: launch_remesh_t<3>(g, A, LF_old, B, LF_new, st, grid); break;
-    case 9: launch_remesh_t<9>(g, A, LF_old, B, LF_new, st, grid); break;
-    case 16: launch_remesh_t<16>(g, A, LF_old, B, LF_new, st, grid); break;
+    case 2: MR_FORMS2(launch_remesh_t, 2, g, A, LF_old, B, LF_new, st, grid); break;
+    case 3: MR_FORMS2(launch_remesh_t, 3, g, A, LF_old, B, LF_new, st, grid); break;
+    case 16: MR_FORMS2(launch_remesh_t, 16, g, A, LF_old, B, LF_new, st, grid); break;
   }
 }
 
-void mr_launch_predict_level(const Geo& g, const MeshDev& B, double* LF, int level, cudaStream_t st,
-                             int grid) {
+void mr_launch_predict_level(const Geo& g, const MeshDev& B, void* LF, int level, cudaStream_t st, int grid) {
   switch (g.d * 100 + g.Q) {
-    case 102: launch_predict_t<1, 2>(g, B, LF, level, st, grid); break;
-    case 103: launch_predict_t<1, 3>(g, B, LF, level, st, grid); break;
-    case 216: launch_predict_t<2, 16>(g, B, LF, level, st, grid); break;
-    case 209: launch_predict_t<2, 9>(g, B, LF, level, st, grid); break;
+    case 102: MR_FORMS3(launch_predict_t, 1, 2, g, B, LF, level, st, grid); break;
+    case 103: MR_FORMS3(launch_predict_t, 1, 3, g, B, LF, level, st, grid); break;
+    case 216: MR_FORMS3(launch_predict_t, 2, 16, g, B, LF, level, st, grid); break;
   }
 }
 
-void mr_launch_stream_collide(const Geo& g, const MeshDev& B, const double* LF_in, double* LF_out,
-                              const double* W, int do_stream, int do_collide, cudaStream_t st,
-                              int grid) {
+void mr_launch_stream_collide(const Geo& g, const MeshDev& B, const void* LF_in, void* LF_out, const double* W,
+                              int do_stream, int do_collide, cudaStream_t st, int grid) {
   switch (g.scheme) {
-    case 0: k_stream_collide<0><<<grid, 128, 0, st>>>(g, B, LF_in, LF_out, W, do_stream, do_collide); break;
-    case 1: k_stream_collide<1><<<grid, 128, 0, st>>>(g, B, LF_in, LF_out, W, do_stream, do_collide); break;
-    case 2: k_stream_collide<2><<<grid, 128, 0, st>>>(g, B, LF_in, LF_out, W, do_stream, do_collide); break;
-    case 3: k_stream_collide<3><<<grid, 128, 0, st>>>(g, B, LF_in, LF_out, W, do_stream, do_collide); break;
+    case 0: MR_FORMS2(launch_stream_t, 0, g, B, LF_in, LF_out, W, do_stream, do_collide, st, grid); break;
+    case 1: MR_FORMS2(launch_stream_t, 1, g, B, LF_in, LF_out, W, do_stream, do_collide, st, grid); break;
+    case 2: MR_FORMS2(launch_stream_t, 2, g, B, LF_in, LF_out, W, do_stream, do_collide, st, grid); break;
+    case 3: MR_FORMS2(launch_stream_t, 3, g, B, LF_in, LF_out, W, do_stream, do_collide, st, grid); break;
   }
 }
 
-void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, double* LF, cudaStream_t st,
-                       int grid) {
+void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, void* LF, cudaStream_t st, int grid) {
   switch (g.scheme) {
-    case 0: k_init_eq<0><<<grid, 256, 0, st>>>(g, B, cons, LF); break;
-    case 1: k_init_eq<1><<<grid, 256, 0, st>>>(g, B, cons, LF); break;
-    case 2: k_init_eq<2><<<grid, 256, 0, st>>>(g, B, cons, LF); break;
-    case 3: k_init_eq<3><<<grid, 256, 0, st>>>(g, B, cons, LF); break;
+    case 0: MR_FORMS2(launch_init_t, 0, g, B, cons, LF, st, grid); break;
+    case 1: MR_FORMS2(launch_init_t, 1, g, B, cons, LF, st, grid); break;
+    case 2: MR_FORMS2(launch_init_t, 2, g, B, cons, LF, st, grid); break;
+    case 3: MR_FORMS2(launch_init_t, 3, g, B, cons, LF, st, grid); break;
   }
 }
 
-void mr_launch_gather_input(const Geo& g, const MeshDev& B, const int32_t* inidx, long long n,
-                            const double* fin, double* LF, cudaStream_t st, int grid) {
-  k_gather_input<<<grid, 256, 0, st>>>(g, B, inidx, n, fin, LF);
+template <int F>
+static void launch_gather_t(const Geo& g, const MeshDev& B, const int32_t* inidx, long long n, const double* fin,
+                            void* LF, cudaStream_t st, int grid) {
+  k_gather_input<F><<<grid, 256, 0, st>>>(g, B, inidx, n, fin, LF);
+}
+void mr_launch_gather_input(const Geo& g, const MeshDev& B, const int32_t* inidx, long long n, const double* fin,
+                            void* LF, cudaStream_t st, int grid) {
+  MR_FORMS(launch_gather_t, g, B, inidx, n, fin, LF, st, grid);
 }
 
-void mr_launch_leaves_out(const Geo& g, const MeshDev& B, const double* LF, long long n,
-                          unsigned long long* keys, signed char* levels, double* f, cudaStream_t st,
-                          int grid) {
-  k_leaves_out<<<grid, 256, 0, st>>>(g, B, LF, n, keys, levels, f);
+template <int F>
+static void launch_out_t(const Geo& g, const MeshDev& B, const void* LF, long long n, unsigned long long* keys,
+                         signed char* levels, double* f, cudaStream_t st, int grid) {
+  k_leaves_out<F><<<grid, 256, 0, st>>>(g, B, LF, n, keys, levels, f);
+}
+void mr_launch_leaves_out(const Geo& g, const MeshDev& B, const void* LF, long long n, unsigned long long* keys,
+                          signed char* levels, double* f, cudaStream_t st, int grid) {
+  MR_FORMS(launch_out_t, g, B, LF, n, keys, levels, f, st, grid);
 }
 
-void mr_launch_project_dense(const Geo& g, const MeshDev& B, const double* LF, int level,
-                             const double* prev, double* cur, cudaStream_t st, int grid) {
-  if (g.d == 1)
-    k_project_dense<1><<<grid, 256, 0, st>>>(g, B, LF, level, prev, cur);
-  else
-    k_project_dense<2><<<grid, 256, 0, st>>>(g, B, LF, level, prev, cur);
+template <int D, int F>
+static void launch_dense_t(const Geo& g, const MeshDev& B, const void* LF, int level, const double* prev,
+                           double* cur, cudaStream_t st, int grid) {
+  k_project_dense<D, F><<<grid, 256, 0, st>>>(g, B, LF, level, prev, cur);
+}
+void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int level, const double* prev,
+                             double* cur, cudaStream_t st, int grid) {
+  if (g.d == 1) {
+    MR_FORMS2(launch_dense_t, 1, g, B, LF, level, prev, cur, st, grid);
+  } else {
+    MR_FORMS2(launch_dense_t, 2, g, B, LF, level, prev, cur, st, grid);
+  }
 }
 
 void mr_launch_count_updates(MeshCounts* cnt, cudaStream_t st) { k_count_updates<<<1, 1, 0, st>>>(cnt); }
