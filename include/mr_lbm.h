@@ -14,7 +14,8 @@
  * transport (Eq. AdaptiveAdvectionPhase evaluated with the flattened weights
  * of Eq. PredictionWithMatrixNew plus the finer-neighbour correction of
  * Sec. 6.1, boundaries by Eq. AdvectionOnBoundary) and the collision on the
- * leaves (Eq. AdaptiveCollision).
+ * leaves (Eq. AdaptiveCollision), and, for D2Q9 with an obstacle, the
+ * penalisation of Sec. 7.2.2.
  *
  * Conventions shared by every entry point:
  *  - every function returns an mr_status and never aborts or throws;
@@ -62,14 +63,22 @@ typedef enum {
   MR_D1Q2_BURGERS = 1,       /* m^eq = (u, u^2/2) */
   MR_D1Q3_SHALLOW_WATER = 2, /* m^eq = (h, q, q^2/h + g h^2/2), g = phys[0] */
   MR_D2Q4x4_EULER = 3,       /* vectorial D2Q4^4 of Sec. 7.1.2, gamma = phys[0] */
-  MR_D2Q9_NS = 4             /* Sec. 7.2.2; accepted by the oracle only, MR_EINVAL here */
+  MR_D2Q9_NS = 4             /* D2Q9 of Sec. 7.2.2 (orthogonal moments, Lallemand-Luo):
+                                conserved (rho, q_x, q_y); s[0] relaxes the energy, energy
+                                square and heat-flux moments, s[1] the two stress moments;
+                                rho0 = phys[0], u0 = (phys[1], phys[2]) for
+                                MR_BC_BOUNCE_BACK_VELOCITY and the obstacle; obstacle disc
+                                centre (phys[3], phys[4]), radius phys[5].  Needs the
+                                tensor-product prediction (cross_sign +1). */
 } mr_scheme;
 
 typedef enum {
   MR_BC_PERIODIC = 0,        /* both faces of an axis must be periodic */
   MR_BC_COPY = 1,            /* Eq. refBoundaryConditions, copy */
   MR_BC_BOUNCE_BACK = 2,     /* Eq. refBoundaryConditions, bounce back */
-  MR_BC_ANTI_BOUNCE_BACK = 3 /* Eq. refBoundaryConditions, anti bounce back */
+  MR_BC_ANTI_BOUNCE_BACK = 3, /* Eq. refBoundaryConditions, anti bounce back */
+  MR_BC_BOUNCE_BACK_VELOCITY = 4 /* bounce back of a wall moving at u0 (Sec. 7.2.2, D2Q9 only):
+                                    f^{h dagger} + f^{h,eq}(rho0, u0) - f^{h dagger,eq}(rho0, u0) */
 } mr_bc;
 
 /* Storage and arithmetic of the populations.  The details that decide the
@@ -87,9 +96,10 @@ typedef struct {
   double lambda;         /* lattice velocity lambda = dx/dt, Eq. acousticscaling; > 0 */
   double s[16];          /* relaxation rates in [0, 2] of the non-conserved moments:
                             D1Q2: s[0]; D1Q3: s[0] (third moment);
-                            D2Q4^4: s[i] = s_i^q, s[4+i] = s_i^xy, i = 0..3 */
+                            D2Q4^4: s[i] = s_i^q, s[4+i] = s_i^xy, i = 0..3;
+                            D2Q9: s[0] (energy, energy square, heat flux), s[1] (stress) */
   double phys[8];        /* scheme constants (see mr_scheme) */
-  double xmin[3], xmax[3]; /* physical domain, informational */
+  double xmin[3], xmax[3]; /* physical domain (used by the obstacle only) */
   int roots[3];          /* cells per axis at level 0 (1 for the unit square) */
   int min_level, max_level; /* J_min and J; 2 <= J_min <= J <= 15 */
   double eps;            /* threshold epsilon >= 0, eps_j = 2^{d(j-J)} eps (Sec. 4.4) */
@@ -100,6 +110,9 @@ typedef struct {
                             -1: diagonal term with the sign printed in Sec. 4.1 */
   int precision;         /* mr_precision */
   long long leaf_capacity; /* maximum number of leaves; 0 = all finest cells */
+  int obstacle;          /* 1: penalisation of Sec. 7.2.2 after each collision (D2Q9 only):
+                            f <- phi f^eq(rho0, 0) + (1 - phi) f, phi = share of the leaf's
+                            finest-cell centres inside the disc; xmin / xmax place the disc */
 } mr_lbm_config;
 
 typedef struct mr_lbm* mr_lbm_t;
@@ -118,7 +131,7 @@ mr_status mr_lbm_destroy(mr_lbm_t h);
  * f = M^{-1} m^eq of the given conserved moments.  `conserved` is SoA
  * [ncons][N_J] of doubles, N_J = prod_a roots[a] 2^J cells of level J,
  * row-major (x fastest); ncons = 1 (D1Q2), 2 (D1Q3), 4 (D2Q4^4:
- * rho, rho u, rho v, E). */
+ * rho, rho u, rho v, E), 3 (D2Q9: rho, q_x, q_y). */
 mr_status mr_lbm_init(mr_lbm_t h, const double* conserved, int on_device);
 
 /* `nsteps` iterations of the loop of Algorithm 1: adapt the mesh from the

@@ -21,11 +21,11 @@ MR_STATUS = {0: "MR_OK", 1: "MR_EINVAL", 2: "MR_ENOMEM", 3: "MR_ECUDA", 4: "MR_E
              5: "MR_ENOCONV", 6: "MR_ENONFINITE", 7: "MR_ESTATE", 8: "MR_EINTERNAL"}
 SCHEMES = {"d1q2_advection": 0, "d1q2_burgers": 1, "d1q3_shallow_water": 2, "d2q4x4_euler": 3,
            "d2q9_ns": 4}
-BCS = {"periodic": 0, "copy": 1, "bounce_back": 2, "anti_bounce_back": 3}
+BCS = {"periodic": 0, "copy": 1, "bounce_back": 2, "anti_bounce_back": 3, "bounce_back_velocity": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
-NCONS = {0: 1, 1: 1, 2: 2, 3: 4}
-NPOP = {0: 2, 1: 2, 2: 3, 3: 16}
-DIM = {0: 1, 1: 1, 2: 1, 3: 2}
+NCONS = {0: 1, 1: 1, 2: 2, 3: 4, 4: 3}
+NPOP = {0: 2, 1: 2, 2: 3, 3: 16, 4: 9}
+DIM = {0: 1, 1: 1, 2: 1, 3: 2, 4: 2}
 
 
 class MrError(RuntimeError):
@@ -52,6 +52,7 @@ class MrConfig(C.Structure):
         ("cross_sign", C.c_int),
         ("precision", C.c_int),
         ("leaf_capacity", C.c_longlong),
+        ("obstacle", C.c_int),
     ]
 
 
@@ -124,6 +125,7 @@ def make_config(cfg: Dict, leaf_capacity: int = 0) -> MrConfig:
     prec = cfg.get("precision", 0)
     c.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     c.leaf_capacity = int(cfg.get("leaf_capacity", leaf_capacity))
+    c.obstacle = int(cfg.get("obstacle", 0))
     return c
 
 

@@ -69,6 +69,20 @@ bool scheme_setup(Geo& g, const mr_lbm_config* c) {
       for (int i = 0; i < 4; ++i)
         for (int h = 0; h < 4; ++h) g.consw[i][4 * i + h] = 1;
       break;
+    case MR_D2Q9_NS: {
+      static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+      static const int op[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+      g.d = 2; g.q = 9; g.m = 1; g.ncons = 3;
+      for (int h = 0; h < 9; ++h) {
+        g.eta[h][0] = ex[h];
+        g.eta[h][1] = ey[h];
+        g.opp[h] = op[h];
+        g.consw[0][h] = 1;
+        g.consw[1][h] = L * ex[h];
+        g.consw[2][h] = L * ey[h];
+      }
+      break;
+    }
     default:
       return false;
   }
@@ -187,12 +201,40 @@ void host_equilibrium(const Geo& g, const double* u, double* f) {
       }
       break;
     }
+    case MR_D2Q9_NS: {
+      // orthogonal integer rows R_r (the rows of M over their power of
+      // lambda): f = sum_r R_r mu_r / |R_r|^2, j = q / lambda
+      static const int R[9][9] = {{1, 1, 1, 1, 1, 1, 1, 1, 1},         {0, 1, 0, -1, 0, 1, -1, -1, 1},
+                                  {0, 0, 1, 0, -1, 1, 1, -1, -1},      {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+                                  {0, -2, 0, 2, 0, 1, -1, -1, 1},      {0, 0, -2, 0, 2, 1, 1, -1, -1},
+                                  {4, -2, -2, -2, -2, 1, 1, 1, 1},     {0, 1, -1, 1, -1, 0, 0, 0, 0},
+                                  {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+      const double rho = u[0], jx = u[1] / L, jy = u[2] / L;
+      const double j2 = (jx * jx + jy * jy) / rho;
+      const double mu[9] = {rho, jx, jy, -2.0 * rho + 3.0 * j2, -jx, -jy, rho - 3.0 * j2,
+                            (jx * jx - jy * jy) / rho, jx * jy / rho};
+      for (int h = 0; h < 9; ++h) {
+        double acc = 0.0;
+        for (int r = 0; r < 9; ++r) {
+          double n2 = 0.0;
+          for (int k = 0; k < 9; ++k) n2 += (double)(R[r][k] * R[r][k]);
+          acc += R[r][h] * mu[r] / n2;
+        }
+        f[h] = acc;
+      }
+      break;
+    }
   }
 }
 
 mr_status validate(const mr_lbm_config* c) {
   if (!c) return MR_EINVAL;
-  if (c->scheme < 0 || c->scheme > MR_D2Q4x4_EULER) return MR_EINVAL;
+  if (c->scheme < 0 || c->scheme > MR_D2Q9_NS) return MR_EINVAL;
+  if (c->scheme == MR_D2Q9_NS && c->cross_sign == -1) return MR_EINVAL;  // needs the tensor product
+  if (c->obstacle != 0 && (c->obstacle != 1 || c->scheme != MR_D2Q9_NS)) return MR_EINVAL;
+  for (int f = 0; f < 6; ++f)
+    if (c->bc[f] == MR_BC_BOUNCE_BACK_VELOCITY && c->scheme != MR_D2Q9_NS) return MR_EINVAL;
+  if (c->obstacle && !(c->xmax[0] > c->xmin[0]) ) return MR_EINVAL;
   if (!(c->lambda > 0) || !(c->eps >= 0) || c->mu_bar < 0) return MR_EINVAL;
   if (c->pred_s != 0 && c->pred_s != 1) return MR_EINVAL;
   if (c->precision < MR_FP64 || c->precision > MR_FP32_BF16STORE) return MR_EINVAL;
@@ -200,7 +242,7 @@ mr_status validate(const mr_lbm_config* c) {
   for (int i = 0; i < 16; ++i)
     if (!(c->s[i] >= 0.0 && c->s[i] <= 2.0)) return MR_EINVAL;
   for (int f = 0; f < 6; ++f)
-    if (c->bc[f] < MR_BC_PERIODIC || c->bc[f] > MR_BC_ANTI_BOUNCE_BACK) return MR_EINVAL;
+    if (c->bc[f] < MR_BC_PERIODIC || c->bc[f] > MR_BC_BOUNCE_BACK_VELOCITY) return MR_EINVAL;
   for (int a = 0; a < 3; ++a)
     if ((c->bc[2 * a] == MR_BC_PERIODIC) != (c->bc[2 * a + 1] == MR_BC_PERIODIC)) return MR_EINVAL;
   if (c->cross_sign != 0 && c->cross_sign != 1 && c->cross_sign != -1) return MR_EINVAL;
@@ -488,7 +530,22 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   g.mu_bar = cfg->mu_bar;
   g.cross_sign = cfg->cross_sign == -1 ? -1 : 1;
   g.form = cfg->precision;  // MR_FP64 .. MR_FP32_BF16STORE map onto MR_FORM_F64 .. MR_FORM_F32_BF16
-  for (int p = 0; p < MR_MAXQ; ++p) g.off[p] = 0.0;
+  for (int p = 0; p < MR_MAXQ; ++p) g.off[p] = g.feq0[p] = g.bcv[p] = 0.0;
+  g.diag = g.scheme == MR_D2Q9_NS;
+  g.obstacle = cfg->obstacle;
+  g.xlo[0] = cfg->xmin[0];
+  g.xlo[1] = cfg->xmin[1];
+  g.dxJ = (cfg->xmax[0] - cfg->xmin[0]) / g.n[g.J][0];
+  for (int i = 0; i < 3; ++i) g.obs[i] = cfg->phys[3 + i];
+  if (g.scheme == MR_D2Q9_NS) {
+    // rest state (rho0, 0) of the obstacle; wall state (rho0, rho0 u0)
+    const double rest[4] = {cfg->phys[0], 0.0, 0.0, 0.0};
+    const double wall[4] = {cfg->phys[0], cfg->phys[0] * cfg->phys[1], cfg->phys[0] * cfg->phys[2], 0.0};
+    double fw[MR_MAXQ];
+    host_equilibrium(g, rest, g.feq0);
+    host_equilibrium(g, wall, fw);
+    for (int p = 0; p < g.Q; ++p) g.bcv[p] = fw[p] - fw[g.opp[p]];
+  }
   long long nJ = g.ncode[g.J], nint = 0, nall = 0;
   for (int l = g.Jmin; l <= g.J; ++l) {
     nall += g.ncode[l];

@@ -137,6 +137,7 @@ void launch_details_t(const Geo& g, const MeshDev& A, const void* LF, cudaStream
   switch (g.d * 100 + g.Q) {                                      \
     case 102: MR_DISPATCH_F(FN, 1, 2, __VA_ARGS__); break;        \
     case 103: MR_DISPATCH_F(FN, 1, 3, __VA_ARGS__); break;        \
+    case 209: MR_DISPATCH_F(FN, 2, 9, __VA_ARGS__); break;        \
     case 216: MR_DISPATCH_F(FN, 2, 16, __VA_ARGS__); break;       \
     default: break;                                               \
   }

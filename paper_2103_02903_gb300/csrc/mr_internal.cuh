@@ -60,6 +60,13 @@ struct Geo {
   double consw[4][MR_MAXQ];    // conserved moments as linear forms of the populations
   int form;                    // storage / compute form, see MR_FORM_*
   double off[MR_MAXQ];         // stored value = population - off[p] (0 unless 16-bit storage)
+  int diag;                    // lattice with diagonal velocities: 5^d stream window
+  int obstacle;                // penalisation of Sec. 7.2.2 after the collision
+  double obs[3];               // obstacle disc: centre x, y and radius
+  double xlo[2];               // domain origin
+  double dxJ;                  // finest cell size
+  double feq0[MR_MAXQ];        // equilibrium populations at (rho0, 0, 0)
+  double bcv[MR_MAXQ];         // f^{h,eq} - f^{h dagger,eq} at (rho0, u0): bounce back with velocity
 };
 
 // Storage / compute forms: populations are stored as S and transported and

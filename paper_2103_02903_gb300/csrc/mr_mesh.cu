@@ -131,19 +131,29 @@ __global__ void __launch_bounds__(256) k_full_mesh(Geo g, uint8_t* cls) {
 // ---------------------------------------------------------------- ghosts
 // The transport of a leaf on level l reads the reconstructed values of the
 // cells at distance 1 and 2 along each axis on level l (the flattened
-// window).  Those outside R(Lambda) are ghosts: predicted from level l-1,
-// whose stencil cells outside R(Lambda) are ghosts in turn.
+// window), and, for a lattice with diagonal velocities, the whole 5 x 5
+// block around the leaf.  Those outside R(Lambda) are ghosts: predicted from
+// level l-1, whose stencil cells outside R(Lambda) are ghosts in turn.
 template <int D>
 __global__ void __launch_bounds__(256) k_mark_ghosts(Geo g, uint8_t* cls) {
-  const int nwin = 4 * D;
+  const bool block = D == 2 && g.diag;
+  const int nwin = block ? 25 : 4 * D;
   MR_DENSE_CHUNK_BEGIN(g, 0u, l, c, gi)
     if ((cls[gi] & 3u) != MR_C_LEAF) continue;
     int x, y;
     mr_decode(g, l, c, x, y);
     for (int w = 0; w < nwin; ++w) {
-      const int axis = w >> 2, k = w & 3;
-      const int off = k < 2 ? k - 2 : k - 1;  // -2, -1, +1, +2
-      int nx = x + (axis == 0 ? off : 0), ny = y + (axis == 1 ? off : 0);
+      int nx, ny;
+      if (block) {
+        if (w == 12) continue;  // the leaf itself
+        nx = x + w % 5 - 2;
+        ny = y + w / 5 - 2;
+      } else {
+        const int axis = w >> 2, k = w & 3;
+        const int off = k < 2 ? k - 2 : k - 1;  // -2, -1, +1, +2
+        nx = x + (axis == 0 ? off : 0);
+        ny = y + (axis == 1 ? off : 0);
+      }
       if (!mr_nbr_mesh(g, l, nx, ny)) continue;
       const uint32_t gw = g.base[l] + mr_encode(g, l, nx, ny);
       if (cls[gw] & 3u) continue;

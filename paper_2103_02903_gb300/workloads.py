@@ -194,10 +194,42 @@ def ns_obstacle_2d(seed: int = 0, max_level: int = 10, min_level: int = 2, eps: 
     return cfg, np.stack([rho, rho * u0 * np.ones_like(X), rho * dv]).astype(np.float64)
 
 
+def vortices_2d(seed: int = 0, max_level: int = 8, min_level: int = 2, eps: float = 1e-4,
+                n_vortices: int = 0, bc: str = "periodic"):
+    """D2Q9 on the periodic unit square with 2-8 Gaussian (Lamb-Oseen) vortices:
+    seeded centres, core radii in [0.02, 0.1], circulations +-U(0.5, 1) * 0.05
+    (velocity scale 0.05, lambda = 1), rho = 1; minimum-image distances.
+    ``bc`` other than periodic puts that condition on all four faces."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lam, rho0, u0 = 1.0, 1.0, 0.05
+    cfg = base_config("d2q9_ns", lambda_=lam, min_level=min_level, max_level=max_level, eps=eps,
+                      mu_bar=1, bc=[bc] * 4 + ["periodic"] * 2)
+    cfg["s"][0] = 1.5
+    cfg["s"][1] = 1.8
+    cfg["phys"][0:3] = [rho0, 0.0, 0.0]
+    X, Y = cell_centres(cfg)
+    nv = n_vortices or int(rng.integers(2, 9))
+    ux = np.zeros_like(X)
+    uy = np.zeros_like(X)
+    for _ in range(nv):
+        xc, yc = rng.uniform(0.0, 1.0, 2)
+        R = rng.uniform(0.02, 0.1)
+        gam = rng.choice([-1.0, 1.0]) * rng.uniform(0.5, 1.0) * u0 * 2.0 * math.pi * R
+        dx = (X - xc + 0.5) % 1.0 - 0.5
+        dy = (Y - yc + 0.5) % 1.0 - 0.5
+        r2 = np.maximum(dx * dx + dy * dy, 1e-300)
+        ut = gam / (2.0 * math.pi * r2) * (1.0 - np.exp(-r2 / (R * R)))
+        ux += -dy * ut
+        uy += dx * ut
+    rho = np.full_like(X, rho0)
+    return cfg, np.stack([rho, rho * ux, rho * uy]).astype(np.float64)
+
+
 WORKLOADS = {
     "advection_1d": advection_1d,
     "burgers_1d": burgers_1d,
     "shallow_water_1d": shallow_water_1d,
     "euler_2d": euler_2d,
     "ns_obstacle_2d": ns_obstacle_2d,
+    "vortices_2d": vortices_2d,
 }

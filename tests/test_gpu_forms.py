@@ -30,6 +30,7 @@ def _l1(a, b):
     ("advection_1d", dict(max_level=9), 35),
     ("shallow_water_1d", dict(max_level=10), 40),
     ("euler_2d", dict(max_level=7), 20),
+    ("vortices_2d", dict(max_level=7), 20),
 ])
 def test_form_error_vs_fp64_oracle(form, name, kw, steps):
     from paper_2103_02903_gb300.binding import Solver
