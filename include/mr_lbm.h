@@ -220,6 +220,40 @@ const char* mr_lbm_strerror(mr_status s);
 mr_status mr_lbm_flattened_weights(int roots, int level, int max_level, int periodic, int k,
                                    double* out);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent solvers (any mix of schemes, levels, thresholds and
+ * forms) stepped together: every kernel of a time step runs once for all
+ * instances of the same scheme and storage form, whose uneven leaf counts
+ * are spread over the whole GPU, and the step is replayed from a CUDA graph
+ * in which instances of different schemes or forms are concurrent branches.
+ * The batch owns its instances; mr_lbm_batch_instance lends one as an
+ * ordinary handle for mr_lbm_init, mr_lbm_set_leaves, mr_lbm_get_leaves,
+ * mr_lbm_project, mr_lbm_stats and mr_lbm_counters.  mr_lbm_step,
+ * mr_lbm_adapt and mr_lbm_destroy refuse a lent handle with MR_ESTATE (the
+ * instances share one mesh parity). */
+typedef struct mr_lbm_batch* mr_lbm_batch_t;
+
+/* Create n solvers from cfgs[0..n-1] on the current device, all queued on
+ * `cuda_stream`.  Fails with the first failing instance's status. */
+mr_status mr_lbm_batch_create(const mr_lbm_config* cfgs, int n, void* cuda_stream, mr_lbm_batch_t* out);
+/* Borrow instance i (0 <= i < n, in the order of cfgs). */
+mr_status mr_lbm_batch_instance(mr_lbm_batch_t b, int i, mr_lbm_t* out);
+/* `nsteps` steps of Algorithm 1 for every instance (all must be
+ * initialised: MR_ESTATE otherwise).  Asynchronous. */
+mr_status mr_lbm_batch_step(mr_lbm_batch_t b, int nsteps);
+/* Wait and report the first deferred device-side error of any instance. */
+mr_status mr_lbm_batch_synchronize(mr_lbm_batch_t b);
+/* Sum of the instances' leaf updates; the number of steps taken. */
+mr_status mr_lbm_batch_counters(mr_lbm_batch_t b, long long* leaf_updates, long long* steps);
+/* Kernel launches queued by the batch's steps. */
+long long mr_lbm_batch_launch_count(mr_lbm_batch_t b);
+/* Event timing of one kernel group of the batched steps (groups as for
+ * mr_lbm_profile_enable). */
+mr_status mr_lbm_batch_profile_enable(mr_lbm_batch_t b, int group);
+mr_status mr_lbm_batch_profile_read(mr_lbm_batch_t b, double* total_ms, long long* launches);
+/* Release the batch and all its instances.  Accepts NULL. */
+mr_status mr_lbm_batch_destroy(mr_lbm_batch_t b);
+
 #ifdef __cplusplus
 }
 #endif

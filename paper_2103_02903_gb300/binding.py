@@ -87,10 +87,23 @@ def library():
         L.mr_lbm_strerror.argtypes = [i]
         L.mr_lbm_strerror.restype = C.c_char_p
         L.mr_lbm_flattened_weights.argtypes = [i, i, i, i, i, vp]
+        L.mr_lbm_batch_create.argtypes = [C.POINTER(MrConfig), i, vp, C.POINTER(vp)]
+        L.mr_lbm_batch_instance.argtypes = [vp, i, C.POINTER(vp)]
+        L.mr_lbm_batch_step.argtypes = [vp, i]
+        L.mr_lbm_batch_synchronize.argtypes = [vp]
+        L.mr_lbm_batch_counters.argtypes = [vp, C.POINTER(ll), C.POINTER(ll)]
+        L.mr_lbm_batch_launch_count.argtypes = [vp]
+        L.mr_lbm_batch_launch_count.restype = ll
+        L.mr_lbm_batch_profile_enable.argtypes = [vp, i]
+        L.mr_lbm_batch_profile_read.argtypes = [vp, C.POINTER(d), C.POINTER(ll)]
+        L.mr_lbm_batch_destroy.argtypes = [vp]
         for name in ("mr_lbm_create", "mr_lbm_destroy", "mr_lbm_init", "mr_lbm_step", "mr_lbm_adapt",
                      "mr_lbm_project", "mr_lbm_project_noalloc", "mr_lbm_get_leaves", "mr_lbm_set_leaves", "mr_lbm_stats",
                      "mr_lbm_counters", "mr_lbm_profile_enable", "mr_lbm_profile_read",
-                     "mr_lbm_synchronize", "mr_lbm_flattened_weights"):
+                     "mr_lbm_synchronize", "mr_lbm_flattened_weights", "mr_lbm_batch_create",
+                     "mr_lbm_batch_instance", "mr_lbm_batch_step", "mr_lbm_batch_synchronize",
+                     "mr_lbm_batch_counters", "mr_lbm_batch_profile_enable", "mr_lbm_batch_profile_read",
+                     "mr_lbm_batch_destroy"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -152,12 +165,16 @@ def flattened_weights(roots: int, level: int, max_level: int, periodic: bool, k:
 class Solver:
     """One adaptive MR-LBM simulation on the current CUDA device."""
 
-    def __init__(self, cfg: Dict, stream: Optional[int] = None, leaf_capacity: int = 0):
+    def __init__(self, cfg: Dict, stream: Optional[int] = None, leaf_capacity: int = 0, _borrowed=None):
         self.cfg = dict(cfg)
         self._c = make_config(cfg, leaf_capacity)
-        h = C.c_void_p()
-        _check(library().mr_lbm_create(C.byref(self._c), C.c_void_p(stream or 0), C.byref(h)),
-               "mr_lbm_create")
+        self._owned = _borrowed is None
+        if _borrowed is None:
+            h = C.c_void_p()
+            _check(library().mr_lbm_create(C.byref(self._c), C.c_void_p(stream or 0), C.byref(h)),
+                   "mr_lbm_create")
+        else:
+            h = _borrowed
         self.h = h
         sid = self._c.scheme
         self.d, self.Q, self.ncons = DIM[sid], NPOP[sid], NCONS[sid]
@@ -165,7 +182,8 @@ class Solver:
 
     def close(self):
         if getattr(self, "h", None):
-            library().mr_lbm_destroy(self.h)
+            if self._owned:
+                library().mr_lbm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -267,6 +285,62 @@ class Solver:
 
     def synchronize(self):
         _check(library().mr_lbm_synchronize(self.h), "mr_lbm_synchronize")
+
+
+class Batch:
+    """Many independent simulations stepped by shared launches
+    (mr_lbm_batch_*); ``instances[i]`` is a borrowed Solver for input,
+    output and statistics of configuration i."""
+
+    def __init__(self, cfgs, stream: Optional[int] = None):
+        n = len(cfgs)
+        arr = (MrConfig * n)(*[make_config(c) for c in cfgs])
+        b = C.c_void_p()
+        _check(library().mr_lbm_batch_create(arr, n, C.c_void_p(stream or 0), C.byref(b)), "mr_lbm_batch_create")
+        self.b = b
+        self.instances = []
+        for i, c in enumerate(cfgs):
+            h = C.c_void_p()
+            _check(library().mr_lbm_batch_instance(b, i, C.byref(h)), "mr_lbm_batch_instance")
+            self.instances.append(Solver(c, _borrowed=h))
+
+    def __len__(self):
+        return len(self.instances)
+
+    def step(self, n: int = 1):
+        _check(library().mr_lbm_batch_step(self.b, int(n)), "mr_lbm_batch_step")
+
+    def synchronize(self):
+        _check(library().mr_lbm_batch_synchronize(self.b), "mr_lbm_batch_synchronize")
+
+    def counters(self):
+        a, c = C.c_longlong(), C.c_longlong()
+        _check(library().mr_lbm_batch_counters(self.b, C.byref(a), C.byref(c)), "mr_lbm_batch_counters")
+        return a.value, c.value
+
+    def launch_count(self) -> int:
+        return int(library().mr_lbm_batch_launch_count(self.b))
+
+    def profile_enable(self, on=True):
+        _check(library().mr_lbm_batch_profile_enable(self.b, int(on)), "mr_lbm_batch_profile_enable")
+
+    def profile_read(self):
+        ms, n = C.c_double(), C.c_longlong()
+        _check(library().mr_lbm_batch_profile_read(self.b, C.byref(ms), C.byref(n)), "mr_lbm_batch_profile_read")
+        return ms.value, n.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            for s in self.instances:
+                s.h = None
+            library().mr_lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- keys

@@ -270,91 +270,141 @@ mr_status read_counts(mr_lbm* h, MeshCounts* out /*[2]*/) {
   return MR_OK;
 }
 
-cudaEvent_t next_event(mr_lbm* h) {
-  if (h->ev_used == h->ev_pool.size()) {
+// ----------------------------------------------------------------- groups
+void fill_desc(const mr_lbm* h, InstDev& d) {
+  memset(&d, 0, sizeof(d));
+  d.g = h->g;
+  d.mesh[0] = h->mesh[0];
+  d.mesh[1] = h->mesh[1];
+  d.fstate = h->fstate;
+  d.fscratch = h->fscratch;
+  d.flags = h->flags;
+  d.cls = h->cls;
+  d.bcounts = h->bcounts;
+  d.W = h->W;
+}
+
+// Write the handle's descriptor to its device slot (stream-ordered).
+bool upload_desc(mr_lbm* h) {
+  InstDev d;
+  fill_desc(h, d);
+  return cuda_ok(h, cudaMemcpyAsync(h->dinst, &d, sizeof(d), cudaMemcpyHostToDevice, h->st));
+}
+
+// Host summary of a group whose descriptors are at `dev`; chunk_pre[n + 1]
+// is written to `dchunk` on stream st.
+bool make_group(Group& G, const std::vector<const mr_lbm*>& members, const InstDev* dev, int* dchunk,
+                cudaStream_t st, int nsm) {
+  memset(&G, 0, sizeof(G));
+  G.dev = dev;
+  G.chunk_pre = dchunk;
+  G.n = (int)members.size();
+  G.nsm = nsm;
+  const Geo& g0 = members[0]->g;
+  G.d = g0.d;
+  G.Q = g0.Q;
+  G.scheme = g0.scheme;
+  G.form = g0.form;
+  std::vector<int> pre(G.n + 1, 0);
+  for (int b = 0; b < G.n; ++b) {
+    const Geo& g = members[b]->g;
+    const int chunks = (int)(g.base[g.J + 1] / MR_DENSE_ALIGN);
+    pre[b + 1] = pre[b] + chunks;
+    G.span = std::max(G.span, g.J - g.Jmin);
+    G.grade = G.grade || g.J > g.Jmin + 1;
+    G.capL += g.cap[0];
+    G.capI += g.cap[1];
+    for (int k = 1; k <= g.J - g.Jmin; ++k) {
+      G.proj_cells[k] += g.ncode[g.J - k];
+      G.pred_cells[k] += g.ncode[g.Jmin + k];
+    }
+  }
+  G.chunks = pre[G.n];
+  return cudaMemcpyAsync(dchunk, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+         cudaStreamSynchronize(st) == cudaSuccess;
+}
+
+// ----------------------------------------------------------------- execution
+cudaEvent_t next_event(Exec& x) {
+  if (x.ev_used == x.ev_pool.size()) {
     cudaEvent_t e;
     cudaEventCreate(&e);
-    h->ev_pool.push_back(e);
+    x.ev_pool.push_back(e);
   }
-  return h->ev_pool[h->ev_used++];
+  return x.ev_pool[x.ev_used++];
 }
 
-// Kernel groups that mr_lbm_profile_enable can time.
+// Kernel groups that the profile calls can time.
 enum { PG_STREAM = 1, PG_DETAILS = 2, PG_PROJECT = 3, PG_PREDICT = 4, PG_MESH = 5, PG_REMESH = 6 };
 
-inline void prof_begin(mr_lbm* h, int group) {
-  if (h->prof_group == group) cudaEventRecord(next_event(h), h->st);
+inline void prof_begin(Exec& x, int group) {
+  if (x.prof_group == group) cudaEventRecord(next_event(x), x.st);
 }
-inline void prof_end(mr_lbm* h, int group) {
-  if (h->prof_group == group) cudaEventRecord(next_event(h), h->st);
+inline void prof_end(Exec& x, int group) {
+  if (x.prof_group == group) cudaEventRecord(next_event(x), x.st);
 }
 
 // Encode of the current state: internal values, bottom-up (Def. Projection).
-void run_projection(mr_lbm* h, const MeshDev& A) {
-  for (int L = h->g.J - 1; L >= h->g.Jmin; --L) {
-    prof_begin(h, PG_PROJECT);
-    mr_launch_project(h->g, A, h->fstate, L, h->st, grid_for(h, 8));
-    prof_end(h, PG_PROJECT);
-    count_launch(h);
+void run_projection(Exec& x, const Group& G, int cur) {
+  for (int k = 1; k <= G.span; ++k) {
+    prof_begin(x, PG_PROJECT);
+    mr_launch_project(G, cur, k, x.st);
+    prof_end(x, PG_PROJECT);
+    x.launches += 1;
   }
 }
 
-// Build mesh `B` from the classification in h->cls (LEAF / INT bits).
-void run_build(mr_lbm* h, MeshDev& B) {
-  mr_launch_mark_ghosts(h->g, h->cls, h->st, grid_for(h));
-  mr_launch_compact(h->g, h->cls, h->flags, h->bcounts, B, h->st);
-  count_launch(h, 4);
+// Build mesh `dst` from the classification in cls (LEAF / INT bits).
+void run_build(Exec& x, const Group& G, int dst) {
+  mr_launch_mark_ghosts(G, x.st);
+  mr_launch_compact(G, dst, x.st);
+  x.launches += 4;
 }
 
-// Adaptation and data transfer; on return the new mesh is mesh[1-cur] and
-// its (pre-transport) leaf values are in h->fscratch.
-void run_adapt(mr_lbm* h) {
-  const Geo& g = h->g;
-  MeshDev& A = h->mesh[h->cur];
-  MeshDev& B = h->mesh[1 - h->cur];
-  run_projection(h, A);
-  prof_begin(h, PG_DETAILS);
-  mr_launch_details(g, A, h->fstate, h->st, grid_for(h, 8));
-  prof_end(h, PG_DETAILS);
-  prof_begin(h, PG_MESH);
-  mr_launch_flags_T(g, A, h->flags, h->st, grid_for(h));
-  mr_launch_flags_H(g, A, h->flags, h->st, grid_for(h));
-  mr_launch_grade(g, h->flags, A.cnt, h->st, grid_for(h));
-  mr_launch_classify(g, h->flags, h->cls, h->st, grid_for(h));
-  count_launch(h, g.J > g.Jmin + 1 ? 5 : 4);
-  run_build(h, B);
-  prof_end(h, PG_MESH);
-  prof_begin(h, PG_REMESH);
-  mr_launch_remesh_copy(g, A, h->fstate, B, h->fscratch, h->st, grid_for(h, 8));
-  prof_end(h, PG_REMESH);
-  count_launch(h);
-  for (int l = g.Jmin + 1; l <= g.J; ++l) {
-    prof_begin(h, PG_PREDICT);
-    mr_launch_predict_level(g, B, h->fscratch, l, h->st, grid_for(h, 8));
-    prof_end(h, PG_PREDICT);
-    count_launch(h);
+// Adaptation and data transfer; on return the new mesh is 1 - cur and its
+// (pre-transport) leaf values are in fscratch.
+void run_adapt(Exec& x, const Group& G, int cur) {
+  run_projection(x, G, cur);
+  prof_begin(x, PG_DETAILS);
+  mr_launch_details(G, cur, x.st);
+  prof_end(x, PG_DETAILS);
+  prof_begin(x, PG_MESH);
+  mr_launch_flags_T(G, cur, x.st);
+  mr_launch_flags_H(G, cur, x.st);
+  mr_launch_grade(G, x.st);
+  mr_launch_classify(G, x.st);
+  x.launches += G.grade ? 5 : 4;
+  run_build(x, G, 1 - cur);
+  prof_end(x, PG_MESH);
+  prof_begin(x, PG_REMESH);
+  mr_launch_remesh_copy(G, cur, x.st);
+  prof_end(x, PG_REMESH);
+  x.launches += 1;
+  for (int k = 1; k <= G.span; ++k) {
+    prof_begin(x, PG_PREDICT);
+    mr_launch_predict_level(G, 1 - cur, k, x.st);
+    prof_end(x, PG_PREDICT);
+    x.launches += 1;
   }
 }
 
-void run_stream(mr_lbm* h, const MeshDev& B, int do_stream, int do_collide) {
-  prof_begin(h, PG_STREAM);
-  mr_launch_stream_collide(h->g, B, h->fscratch, h->fstate, h->W, do_stream, do_collide, h->st,
-                           grid_for(h, 8));
-  prof_end(h, PG_STREAM);
-  count_launch(h);
+void run_stream(Exec& x, const Group& G, int dst, int do_stream, int do_collide) {
+  prof_begin(x, PG_STREAM);
+  mr_launch_stream_collide(G, dst, do_stream, do_collide, x.st);
+  prof_end(x, PG_STREAM);
+  x.launches += 1;
 }
 
-// One iteration of the loop of Algorithm 1 on the current stream.
-void run_step(mr_lbm* h) {
-  run_adapt(h);
-  MeshDev& B = h->mesh[1 - h->cur];
-  run_stream(h, B, 1, 1);
-  mr_launch_count_updates(B.cnt, h->st);
-  count_launch(h);
+// One iteration of the loop of Algorithm 1 for every instance of a group.
+void run_step(Exec& x, const Group& G, int cur) {
+  run_adapt(x, G, cur);
+  run_stream(x, G, 1 - cur, 1, 1);
+  mr_launch_count_updates(G, 1 - cur, x.st);
+  x.launches += 1;
 }
 
-void drop_graphs(mr_lbm* h) {
-  for (auto& G : h->graphs) {
+void drop_graphs(Exec& x) {
+  for (auto& G : x.graphs) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
     if (G.graph) cudaGraphDestroy(G.graph);
     G.exec = nullptr;
@@ -364,31 +414,33 @@ void drop_graphs(mr_lbm* h) {
   }
 }
 
-// Capture run_step() for the current mesh parity into h->graphs[h->cur].
-bool capture_step(mr_lbm* h) {
-  mr_lbm::StepGraph& G = h->graphs[h->cur];
-  if (!h->cap_st && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) return false;
-  while (h->ev_pool.size() < h->ev_used + 64) {  // events are created outside the capture
+// Capture `body` (the launches of one step on x.st) for the current mesh
+// parity into x.graphs[x.cur].
+template <class Body>
+bool capture_step(Exec& x, Body body) {
+  StepGraph& G = x.graphs[x.cur];
+  if (!x.cap_st && cudaStreamCreateWithFlags(&x.cap_st, cudaStreamNonBlocking) != cudaSuccess) return false;
+  while (x.ev_pool.size() < x.ev_used + 64) {  // events are created outside the capture
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return false;
-    h->ev_pool.push_back(e);
+    x.ev_pool.push_back(e);
   }
-  const size_t ev0 = h->ev_used;
-  const long long l0 = h->launches;
-  cudaStream_t orig = h->st;
-  h->st = h->cap_st;
-  if (cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    h->st = orig;
+  const size_t ev0 = x.ev_used;
+  const long long l0 = x.launches;
+  cudaStream_t orig = x.st;
+  x.st = x.cap_st;
+  if (cudaStreamBeginCapture(x.cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    x.st = orig;
     return false;
   }
-  run_step(h);
+  body();
   cudaGraph_t graph = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(h->cap_st, &graph);
-  h->st = orig;
-  std::vector<cudaEvent_t> cap_events(h->ev_pool.begin() + ev0, h->ev_pool.begin() + h->ev_used);
-  h->ev_used = ev0;
-  G.launches = h->launches - l0;
-  h->launches = l0;
+  const cudaError_t e = cudaStreamEndCapture(x.cap_st, &graph);
+  x.st = orig;
+  std::vector<cudaEvent_t> cap_events(x.ev_pool.begin() + ev0, x.ev_pool.begin() + x.ev_used);
+  x.ev_used = ev0;
+  G.launches = x.launches - l0;
+  x.launches = l0;
   if (e != cudaSuccess || !graph) return false;
   size_t n = 0;
   cudaGraphGetNodes(graph, nullptr, &n);
@@ -414,26 +466,40 @@ bool capture_step(mr_lbm* h) {
     return false;
   }
   G.graph = graph;
-  G.prof = h->prof_group;
+  G.prof = x.prof_group;
   return true;
 }
 
 // One step by graph replay (captured on first use for this parity and
 // profiling mode); false if graphs cannot be used, and nothing was queued.
-bool graph_step(mr_lbm* h) {
-  mr_lbm::StepGraph& G = h->graphs[h->cur];
-  if (G.exec && G.prof != h->prof_group) {
+template <class Body>
+bool graph_step(Exec& x, Body body) {
+  StepGraph& G = x.graphs[x.cur];
+  if (G.exec && G.prof != x.prof_group) {
     cudaGraphExecDestroy(G.exec);
     cudaGraphDestroy(G.graph);
     G.exec = nullptr;
     G.graph = nullptr;
   }
-  if (!G.exec && !capture_step(h)) return false;
+  if (!G.exec && !capture_step(x, body)) return false;
   for (cudaGraphNode_t nd : G.ev_nodes)
-    if (cudaGraphExecEventRecordNodeSetEvent(G.exec, nd, next_event(h)) != cudaSuccess) return false;
-  if (cudaGraphLaunch(G.exec, h->st) != cudaSuccess) return false;
-  h->launches += G.launches;
+    if (cudaGraphExecEventRecordNodeSetEvent(G.exec, nd, next_event(x)) != cudaSuccess) return false;
+  if (cudaGraphLaunch(G.exec, x.st) != cudaSuccess) return false;
+  x.launches += G.launches;
   return true;
+}
+
+// `nsteps` steps queued on x (graph replay, or direct launches when graphs
+// are unavailable); x.cur flips after each.
+template <class Body>
+void queue_steps(Exec& x, int nsteps, Body body) {
+  for (int it = 0; it < nsteps; ++it) {
+    if (!(x.use_graph && graph_step(x, body))) {
+      x.use_graph = false;  // graphs unavailable: launch the kernels directly from now on
+      body();
+    }
+    x.cur = 1 - x.cur;
+  }
 }
 
 mr_status ensure_staging(mr_lbm* h, size_t bytes) {
@@ -446,10 +512,21 @@ mr_status ensure_staging(mr_lbm* h, size_t bytes) {
   return MR_OK;
 }
 
+double profile_total(Exec& x, long long* launches) {
+  double tot = 0;
+  for (size_t i = 0; i + 1 < x.ev_used; i += 2) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, x.ev_pool[i], x.ev_pool[i + 1]) != cudaSuccess) return -1.0;
+    tot += ms;
+  }
+  if (launches) *launches = (long long)(x.ev_used / 2);
+  return tot;
+}
+
 }  // namespace
 
 mr_status mr_handle_fail(mr_lbm* h, mr_status s) { return fail(h, s); }
-void mr_handle_projection(mr_lbm* h) { run_projection(h, h->mesh[h->cur]); }
+void mr_handle_projection(mr_lbm* h) { run_projection(*h, h->grp, h->cur); }
 mr_status mr_handle_read_counts(mr_lbm* h, MeshCounts* out) { return read_counts(h, out); }
 
 // =================================================================== C-ABI
@@ -586,9 +663,15 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   std::vector<double> W;
   build_tables(g, W);
   ok = ok && dalloc(h, &h->W, W.size());
+  int* dchunk = nullptr;
+  ok = ok && dalloc(h, &h->dinst, 1) && dalloc(h, &dchunk, 2);
   if (!ok) {
     mr_lbm_destroy(h);
     return MR_ENOMEM;
+  }
+  if (!make_group(h->grp, {h}, h->dinst, dchunk, h->st, h->nsm) || !upload_desc(h)) {
+    mr_lbm_destroy(h);
+    return MR_ECUDA;
   }
   bool cok = cudaMemsetAsync(h->cntbuf, 0, 2 * sizeof(MeshCounts), h->st) == cudaSuccess &&
              cudaMemsetAsync(h->flags, 0, dense, h->st) == cudaSuccess &&
@@ -607,10 +690,25 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   return MR_OK;
 }
 
+static void destroy_handle_impl(mr_lbm_t h);
+static mr_status init_impl(mr_lbm_t h, const double* conserved, int on_device);
+
 mr_status mr_lbm_destroy(mr_lbm_t h) {
   if (!h) return MR_OK;
+  if (h->batch) return MR_ESTATE;  // owned by its batch
+  destroy_handle_impl(h);
+  return MR_OK;
+}
+
+mr_status mr_lbm_init(mr_lbm_t h, const double* conserved, int on_device) {
+  if (!h || !conserved) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  return init_impl(h, conserved, on_device);
+}
+
+static void destroy_handle_impl(mr_lbm_t h) {
   cudaStreamSynchronize(h->st);
-  drop_graphs(h);
+  drop_graphs(*h);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   for (void* p : h->allocs) cudaFree(p);
   if (h->staging) cudaFree(h->staging);
@@ -618,12 +716,9 @@ mr_status mr_lbm_destroy(mr_lbm_t h) {
     if (h->dense[i]) cudaFree(h->dense[i]);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
-  return MR_OK;
 }
 
-mr_status mr_lbm_init(mr_lbm_t h, const double* conserved, int on_device) {
-  if (!h || !conserved) return MR_EINVAL;
-  if (h->sticky != MR_OK) return h->sticky;
+static mr_status init_impl(mr_lbm_t h, const double* conserved, int on_device) {
   const Geo& g = h->g;
   const size_t bytes = (size_t)g.ncons * g.ncode[g.J] * sizeof(double);
   const double* src = conserved;
@@ -645,7 +740,7 @@ mr_status mr_lbm_init(mr_lbm_t h, const double* conserved, int on_device) {
       u[k] = s / (double)N;
     }
     host_equilibrium(h->g, u, h->g.off);
-    drop_graphs(h);
+    if (!upload_desc(h)) return MR_ECUDA;
   }
   if (!on_device) {
     if (ensure_staging(h, bytes) != MR_OK) return h->sticky;
@@ -656,7 +751,7 @@ mr_status mr_lbm_init(mr_lbm_t h, const double* conserved, int on_device) {
   MeshDev& B = h->mesh[h->cur];
   mr_launch_full_mesh(g, h->cls, h->st, grid_for(h));
   count_launch(h);
-  run_build(h, B);
+  run_build(*h, h->grp, h->cur);
   mr_launch_init_eq(g, B, src, h->fstate, h->st, grid_for(h));
   count_launch(h);
   if (check_launch(h) != MR_OK) return h->sticky;
@@ -668,24 +763,20 @@ mr_status mr_lbm_init(mr_lbm_t h, const double* conserved, int on_device) {
 mr_status mr_lbm_step(mr_lbm_t h, int nsteps) {
   if (!h || nsteps < 0) return MR_EINVAL;
   if (h->sticky != MR_OK) return h->sticky;
+  if (h->batch) return MR_ESTATE;  // the batch steps its instances
   if (!h->initialized) return fail(h, MR_ESTATE);
-  for (int it = 0; it < nsteps; ++it) {
-    if (!(h->use_graph && graph_step(h))) {
-      h->use_graph = false;  // graphs unavailable: launch the kernels directly from now on
-      run_step(h);
-    }
-    h->cur = 1 - h->cur;
-  }
+  queue_steps(*h, nsteps, [h]() { run_step(*h, h->grp, h->cur); });
   return check_launch(h);
 }
 
 mr_status mr_lbm_adapt(mr_lbm_t h) {
   if (!h) return MR_EINVAL;
   if (h->sticky != MR_OK) return h->sticky;
+  if (h->batch) return MR_ESTATE;  // the batch steps its instances
   if (!h->initialized) return fail(h, MR_ESTATE);
-  run_adapt(h);
+  run_adapt(*h, h->grp, h->cur);
   std::swap(h->fstate, h->fscratch);
-  drop_graphs(h);  // captured steps refer to the swapped buffers
+  if (!upload_desc(h)) return MR_ECUDA;  // the kernels read the buffers from the descriptor
   h->cur = 1 - h->cur;
   return check_launch(h);
 }
@@ -706,7 +797,7 @@ mr_status mr_lbm_project(mr_lbm_t h, int level, double* out, int on_device) {
     h->dense_elems = need;
   }
   const MeshDev& A = h->mesh[h->cur];
-  run_projection(h, A);
+  run_projection(*h, h->grp, h->cur);
   int pb = 0;
   for (int l = g.Jmin; l <= level; ++l) {
     mr_launch_project_dense(g, A, h->fstate, l, h->dense[pb], h->dense[1 - pb], h->st, grid_for(h));
@@ -784,7 +875,7 @@ mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* k
       for (long long i = 0; i < n; ++i) s += fp[(size_t)p * n + i];
       h->g.off[p] = s / (double)n;
     }
-    drop_graphs(h);
+    if (!upload_desc(h)) return MR_ECUDA;
   }
   const unsigned long long* dk = keys;
   const signed char* dl = levels;
@@ -813,7 +904,7 @@ mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* k
   if (s != MR_OK) return s;
   unsigned long long full = g.ncode[g.J];
   if (vol != full) return fail(h, MR_EINVAL);
-  run_build(h, B);
+  run_build(*h, h->grp, h->cur);
   mr_launch_gather_input(g, B, h->inidx, n, df, h->fstate, h->st, grid_for(h));
   count_launch(h);
   // reset the input index map for the next call
@@ -869,14 +960,9 @@ mr_status mr_lbm_profile_enable(mr_lbm_t h, int on) {
 mr_status mr_lbm_profile_read(mr_lbm_t h, double* total_ms, long long* launches) {
   if (!h) return MR_EINVAL;
   if (!cuda_ok(h, cudaStreamSynchronize(h->st))) return MR_ECUDA;
-  double tot = 0;
-  for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, h->ev_pool[i], h->ev_pool[i + 1]) != cudaSuccess) return fail(h, MR_ECUDA);
-    tot += ms;
-  }
+  const double tot = profile_total(*h, launches);
+  if (tot < 0) return fail(h, MR_ECUDA);
   if (total_ms) *total_ms = tot;
-  if (launches) *launches = (long long)(h->ev_used / 2);
   return MR_OK;
 }
 
@@ -885,6 +971,196 @@ mr_status mr_lbm_synchronize(mr_lbm_t h) {
   if (h->sticky != MR_OK) return h->sticky;
   MeshCounts hc[2];
   return read_counts(h, hc);
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- batches
+struct mr_lbm_batch : Exec {
+  std::vector<mr_lbm*> inst;  // in the caller's order
+  struct Part {               // instances of one scheme and form, contiguous in descs
+    Group G;
+    int* chunk_pre = nullptr;
+    cudaStream_t side = nullptr;  // branch stream of the parts after the first
+    cudaEvent_t done = nullptr;
+  };
+  std::vector<Part> parts;
+  InstDev* descs = nullptr;
+  cudaEvent_t fork = nullptr;
+  mr_status sticky = MR_OK;
+};
+
+namespace {
+
+// One step of every instance: one chain of launches per part, the parts
+// after the first on branch streams forked from and joined to b->st.
+void run_batch_step(mr_lbm_batch* b) {
+  const int cur = b->cur;
+  cudaStream_t main = b->st;
+  const size_t np = b->parts.size();
+  if (np > 1) {
+    cudaEventRecord(b->fork, main);
+    for (size_t p = 1; p < np; ++p) cudaStreamWaitEvent(b->parts[p].side, b->fork, 0);
+  }
+  for (size_t p = 0; p < np; ++p) {
+    b->st = p == 0 ? main : b->parts[p].side;
+    run_step(*b, b->parts[p].G, cur);
+  }
+  b->st = main;
+  for (size_t p = 1; p < np; ++p) {
+    cudaEventRecord(b->parts[p].done, b->parts[p].side);
+    cudaStreamWaitEvent(main, b->parts[p].done, 0);
+  }
+}
+
+void free_batch(mr_lbm_batch* b) {
+  if (b->st) cudaStreamSynchronize(b->st);
+  drop_graphs(*b);
+  if (b->cap_st) cudaStreamDestroy(b->cap_st);
+  for (auto& p : b->parts) {
+    if (p.side) cudaStreamDestroy(p.side);
+    if (p.done) cudaEventDestroy(p.done);
+    if (p.chunk_pre) cudaFree(p.chunk_pre);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (mr_lbm* h : b->inst)
+    if (h) {
+      h->batch = nullptr;
+      destroy_handle_impl(h);
+    }
+  if (b->descs) cudaFree(b->descs);
+  for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+mr_status mr_lbm_batch_create(const mr_lbm_config* cfgs, int n, void* cuda_stream, mr_lbm_batch_t* out) {
+  if (!out) return MR_EINVAL;
+  *out = nullptr;
+  if (!cfgs || n <= 0) return MR_EINVAL;
+  mr_lbm_batch* b = new (std::nothrow) mr_lbm_batch();
+  if (!b) return MR_ENOMEM;
+  b->st = (cudaStream_t)cuda_stream;
+  b->inst.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    const mr_status s = mr_lbm_create(&cfgs[i], cuda_stream, &b->inst[i]);
+    if (s != MR_OK) {
+      free_batch(b);
+      return s;
+    }
+  }
+  b->nsm = b->inst[0]->nsm;
+  // parts: instances of one scheme and storage form, at most MR_MAXB each
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto key = [&](int i) { return b->inst[i]->g.scheme * 16 + b->inst[i]->g.form; };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
+  if (cudaMalloc(&b->descs, sizeof(InstDev) * n) != cudaSuccess) {
+    free_batch(b);
+    return MR_ENOMEM;
+  }
+  bool ok = true;
+  for (int s = 0; s < n && ok;) {
+    int e = s + 1;
+    while (e < n && e - s < MR_MAXB && key(order[e]) == key(order[s])) ++e;
+    mr_lbm_batch::Part part;
+    std::vector<const mr_lbm*> members;
+    for (int k = s; k < e; ++k) {
+      mr_lbm* h = b->inst[order[k]];
+      h->batch = b;
+      h->dinst = b->descs + k;
+      h->grp.dev = h->dinst;
+      ok = ok && upload_desc(h);
+      members.push_back(h);
+    }
+    ok = ok && cudaMalloc(&part.chunk_pre, sizeof(int) * (e - s + 1)) == cudaSuccess &&
+         make_group(part.G, members, b->descs + s, part.chunk_pre, b->st, b->nsm);
+    if (ok && !b->parts.empty())
+      ok = cudaStreamCreateWithFlags(&part.side, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&part.done, cudaEventDisableTiming) == cudaSuccess;
+    b->parts.push_back(part);
+    s = e;
+  }
+  ok = ok && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+       cudaStreamSynchronize(b->st) == cudaSuccess;
+  if (!ok) {
+    free_batch(b);
+    return MR_ECUDA;
+  }
+  *out = b;
+  return MR_OK;
+}
+
+mr_status mr_lbm_batch_instance(mr_lbm_batch_t b, int i, mr_lbm_t* out) {
+  if (!b || !out || i < 0 || i >= (int)b->inst.size()) return MR_EINVAL;
+  *out = b->inst[i];
+  return MR_OK;
+}
+
+mr_status mr_lbm_batch_step(mr_lbm_batch_t b, int nsteps) {
+  if (!b || nsteps < 0) return MR_EINVAL;
+  if (b->sticky != MR_OK) return b->sticky;
+  for (mr_lbm* h : b->inst) {
+    if (h->sticky != MR_OK) return h->sticky;
+    if (!h->initialized || h->cur != b->cur) return MR_ESTATE;
+  }
+  queue_steps(*b, nsteps, [b]() { run_batch_step(b); });
+  for (mr_lbm* h : b->inst) h->cur = b->cur;
+  if (cudaGetLastError() != cudaSuccess) b->sticky = MR_ECUDA;
+  return b->sticky;
+}
+
+mr_status mr_lbm_batch_synchronize(mr_lbm_batch_t b) {
+  if (!b) return MR_EINVAL;
+  if (b->sticky != MR_OK) return b->sticky;
+  mr_status first = MR_OK;
+  for (mr_lbm* h : b->inst) {
+    const mr_status s = mr_lbm_synchronize(h);
+    if (first == MR_OK) first = s;
+  }
+  return first;
+}
+
+mr_status mr_lbm_batch_counters(mr_lbm_batch_t b, long long* leaf_updates, long long* steps) {
+  if (!b) return MR_EINVAL;
+  long long lu = 0, st = 0;
+  for (mr_lbm* h : b->inst) {
+    long long a = 0, c = 0;
+    const mr_status s = mr_lbm_counters(h, &a, &c);
+    if (s != MR_OK) return s;
+    lu += a;
+    st = std::max(st, c);
+  }
+  if (leaf_updates) *leaf_updates = lu;
+  if (steps) *steps = st;
+  return MR_OK;
+}
+
+long long mr_lbm_batch_launch_count(mr_lbm_batch_t b) { return b ? b->launches : 0; }
+
+mr_status mr_lbm_batch_profile_enable(mr_lbm_batch_t b, int on) {
+  if (!b || on < 0 || on > 6) return MR_EINVAL;
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return MR_ECUDA;
+  b->prof_group = on;
+  b->ev_used = 0;
+  return MR_OK;
+}
+
+mr_status mr_lbm_batch_profile_read(mr_lbm_batch_t b, double* total_ms, long long* launches) {
+  if (!b) return MR_EINVAL;
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return MR_ECUDA;
+  const double tot = profile_total(*b, launches);
+  if (tot < 0) return MR_ECUDA;
+  if (total_ms) *total_ms = tot;
+  return MR_OK;
+}
+
+mr_status mr_lbm_batch_destroy(mr_lbm_batch_t b) {
+  if (b) free_batch(b);
+  return MR_OK;
 }
 
 }  // extern "C"

@@ -115,12 +115,12 @@ __device__ __forceinline__ int mr_level_of(const Geo& g, uint32_t gi) {
 }
 
 // Dense kernels run one block of 256 threads per 1024-cell chunk of the dense
-// index space, starting at chunk `chunk0`.  Every level starts on a chunk
+// index space; CHUNK is the block's chunk.  Every level starts on a chunk
 // boundary, so a block finds its level once; the body sees the level L, the
 // code C and the dense index GI of each valid cell of the chunk.
-#define MR_DENSE_CHUNK_BEGIN(g, chunk0, L, C, GI)                              \
+#define MR_DENSE_CHUNK_BEGIN(g, CHUNK, L, C, GI)                               \
   {                                                                           \
-    const uint32_t mr_chunk_ = (chunk0) + blockIdx.x;                         \
+    const uint32_t mr_chunk_ = (CHUNK);                                       \
     const int L = mr_level_of(g, mr_chunk_ * MR_DENSE_ALIGN);                 \
     const uint32_t mr_cb_ = mr_chunk_ * MR_DENSE_ALIGN - (g).base[L];         \
     for (int mr_k_ = 0; mr_k_ < (int)(MR_DENSE_ALIGN / 256u); ++mr_k_) {      \
@@ -130,6 +130,90 @@ __device__ __forceinline__ int mr_level_of(const Geo& g, uint32_t gi) {
 #define MR_DENSE_CHUNK_END \
   }                        \
   }
+
+// ------------------------------------------------------------------ groups
+// A step kernel runs one phase for every instance of a group.  The phase's
+// work in instance b is count(b) passes of the block ("tiles"); the tiles of
+// all instances are numbered in instance order and the blocks stride over
+// them, so the work of uneven instances is spread over the whole grid.
+// pre (shared, n + 1 ints) receives the first tile of every instance; the
+// return value is the number of tiles.  Block-wide: every thread calls it.
+template <class CountF>
+__device__ __forceinline__ int mr_group_prefix(int* pre, int n, CountF count) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  if (n == 1) {
+    if (tid == 0) {
+      pre[0] = 0;
+      pre[1] = count(0);
+    }
+    __syncthreads();
+    return pre[1];
+  }
+  for (int b = tid; b < n; b += nt) pre[b + 1] = count(b);
+  __syncthreads();
+  if (tid < 32) {
+    // each lane scans a run of entries, then the runs are offset by a warp scan
+    const int per = (n + 31) / 32, lo = 1 + tid * per, hi = min(lo + per, n + 1);
+    int s = 0;
+    for (int b = lo; b < hi; ++b) s += pre[b];
+    int x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (tid >= o) x += y;
+    }
+    int run = x - s;
+    for (int b = lo; b < hi; ++b) {
+      run += pre[b];
+      pre[b] = run;
+    }
+    if (tid == 0) pre[0] = 0;
+  }
+  __syncthreads();
+  return pre[n];
+}
+
+// instance of tile t: the largest b with pre[b] <= t
+__device__ __forceinline__ int mr_group_find(const int* pre, int n, int t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// The block's shared copy of the descriptor of instance b (b block-uniform);
+// `have` is the instance currently held (-1 before the first).
+__device__ __forceinline__ void mr_inst_use(InstDev& si, int& have, const InstDev* __restrict__ IB, int b) {
+  if (have == b) return;
+  __syncthreads();
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int4* s = reinterpret_cast<const int4*>(IB + b);
+  int4* d = reinterpret_cast<int4*>(&si);
+  for (int k = tid; k < (int)(sizeof(InstDev) / sizeof(int4)); k += nt) d[k] = __ldg(s + k);
+  __syncthreads();
+  have = b;
+}
+
+// Dense kernels: instance and chunk of this block, from the group's chunk
+// prefix (one block per dense chunk of every instance).
+__device__ __forceinline__ int mr_group_chunk(const int* __restrict__ chunk_pre, int n, int& chunk) {
+  int lo = 0, hi = n - 1;
+  const int t = (int)blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(chunk_pre + mid) <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  chunk = t - __ldg(chunk_pre + lo);
+  return lo;
+}
 
 // Canonical s = 1 prediction of child ci from a 3^D stencil (x fastest),
 // evaluated in the order written in Sec. 4.1 with no fused multiply-add:

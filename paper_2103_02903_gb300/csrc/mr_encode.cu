@@ -24,13 +24,30 @@ struct PopRows {
 };
 
 template <int D, int Q, int F>
-__global__ void __launch_bounds__(256) k_project(Geo g, MeshDev A, const void* __restrict__ LF, int level) {
+__global__ void __launch_bounds__(256) k_project(const InstDev* __restrict__ IB, int n, int cur, int k) {
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
-  const int begin = A.cnt->off[MR_CLS_INT][level], end = A.cnt->off[MR_CLS_INT][level + 1];
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  const int tiles = mr_group_prefix(pre, n, [&](int b) {
+    const InstDev& I = IB[b];
+    const int L = I.g.J - k;
+    if (L < I.g.Jmin) return 0;
+    const MeshCounts* c = I.mesh[cur].cnt;
+    return (c->off[MR_CLS_INT][L + 1] - c->off[MR_CLS_INT][L] + 31) / 32;
+  });
   const double scale = D == 1 ? 0.5 : 0.25;
-  S* IF = (S*)A.IF;
-  for (int i = begin + blockIdx.x * 32 + threadIdx.x; i < end; i += gridDim.x * 32) {
+  int have = -1;
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int b = mr_group_find(pre, n, t);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    const MeshDev& A = si.mesh[cur];
+    const int level = g.J - k;
+    const int i = A.cnt->off[MR_CLS_INT][level] + (t - pre[b]) * 32 + threadIdx.x;
+    if (i >= A.cnt->off[MR_CLS_INT][level + 1]) continue;
+    const void* LF = si.fstate;
+    S* IF = (S*)A.IF;
     const uint32_t code = A.code[MR_CLS_INT][i];
     ValPtr<S> ch[1 << D];
     bool ok = true;
@@ -55,15 +72,24 @@ __global__ void __launch_bounds__(256) k_project(Geo g, MeshDev A, const void* _
 }
 
 template <int D, int Q, int F>
-__global__ void __launch_bounds__(256) k_details(Geo g, MeshDev A, const void* __restrict__ LF) {
+__global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB, int n, int cur) {
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
   __shared__ double red[PY][32];
-  const int n = A.cnt->total[MR_CLS_INT];
-  for (int i0 = blockIdx.x * 32; i0 < n; i0 += gridDim.x * 32) {  // uniform over the block
-    const int i = i0 + threadIdx.x;
+  const int tiles = mr_group_prefix(pre, n, [&](int b) { return (IB[b].mesh[cur].cnt->total[MR_CLS_INT] + 31) / 32; });
+  int have = -1;
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {  // uniform over the block
+    const int b = mr_group_find(pre, n, t);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    const MeshDev& A = si.mesh[cur];
+    const void* LF = si.fstate;
+    const int nI = A.cnt->total[MR_CLS_INT];
+    const int i = (t - pre[b]) * 32 + threadIdx.x;
     double gmax = 0.0;
-    if (i < n) {
+    if (i < nI) {
       const int L = A.lvl[MR_CLS_INT][i];
       const uint32_t code = A.code[MR_CLS_INT][i];
       int x, y;
@@ -72,9 +98,9 @@ __global__ void __launch_bounds__(256) k_details(Geo g, MeshDev A, const void* _
       bool ok = mr_stencil_entries<D>(g, A, L, x, y, st);
       ValPtr<S> sv[D == 2 ? 9 : 3], cv[1 << D];
 #pragma unroll
-      for (int k = 0; k < (D == 2 ? 9 : 3); ++k) {
-        ok = ok && (((uint32_t)st[k]) >> 30) <= MR_CLS_INT;
-        sv[k] = mr_resolve<S>(g, A, LF, st[k]);
+      for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) {
+        ok = ok && (((uint32_t)st[kk]) >> 30) <= MR_CLS_INT;
+        sv[kk] = mr_resolve<S>(g, A, LF, st[kk]);
       }
 #pragma unroll
       for (int ci = 0; ci < (1 << D); ++ci) {
@@ -89,7 +115,7 @@ __global__ void __launch_bounds__(256) k_details(Geo g, MeshDev A, const void* _
         for (int p = threadIdx.y; p < Q; p += PY) {
           double v[D == 2 ? 9 : 3], c[1 << D];
 #pragma unroll
-          for (int k = 0; k < (D == 2 ? 9 : 3); ++k) v[k] = mr_ld(sv[k], p);
+          for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) v[kk] = mr_ld(sv[kk], p);
 #pragma unroll
           for (int ci = 0; ci < (1 << D); ++ci) c[ci] = mr_ld(cv[ci], p);
 #pragma unroll
@@ -102,31 +128,31 @@ __global__ void __launch_bounds__(256) k_details(Geo g, MeshDev A, const void* _
     }
     red[threadIdx.y][threadIdx.x] = gmax;
     __syncthreads();
-    if (threadIdx.y == 0 && i < n) {
+    if (threadIdx.y == 0 && i < nI) {
       double m = red[0][threadIdx.x];
 #pragma unroll
-      for (int k = 1; k < PY; ++k) m = fmax(m, red[k][threadIdx.x]);
+      for (int kk = 1; kk < PY; ++kk) m = fmax(m, red[kk][threadIdx.x]);
       A.G[i] = m;
     }
     __syncthreads();
   }
 }
 
-// `grid` is the maximum number of blocks; a block covers 32 cells.
 template <int D, int Q, int F>
-void launch_project_t(const Geo& g, const MeshDev& A, const void* LF, int level, cudaStream_t st, int grid) {
-  const int need = (int)((g.ncode[level] + 31) / 32);
-  k_project<D, Q, F><<<need < grid ? need : grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LF, level);
+void launch_project_t(const Group& G, int cur, int k, cudaStream_t st) {
+  k_project<D, Q, F><<<mr_tile_grid(G, G.proj_cells[k], 32, 8), dim3(32, PopRows<Q>::value), mr_pre_bytes(G), st>>>(G.dev, G.n,
+                                                                                                    cur, k);
 }
 template <int D, int Q, int F>
-void launch_details_t(const Geo& g, const MeshDev& A, const void* LF, cudaStream_t st, int grid) {
-  k_details<D, Q, F><<<grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LF);
+void launch_details_t(const Group& G, int cur, cudaStream_t st) {
+  k_details<D, Q, F><<<mr_tile_grid(G, G.capI, 32, 8), dim3(32, PopRows<Q>::value), mr_pre_bytes(G), st>>>(G.dev, G.n,
+                                                                                                    cur);
 }
 
 }  // namespace
 
 #define MR_DISPATCH_F(FN, D, Q, ...)                       \
-  switch (g.form) {                                        \
+  switch (G.form) {                                        \
     case MR_FORM_F64: FN<D, Q, MR_FORM_F64>(__VA_ARGS__); break;       \
     case MR_FORM_F32: FN<D, Q, MR_FORM_F32>(__VA_ARGS__); break;       \
     case MR_FORM_F32_F16: FN<D, Q, MR_FORM_F32_F16>(__VA_ARGS__); break; \
@@ -134,7 +160,7 @@ void launch_details_t(const Geo& g, const MeshDev& A, const void* LF, cudaStream
   }
 
 #define MR_DISPATCH_DQF(FN, ...)                                  \
-  switch (g.d * 100 + g.Q) {                                      \
+  switch (G.d * 100 + G.Q) {                                      \
     case 102: MR_DISPATCH_F(FN, 1, 2, __VA_ARGS__); break;        \
     case 103: MR_DISPATCH_F(FN, 1, 3, __VA_ARGS__); break;        \
     case 209: MR_DISPATCH_F(FN, 2, 9, __VA_ARGS__); break;        \
@@ -142,10 +168,8 @@ void launch_details_t(const Geo& g, const MeshDev& A, const void* LF, cudaStream
     default: break;                                               \
   }
 
-void mr_launch_project(const Geo& g, const MeshDev& A, const void* LF, int level, cudaStream_t st, int grid) {
-  MR_DISPATCH_DQF(launch_project_t, g, A, LF, level, st, grid);
+void mr_launch_project(const Group& G, int cur, int k, cudaStream_t st) {
+  MR_DISPATCH_DQF(launch_project_t, G, cur, k, st);
 }
 
-void mr_launch_details(const Geo& g, const MeshDev& A, const void* LF, cudaStream_t st, int grid) {
-  MR_DISPATCH_DQF(launch_details_t, g, A, LF, st, grid);
-}
+void mr_launch_details(const Group& G, int cur, cudaStream_t st) { MR_DISPATCH_DQF(launch_details_t, G, cur, st); }

@@ -1,4 +1,4 @@
-// Handle of the C-ABI (private to the library's translation units) and the
+// Handles of the C-ABI (private to the library's translation units) and the
 // host-side helpers that more than one of them uses.
 #pragma once
 
@@ -9,13 +9,39 @@
 #include "../../include/mr_lbm.h"
 #include "mr_internal.cuh"
 
-struct mr_lbm {
-  Geo g;
+// One time step captured as a CUDA graph per mesh parity (the two meshes
+// alternate), replayed by the step calls; the event-record nodes of a
+// profiled kernel group are pointed at fresh events before each replay.
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  int prof = -1;
+  long long launches = 0;
+  std::vector<cudaGraphNode_t> ev_nodes;
+  cudaGraph_t graph = nullptr;
+};
+
+// What queues time steps: a stream, the parity of the current mesh, the
+// captured graphs, launch counting and the optional event timing of one
+// kernel group.  A solver and a batch of solvers are both executors.
+struct Exec {
   cudaStream_t st = nullptr;
   int nsm = 152;
+  int cur = 0;
+  long long launches = 0;
+  int prof_group = 0;  // 0 = off, else the kernel group timed with events
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  StepGraph graphs[2];
+  bool use_graph = true;
+  cudaStream_t cap_st = nullptr;
+};
+
+struct mr_lbm_batch;
+
+struct mr_lbm : Exec {
+  Geo g;
   MeshDev mesh[2];
   MeshCounts* cntbuf = nullptr;  // two MeshCounts
-  int cur = 0;
   void* fstate = nullptr;    // leaf populations [Q][cap_leaf], storage type of the form
   void* fscratch = nullptr;  // pre-transport leaf populations, same layout
   uint8_t* flags = nullptr;
@@ -30,23 +56,13 @@ struct mr_lbm {
   size_t staging_bytes = 0;
   bool initialized = false;
   mr_status sticky = MR_OK;
-  long long launches = 0;
-  int prof_group = 0;  // 0 = off, else the kernel group timed with events
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_used = 0;
   std::vector<void*> allocs;
-  // One time step captured as a CUDA graph per mesh parity (the two meshes
-  // alternate), replayed by mr_lbm_step; the event-record nodes of a
-  // profiled kernel group are pointed at fresh events before each replay.
-  struct StepGraph {
-    cudaGraphExec_t exec = nullptr;
-    int prof = -1;
-    long long launches = 0;
-    std::vector<cudaGraphNode_t> ev_nodes;
-    cudaGraph_t graph = nullptr;
-  } graphs[2];
-  bool use_graph = true;
-  cudaStream_t cap_st = nullptr;
+  // The instance's descriptor in device memory (its slot in the batch's
+  // array when it belongs to a batch) and the group of one that the
+  // single-instance calls launch with.
+  InstDev* dinst = nullptr;
+  Group grp;
+  mr_lbm_batch* batch = nullptr;
 };
 
 // Record a sticky failure on the handle and return it.

@@ -174,28 +174,73 @@ __host__ __device__ inline int mr_slot(int k, int N, int periodic) {
 }
 
 // ------------------------------------------------------------------------
+// instances and groups
+// ------------------------------------------------------------------------
+
+#define MR_MAXB 1024  // instances of one group
+
+// Everything the step kernels need about one instance, in device memory.
+// Leaf-value arrays are void*: their element type is the storage type of
+// g.form.  fstate holds the stored (post-collision) leaf values of the
+// current mesh, fscratch the values moved to the new mesh before transport.
+struct __align__(16) InstDev {
+  Geo g;
+  MeshDev mesh[2];
+  void* fstate;
+  void* fscratch;
+  uint8_t* flags;     // dense: T / H / G marks
+  uint8_t* cls;       // dense: classification of the new mesh
+  int* bcounts;       // per dense chunk: leaf / internal / ghost counts, then offsets
+  const double* W;    // flattened weights, MR_WIDX layout
+};
+
+// Instances of one scheme and storage form, stepped by shared launches: every
+// step kernel covers all of them (a single solver is a group of one).  All
+// instances of a group are on the same mesh parity.
+struct Group {
+  const InstDev* dev;    // device array [n]
+  const int* chunk_pre;  // device array [n + 1]: first dense chunk of each instance
+  int n;
+  int d, Q, scheme, form;
+  int chunks;            // dense chunks of all instances
+  int span;              // maximum of J - J_min
+  bool grade;            // some instance has J > J_min + 1
+  long long capL, capI;  // summed leaf / internal capacities
+  long long proj_cells[MR_MAXL];  // summed cells of level J - k (projection phase k)
+  long long pred_cells[MR_MAXL];  // summed cells of level J_min + k (prediction phase k)
+  int nsm;
+};
+
+// Grid of a tiled step kernel: at most `per_sm` blocks per SM, and no more
+// blocks than the tiles the group can have for `max_items` items.
+inline int mr_tile_grid(const Group& G, long long max_items, int items_per_tile, int per_sm) {
+  const long long need = (max_items + items_per_tile - 1) / items_per_tile + G.n;
+  const long long cap = (long long)G.nsm * per_sm;
+  return (int)(need < cap ? need : cap);
+}
+// dynamic shared memory of a tiled step kernel: the tile prefix
+inline size_t mr_pre_bytes(const Group& G) { return (size_t)(G.n + 1) * sizeof(int); }
+
+// ------------------------------------------------------------------------
 // kernels (defined in mr_encode.cu, mr_mesh.cu, mr_stream.cu)
 // ------------------------------------------------------------------------
 
-// Leaf-value arrays (LF) are passed as void*: their element type is the
-// storage type of g.form.
-void mr_launch_project(const Geo& g, const MeshDev& A, const void* LF, int level, cudaStream_t st,
-                       int grid);
-void mr_launch_details(const Geo& g, const MeshDev& A, const void* LF, cudaStream_t st, int grid);
-void mr_launch_flags_T(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid);
-void mr_launch_flags_H(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid);
-void mr_launch_grade(const Geo& g, uint8_t* flags, MeshCounts* errc, cudaStream_t st, int grid);
-void mr_launch_classify(const Geo& g, const uint8_t* flags, uint8_t* cls, cudaStream_t st, int grid);
-void mr_launch_mark_ghosts(const Geo& g, uint8_t* cls, cudaStream_t st, int grid);
-void mr_launch_compact(const Geo& g, uint8_t* cls, uint8_t* flags, int* block_counts, MeshDev& B,
-                       cudaStream_t st);
-void mr_launch_remesh_copy(const Geo& g, const MeshDev& A, const void* LF_old, const MeshDev& B,
-                           void* LF_new, cudaStream_t st, int grid);
-void mr_launch_predict_level(const Geo& g, const MeshDev& B, void* LF, int level, cudaStream_t st,
-                             int grid);
-void mr_launch_stream_collide(const Geo& g, const MeshDev& B, const void* LF_in, void* LF_out,
-                              const double* W, int do_stream, int do_collide, cudaStream_t st,
-                              int grid);
+// Step kernels, one launch for every instance of a group.  `cur` is the
+// parity of the current mesh (values in fstate); the new mesh is 1 - cur.
+void mr_launch_project(const Group& G, int cur, int k, cudaStream_t st);  // level J - k
+void mr_launch_details(const Group& G, int cur, cudaStream_t st);
+void mr_launch_flags_T(const Group& G, int cur, cudaStream_t st);
+void mr_launch_flags_H(const Group& G, int cur, cudaStream_t st);
+void mr_launch_grade(const Group& G, cudaStream_t st);
+void mr_launch_classify(const Group& G, cudaStream_t st);
+void mr_launch_mark_ghosts(const Group& G, cudaStream_t st);
+void mr_launch_compact(const Group& G, int dst, cudaStream_t st);  // count + scan + scatter into mesh dst
+void mr_launch_remesh_copy(const Group& G, int cur, cudaStream_t st);
+void mr_launch_predict_level(const Group& G, int dst, int k, cudaStream_t st);  // level J_min + k
+void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st);
+void mr_launch_count_updates(const Group& G, int dst, cudaStream_t st);
+
+// Input / output kernels of one instance.
 void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, void* LF,
                        cudaStream_t st, int grid);
 void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int grid);
@@ -211,4 +256,3 @@ void mr_launch_leaves_out(const Geo& g, const MeshDev& B, const void* LF, long l
 void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int level,
                              const double* prev, double* cur, cudaStream_t st, int grid);
 size_t mr_form_bytes(int form);  // bytes per stored population value
-void mr_launch_count_updates(MeshCounts* cnt, cudaStream_t st);

@@ -18,10 +18,27 @@ namespace {
 __device__ __forceinline__ double level_eps(const Geo& g, int l) { return ldexp(g.eps, g.d * (l - g.J)); }
 
 // ---------------------------------------------------------------- T_eps
+// Tiled step kernels over the internal cells of the current mesh: a tile is
+// 256 cells of one instance.
+#define MR_INT_TILES_BEGIN(IB, N, CUR, G_, A_, I_)                                              \
+  extern __shared__ int pre[];                                                                \
+  __shared__ InstDev si;                                                                      \
+  const int tiles =                                                                           \
+      mr_group_prefix(pre, N, [&](int b) { return (IB[b].mesh[CUR].cnt->total[MR_CLS_INT] + 255) / 256; }); \
+  int have = -1;                                                                              \
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {                                        \
+    const int b = mr_group_find(pre, N, t);                                                   \
+    mr_inst_use(si, have, IB, b);                                                             \
+    const Geo& G_ = si.g;                                                                     \
+    const MeshDev& A_ = si.mesh[CUR];                                                         \
+    const int I_ = (t - pre[b]) * 256 + threadIdx.x;                                          \
+    if (I_ >= A_.cnt->total[MR_CLS_INT]) continue;
+#define MR_INT_TILES_END }
+
 template <int D>
-__global__ void __launch_bounds__(256) k_flags_T(Geo g, MeshDev A, uint8_t* flags) {
-  const int n = A.cnt->total[MR_CLS_INT];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) k_flags_T(const InstDev* __restrict__ IB, int n, int cur) {
+  MR_INT_TILES_BEGIN(IB, n, cur, g, A, i)
+    uint8_t* flags = si.flags;
     const int L = A.lvl[MR_CLS_INT][i];
     if (!(A.G[i] >= level_eps(g, L + 1))) continue;
     int l = L;
@@ -32,14 +49,14 @@ __global__ void __launch_bounds__(256) k_flags_T(Geo g, MeshDev A, uint8_t* flag
       --l;
       c >>= D;
     }
-  }
+  MR_INT_TILES_END
 }
 
 // ---------------------------------------------------------------- H_eps
 template <int D>
-__global__ void __launch_bounds__(256) k_flags_H(Geo g, MeshDev A, uint8_t* flags) {
-  const int n = A.cnt->total[MR_CLS_INT];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) k_flags_H(const InstDev* __restrict__ IB, int n, int cur) {
+  MR_INT_TILES_BEGIN(IB, n, cur, g, A, i)
+    uint8_t* flags = si.flags;
     const int L = A.lvl[MR_CLS_INT][i];
     const uint32_t code = A.code[MR_CLS_INT][i];
     if (!(flags[g.base[L] + code] & MR_F_T)) continue;
@@ -61,7 +78,7 @@ __global__ void __launch_bounds__(256) k_flags_H(Geo g, MeshDev A, uint8_t* flag
       for (int ci = 0; ci < (1 << D); ++ci)
         mr_atomic_or_byte(flags, g.base[L + 1] + ((code << D) | (uint32_t)ci), MR_F_H);
     }
-  }
+  MR_INT_TILES_END
 }
 
 // ---------------------------------------------------------------- grading
@@ -70,12 +87,24 @@ __global__ void __launch_bounds__(256) k_flags_H(Geo g, MeshDev A, uint8_t* flag
 // those cells refined on level L-1.  The thread that newly refines a cell
 // continues the cascade from it, depth first, towards J_min.
 template <int D>
-__global__ void __launch_bounds__(256) k_grade(Geo g, uint8_t* flags) {
-  // grid-stride (not one block per chunk): refined cells cluster, and
-  // interleaving spreads their cascades over all blocks
-  const uint32_t lo = g.base[g.Jmin + 1], hi = g.base[g.J];
+__global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, int n) {
+  // tiles of 256 cells strided over the grid (not one block per chunk):
+  // refined cells cluster, and interleaving spreads their cascades
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  const int tiles = mr_group_prefix(pre, n, [&](int b) {
+    const Geo& gb = IB[b].g;
+    return gb.J > gb.Jmin + 1 ? (int)((gb.base[gb.J] - gb.base[gb.Jmin + 1] + 255) / 256) : 0;
+  });
   const int noff = D == 2 ? 9 : 3;
-  for (uint32_t gi = lo + blockIdx.x * blockDim.x + threadIdx.x; gi < hi; gi += gridDim.x * blockDim.x) {
+  int have = -1;
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int b = mr_group_find(pre, n, t);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    uint8_t* flags = si.flags;
+    const uint32_t gi = g.base[g.Jmin + 1] + (uint32_t)(t - pre[b]) * 256u + threadIdx.x;
+    if (gi >= g.base[g.J]) continue;
     if (!(flags[gi] & MR_F_H)) continue;
     const int l0 = mr_level_of(g, gi);
     const uint32_t c0 = gi - g.base[l0];
@@ -112,9 +141,15 @@ __global__ void __launch_bounds__(256) k_grade(Geo g, uint8_t* flags) {
 
 // ---------------------------------------------------------------- classify
 template <int D>
-__global__ void __launch_bounds__(256) k_classify(Geo g, const uint8_t* __restrict__ flags,
-                                                  uint8_t* cls) {
-  MR_DENSE_CHUNK_BEGIN(g, 0u, l, c, gi)
+__global__ void __launch_bounds__(256) k_classify(const InstDev* __restrict__ IB,
+                                                  const int* __restrict__ chunk_pre, int n) {
+  __shared__ InstDev si;
+  int chunk, have = -1;
+  mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
+  const Geo& g = si.g;
+  const uint8_t* flags = si.flags;
+  uint8_t* cls = si.cls;
+  MR_DENSE_CHUNK_BEGIN(g, chunk, l, c, gi)
     const bool inR = (l == g.Jmin) || (flags[g.base[l - 1] + (c >> D)] & (MR_F_H | MR_F_G));
     const bool ref = (l < g.J) && (flags[gi] & (MR_F_H | MR_F_G));
     cls[gi] = inR ? (ref ? MR_C_INT : MR_C_LEAF) : 0;
@@ -122,7 +157,7 @@ __global__ void __launch_bounds__(256) k_classify(Geo g, const uint8_t* __restri
 }
 
 __global__ void __launch_bounds__(256) k_full_mesh(Geo g, uint8_t* cls) {
-  MR_DENSE_CHUNK_BEGIN(g, 0u, l, c, gi)
+  MR_DENSE_CHUNK_BEGIN(g, blockIdx.x, l, c, gi)
     (void)c;
     cls[gi] = l == g.J ? MR_C_LEAF : MR_C_INT;
   MR_DENSE_CHUNK_END
@@ -135,10 +170,16 @@ __global__ void __launch_bounds__(256) k_full_mesh(Geo g, uint8_t* cls) {
 // block around the leaf.  Those outside R(Lambda) are ghosts: predicted from
 // level l-1, whose stencil cells outside R(Lambda) are ghosts in turn.
 template <int D>
-__global__ void __launch_bounds__(256) k_mark_ghosts(Geo g, uint8_t* cls) {
+__global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__ IB,
+                                                     const int* __restrict__ chunk_pre, int n) {
+  __shared__ InstDev si;
+  int chunk, have = -1;
+  mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
+  const Geo& g = si.g;
+  uint8_t* cls = si.cls;
   const bool block = D == 2 && g.diag;
   const int nwin = block ? 25 : 4 * D;
-  MR_DENSE_CHUNK_BEGIN(g, 0u, l, c, gi)
+  MR_DENSE_CHUNK_BEGIN(g, chunk, l, c, gi)
     if ((cls[gi] & 3u) != MR_C_LEAF) continue;
     int x, y;
     mr_decode(g, l, c, x, y);
@@ -206,22 +247,34 @@ __device__ __forceinline__ int cls_of(uint8_t c) {
   return -1;
 }
 
-__global__ void __launch_bounds__(1024) k_count(const uint8_t* __restrict__ cls, int* bc) {
-  const uint32_t gi = blockIdx.x * 1024u + threadIdx.x;
+__global__ void __launch_bounds__(1024) k_count(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
+                                                int n) {
+  int chunk;
+  const int b = mr_group_chunk(chunk_pre, n, chunk);
+  const uint8_t* __restrict__ cls = IB[b].cls;
+  int* bc = IB[b].bcounts;
+  const uint32_t gi = (uint32_t)chunk * 1024u + threadIdx.x;
   const int k = cls_of(cls[gi]);
   const int nl = __syncthreads_count(k == MR_CLS_LEAF);
   const int ni = __syncthreads_count(k == MR_CLS_INT);
   const int ng = __syncthreads_count(k == MR_CLS_GHOST);
   if (threadIdx.x == 0) {
-    bc[blockIdx.x * 3 + 0] = nl;
-    bc[blockIdx.x * 3 + 1] = ni;
-    bc[blockIdx.x * 3 + 2] = ng;
+    bc[chunk * 3 + 0] = nl;
+    bc[chunk * 3 + 1] = ni;
+    bc[chunk * 3 + 2] = ng;
   }
 }
 
-__global__ void __launch_bounds__(1024) k_scan_blocks(Geo g, int* bc, int nblocks, MeshCounts* cnt) {
+__global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict__ IB, int dst) {
   __shared__ int warp_sums[32];
   __shared__ int carry;
+  __shared__ InstDev si;
+  int have = -1;
+  mr_inst_use(si, have, IB, blockIdx.x);
+  const Geo& g = si.g;
+  int* bc = si.bcounts;
+  const int nblocks = (int)(g.base[g.J + 1] / MR_DENSE_ALIGN);
+  MeshCounts* cnt = si.mesh[dst].cnt;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int c = 0; c < 3; ++c) {
     if (threadIdx.x == 0) carry = 0;
@@ -277,11 +330,19 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Geo g, int* bc, int nblock
   }
 }
 
-__global__ void __launch_bounds__(1024) k_scatter(Geo g, uint8_t* cls, uint8_t* flags,
-                                                  const int* __restrict__ bc, MeshDev B) {
+__global__ void __launch_bounds__(1024) k_scatter(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
+                                                  int n, int dst) {
   __shared__ int wcount[32][3];
   __shared__ int woff[32][3];
-  const uint32_t gi = blockIdx.x * 1024u + threadIdx.x;
+  __shared__ InstDev si;
+  int chunk, have = -1;
+  mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
+  const Geo& g = si.g;
+  uint8_t* cls = si.cls;
+  uint8_t* flags = si.flags;
+  const int* __restrict__ bc = si.bcounts;
+  const MeshDev& B = si.mesh[dst];
+  const uint32_t gi = (uint32_t)chunk * 1024u + threadIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int k = cls_of(cls[gi]);
   const uint32_t lt = (1u << lane) - 1u;
@@ -303,7 +364,7 @@ __global__ void __launch_bounds__(1024) k_scatter(Geo g, uint8_t* cls, uint8_t* 
   __syncthreads();
   int32_t entry = MR_MAP_NONE;
   if (k >= 0) {
-    const int pos = bc[blockIdx.x * 3 + k] + woff[wid][k] + pre;
+    const int pos = bc[chunk * 3 + k] + woff[wid][k] + pre;
     if (pos < g.cap[k]) {
       const int l = mr_level_of(g, gi);
       B.code[k][pos] = gi - g.base[l];
@@ -353,47 +414,50 @@ __global__ void __launch_bounds__(256) k_leaves_check(Geo g, const uint8_t* __re
 
 }  // namespace
 
-#define MR_DISPATCH_D(KER, GRID, BLOCK, ST, ...)                 \
+#define MR_DISPATCH_D(KER, GRID, BLOCK, SMEM, ST, ...)           \
   do {                                                           \
-    if (g.d == 1)                                                \
-      KER<1><<<GRID, BLOCK, 0, ST>>>(__VA_ARGS__);               \
+    if (D_ == 1)                                                 \
+      KER<1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);            \
     else                                                         \
-      KER<2><<<GRID, BLOCK, 0, ST>>>(__VA_ARGS__);               \
+      KER<2><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);            \
   } while (0)
 
-void mr_launch_flags_T(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid) {
-  MR_DISPATCH_D(k_flags_T, grid, 256, st, g, A, flags);
+void mr_launch_flags_T(const Group& G, int cur, cudaStream_t st) {
+  const int D_ = G.d;
+  MR_DISPATCH_D(k_flags_T, mr_tile_grid(G, G.capI, 256, 4), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
 }
-void mr_launch_flags_H(const Geo& g, const MeshDev& A, uint8_t* flags, cudaStream_t st, int grid) {
-  MR_DISPATCH_D(k_flags_H, grid, 256, st, g, A, flags);
+void mr_launch_flags_H(const Group& G, int cur, cudaStream_t st) {
+  const int D_ = G.d;
+  MR_DISPATCH_D(k_flags_H, mr_tile_grid(G, G.capI, 256, 4), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
 }
-// dense kernels: one block per 1024-cell chunk (the `grid` argument is unused)
-static int dense_chunks(const Geo& g, int lo_level, int hi_level_excl) {
-  return (int)((g.base[hi_level_excl] - g.base[lo_level]) / MR_DENSE_ALIGN);
+void mr_launch_grade(const Group& G, cudaStream_t st) {
+  const int D_ = G.d;
+  if (G.grade)
+    MR_DISPATCH_D(k_grade, mr_tile_grid(G, (long long)G.chunks * MR_DENSE_ALIGN, 256, 4), 256, mr_pre_bytes(G), st,
+                  G.dev, G.n);
 }
-void mr_launch_grade(const Geo& g, uint8_t* flags, MeshCounts*, cudaStream_t st, int grid) {
-  if (g.J > g.Jmin + 1) MR_DISPATCH_D(k_grade, grid, 256, st, g, flags);
-}
-void mr_launch_classify(const Geo& g, const uint8_t* flags, uint8_t* cls, cudaStream_t st, int) {
-  MR_DISPATCH_D(k_classify, dense_chunks(g, g.Jmin, g.J + 1), 256, st, g, flags, cls);
+// dense kernels: one block per 1024-cell chunk of every instance
+void mr_launch_classify(const Group& G, cudaStream_t st) {
+  const int D_ = G.d;
+  MR_DISPATCH_D(k_classify, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
 }
 void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int) {
-  k_full_mesh<<<dense_chunks(g, g.Jmin, g.J + 1), 256, 0, st>>>(g, cls);
+  k_full_mesh<<<(int)(g.base[g.J + 1] / MR_DENSE_ALIGN), 256, 0, st>>>(g, cls);
 }
-void mr_launch_mark_ghosts(const Geo& g, uint8_t* cls, cudaStream_t st, int) {
-  MR_DISPATCH_D(k_mark_ghosts, dense_chunks(g, g.Jmin, g.J + 1), 256, st, g, cls);
+void mr_launch_mark_ghosts(const Group& G, cudaStream_t st) {
+  const int D_ = G.d;
+  MR_DISPATCH_D(k_mark_ghosts, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
 }
-void mr_launch_compact(const Geo& g, uint8_t* cls, uint8_t* flags, int* block_counts, MeshDev& B,
-                       cudaStream_t st) {
-  const int nblocks = (int)(g.base[g.J + 1] / MR_DENSE_ALIGN);
-  k_count<<<nblocks, 1024, 0, st>>>(cls, block_counts);
-  k_scan_blocks<<<1, 1024, 0, st>>>(g, block_counts, nblocks, B.cnt);
-  k_scatter<<<nblocks, 1024, 0, st>>>(g, cls, flags, block_counts, B);
+void mr_launch_compact(const Group& G, int dst, cudaStream_t st) {
+  k_count<<<G.chunks, 1024, 0, st>>>(G.dev, G.chunk_pre, G.n);
+  k_scan_blocks<<<G.n, 1024, 0, st>>>(G.dev, dst);
+  k_scatter<<<G.chunks, 1024, 0, st>>>(G.dev, G.chunk_pre, G.n, dst);
 }
 void mr_launch_leaves_in(const Geo& g, long long n, const unsigned long long* keys,
                          const signed char* levels, int32_t* inidx, uint8_t* cls, MeshCounts* cnt,
                          unsigned long long* vol, cudaStream_t st, int grid) {
-  MR_DISPATCH_D(k_leaves_in, grid, 256, st, g, n, keys, levels, inidx, cls, cnt, vol);
+  const int D_ = g.d;
+  MR_DISPATCH_D(k_leaves_in, grid, 256, 0, st, g, n, keys, levels, inidx, cls, cnt, vol);
 }
 void mr_launch_leaves_check(const Geo& g, uint8_t* cls, MeshCounts* cnt, cudaStream_t st, int grid) {
   k_leaves_check<<<grid, 256, 0, st>>>(g, cls, cnt);

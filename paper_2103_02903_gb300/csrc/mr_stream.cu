@@ -305,12 +305,27 @@ struct PopRows {
 // Thread layout of the transfer kernels: 32 cells (threadIdx.x) by up to 8
 // populations (threadIdx.y), one population per warp.
 template <int Q, int F>
-__global__ void __launch_bounds__(256) k_remesh_copy(Geo g, MeshDev A, const void* __restrict__ LFold, MeshDev B,
-                                                     void* LFnew) {
+__global__ void __launch_bounds__(256) k_remesh_copy(const InstDev* __restrict__ IB, int ngrp, int cur) {
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
-  const int nL = B.cnt->total[MR_CLS_LEAF], nI = B.cnt->total[MR_CLS_INT];
-  for (int t = blockIdx.x * 32 + threadIdx.x; t < nL + nI; t += gridDim.x * 32) {
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  const int tiles = mr_group_prefix(pre, ngrp, [&](int b) {
+    const MeshCounts* c = IB[b].mesh[1 - cur].cnt;
+    return (c->total[MR_CLS_LEAF] + c->total[MR_CLS_INT] + 31) / 32;
+  });
+  int have = -1;
+  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+    const int b = mr_group_find(pre, ngrp, tt);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    const MeshDev& A = si.mesh[cur];
+    const MeshDev& B = si.mesh[1 - cur];
+    const void* LFold = si.fstate;
+    void* LFnew = si.fscratch;
+    const int nL = B.cnt->total[MR_CLS_LEAF], nI = B.cnt->total[MR_CLS_INT];
+    const int t = (tt - pre[b]) * 32 + threadIdx.x;
+    if (t >= nL + nI) continue;
     const bool leaf = t < nL;
     const int i = leaf ? t : t - nL;
     const int k = leaf ? MR_CLS_LEAF : MR_CLS_INT;
@@ -335,15 +350,34 @@ __global__ void __launch_bounds__(256) k_remesh_copy(Geo g, MeshDev A, const voi
 // Ghosts and newly created leaves of one level: the prediction operator
 // applied to level-1 values of the new mesh (all present by construction).
 template <int D, int Q, int F>
-__global__ void __launch_bounds__(256) k_predict_level(Geo g, MeshDev B, void* LF, int level) {
+__global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict__ IB, int ngrp, int dst, int kl) {
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
   constexpr int PY = PopRows<Q>::value;
-  const int gb = B.cnt->off[MR_CLS_GHOST][level], ge = B.cnt->off[MR_CLS_GHOST][level + 1];
-  const int lb = B.cnt->off[MR_CLS_LEAF][level], le = B.cnt->off[MR_CLS_LEAF][level + 1];
-  const int ng = ge - gb, total = ng + (le - lb);
-  const C cs = (C)g.cross_sign;
-  for (int t = blockIdx.x * 32 + threadIdx.x; t < total; t += gridDim.x * 32) {
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  const int tiles = mr_group_prefix(pre, ngrp, [&](int b) {
+    const Geo& gb = IB[b].g;
+    const int l = gb.Jmin + kl;
+    if (l > gb.J) return 0;
+    const MeshCounts* c = IB[b].mesh[dst].cnt;
+    return (c->off[MR_CLS_GHOST][l + 1] - c->off[MR_CLS_GHOST][l] + c->off[MR_CLS_LEAF][l + 1] -
+            c->off[MR_CLS_LEAF][l] + 31) / 32;
+  });
+  int have = -1;
+  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+    const int b = mr_group_find(pre, ngrp, tt);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    const MeshDev& B = si.mesh[dst];
+    void* LF = si.fscratch;
+    const int level = g.Jmin + kl;
+    const int gb = B.cnt->off[MR_CLS_GHOST][level], ge = B.cnt->off[MR_CLS_GHOST][level + 1];
+    const int lb = B.cnt->off[MR_CLS_LEAF][level], le = B.cnt->off[MR_CLS_LEAF][level + 1];
+    const int ng = ge - gb, total = ng + (le - lb);
+    const C cs = (C)g.cross_sign;
+    const int t = (tt - pre[b]) * 32 + threadIdx.x;
+    if (t >= total) continue;
     uint32_t code;
     S* out;
     size_t ostride;
@@ -569,19 +603,29 @@ __device__ double obstacle_fraction(const Geo& g, int l, uint32_t code) {
 
 // ------------------------------------------------------------------ transport + collision
 template <int SC, int F>
-__global__ void __launch_bounds__(128) k_stream_collide(Geo g, MeshDev B, const void* __restrict__ LFin_,
-                                                        void* __restrict__ LFout_, const double* __restrict__ W,
+__global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restrict__ IB, int ngrp, int dst,
                                                         int do_stream, int do_collide) {
   using Sc = Scheme<SC>;
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
   constexpr bool OFFS = FormT<F>::offs;
   constexpr int D = Sc::D, Q = Sc::Q;
-  const S* LFin = (const S*)LFin_;
-  S* LFout = (S*)LFout_;
-  const int n = B.cnt->total[MR_CLS_LEAF];
-  const C cs = (C)g.cross_sign;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  const int tiles =
+      mr_group_prefix(pre, ngrp, [&](int b) { return (IB[b].mesh[dst].cnt->total[MR_CLS_LEAF] + 127) / 128; });
+  int have = -1;
+  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+    const int b = mr_group_find(pre, ngrp, tt);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    const MeshDev& B = si.mesh[dst];
+    const S* __restrict__ LFin = (const S*)si.fscratch;
+    S* __restrict__ LFout = (S*)si.fstate;
+    const double* __restrict__ W = si.W;
+    const C cs = (C)g.cross_sign;
+    const int i = (tt - pre[b]) * 128 + threadIdx.x;
+    if (i >= B.cnt->total[MR_CLS_LEAF]) continue;
     const int l = B.lvl[MR_CLS_LEAF][i];
     const uint32_t code = B.code[MR_CLS_LEAF][i];
     C f[Q], out[Q], offv[Q];
@@ -819,26 +863,28 @@ __global__ void __launch_bounds__(256) k_project_dense(Geo g, MeshDev B, const v
   }
 }
 
-__global__ void k_count_updates(MeshCounts* cnt) {
+__global__ void k_count_updates(const InstDev* __restrict__ IB, int ngrp, int dst) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= ngrp) return;
+  MeshCounts* cnt = IB[b].mesh[dst].cnt;
   cnt->leaf_updates += cnt->total[MR_CLS_LEAF];
   cnt->steps += 1;
 }
 
 template <int Q, int F>
-void launch_remesh_t(const Geo& g, const MeshDev& A, const void* LFo, const MeshDev& B, void* LFn, cudaStream_t st,
-                     int grid) {
-  k_remesh_copy<Q, F><<<grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, A, LFo, B, LFn);
+void launch_remesh_t(const Group& G, int cur, cudaStream_t st) {
+  k_remesh_copy<Q, F><<<mr_tile_grid(G, G.capL + G.capI, 32, 8), dim3(32, PopRows<Q>::value), mr_pre_bytes(G), st>>>(
+      G.dev, G.n, cur);
 }
 template <int D, int Q, int F>
-void launch_predict_t(const Geo& g, const MeshDev& B, void* LF, int level, cudaStream_t st, int grid) {
-  // `grid` is the maximum number of blocks; a block covers 32 cells
-  const int need = (int)((2u * g.ncode[level] + 31) / 32);
-  k_predict_level<D, Q, F><<<need < grid ? need : grid, dim3(32, PopRows<Q>::value), 0, st>>>(g, B, LF, level);
+void launch_predict_t(const Group& G, int dst, int kl, cudaStream_t st) {
+  // ghosts and leaves of one level: at most twice its cells
+  k_predict_level<D, Q, F><<<mr_tile_grid(G, 2 * G.pred_cells[kl], 32, 8), dim3(32, PopRows<Q>::value),
+                             mr_pre_bytes(G), st>>>(G.dev, G.n, dst, kl);
 }
 template <int SC, int F>
-void launch_stream_t(const Geo& g, const MeshDev& B, const void* in, void* out, const double* W, int ds, int dc,
-                     cudaStream_t st, int grid) {
-  k_stream_collide<SC, F><<<grid, 128, 0, st>>>(g, B, in, out, W, ds, dc);
+void launch_stream_t(const Group& G, int dst, int ds, int dc, cudaStream_t st) {
+  k_stream_collide<SC, F><<<mr_tile_grid(G, G.capL, 128, 8), 128, mr_pre_bytes(G), st>>>(G.dev, G.n, dst, ds, dc);
 }
 template <int SC, int F>
 void launch_init_t(const Geo& g, const MeshDev& B, const double* cons, void* LF, cudaStream_t st, int grid) {
@@ -848,21 +894,21 @@ void launch_init_t(const Geo& g, const MeshDev& B, const double* cons, void* LF,
 }  // namespace
 
 #define MR_FORMS(FN, ...)                                          \
-  switch (g.form) {                                                \
+  switch (G.form) {                                                \
     case MR_FORM_F64: FN<MR_FORM_F64>(__VA_ARGS__); break;         \
     case MR_FORM_F32: FN<MR_FORM_F32>(__VA_ARGS__); break;         \
     case MR_FORM_F32_F16: FN<MR_FORM_F32_F16>(__VA_ARGS__); break; \
     case MR_FORM_F32_BF16: FN<MR_FORM_F32_BF16>(__VA_ARGS__); break; \
   }
 #define MR_FORMS2(FN, A1, ...)                                         \
-  switch (g.form) {                                                    \
+  switch (G.form) {                                                    \
     case MR_FORM_F64: FN<A1, MR_FORM_F64>(__VA_ARGS__); break;         \
     case MR_FORM_F32: FN<A1, MR_FORM_F32>(__VA_ARGS__); break;         \
     case MR_FORM_F32_F16: FN<A1, MR_FORM_F32_F16>(__VA_ARGS__); break; \
     case MR_FORM_F32_BF16: FN<A1, MR_FORM_F32_BF16>(__VA_ARGS__); break; \
   }
 #define MR_FORMS3(FN, A1, A2, ...)                                         \
-  switch (g.form) {                                                        \
+  switch (G.form) {                                                        \
     case MR_FORM_F64: FN<A1, A2, MR_FORM_F64>(__VA_ARGS__); break;         \
     case MR_FORM_F32: FN<A1, A2, MR_FORM_F32>(__VA_ARGS__); break;         \
     case MR_FORM_F32_F16: FN<A1, A2, MR_FORM_F32_F16>(__VA_ARGS__); break; \
@@ -877,37 +923,36 @@ size_t mr_form_bytes(int form) {
   }
 }
 
-void mr_launch_remesh_copy(const Geo& g, const MeshDev& A, const void* LF_old, const MeshDev& B, void* LF_new,
-                           cudaStream_t st, int grid) {
-  switch (g.Q) {
-    case 2: MR_FORMS2(launch_remesh_t, 2, g, A, LF_old, B, LF_new, st, grid); break;
-    case 3: MR_FORMS2(launch_remesh_t, 3, g, A, LF_old, B, LF_new, st, grid); break;
-    case 9: MR_FORMS2(launch_remesh_t, 9, g, A, LF_old, B, LF_new, st, grid); break;
-    case 16: MR_FORMS2(launch_remesh_t, 16, g, A, LF_old, B, LF_new, st, grid); break;
+void mr_launch_remesh_copy(const Group& G, int cur, cudaStream_t st) {
+  switch (G.Q) {
+    case 2: MR_FORMS2(launch_remesh_t, 2, G, cur, st); break;
+    case 3: MR_FORMS2(launch_remesh_t, 3, G, cur, st); break;
+    case 9: MR_FORMS2(launch_remesh_t, 9, G, cur, st); break;
+    case 16: MR_FORMS2(launch_remesh_t, 16, G, cur, st); break;
   }
 }
 
-void mr_launch_predict_level(const Geo& g, const MeshDev& B, void* LF, int level, cudaStream_t st, int grid) {
-  switch (g.d * 100 + g.Q) {
-    case 102: MR_FORMS3(launch_predict_t, 1, 2, g, B, LF, level, st, grid); break;
-    case 103: MR_FORMS3(launch_predict_t, 1, 3, g, B, LF, level, st, grid); break;
-    case 209: MR_FORMS3(launch_predict_t, 2, 9, g, B, LF, level, st, grid); break;
-    case 216: MR_FORMS3(launch_predict_t, 2, 16, g, B, LF, level, st, grid); break;
+void mr_launch_predict_level(const Group& G, int dst, int kl, cudaStream_t st) {
+  switch (G.d * 100 + G.Q) {
+    case 102: MR_FORMS3(launch_predict_t, 1, 2, G, dst, kl, st); break;
+    case 103: MR_FORMS3(launch_predict_t, 1, 3, G, dst, kl, st); break;
+    case 209: MR_FORMS3(launch_predict_t, 2, 9, G, dst, kl, st); break;
+    case 216: MR_FORMS3(launch_predict_t, 2, 16, G, dst, kl, st); break;
   }
 }
 
-void mr_launch_stream_collide(const Geo& g, const MeshDev& B, const void* LF_in, void* LF_out, const double* W,
-                              int do_stream, int do_collide, cudaStream_t st, int grid) {
-  switch (g.scheme) {
-    case 0: MR_FORMS2(launch_stream_t, 0, g, B, LF_in, LF_out, W, do_stream, do_collide, st, grid); break;
-    case 1: MR_FORMS2(launch_stream_t, 1, g, B, LF_in, LF_out, W, do_stream, do_collide, st, grid); break;
-    case 2: MR_FORMS2(launch_stream_t, 2, g, B, LF_in, LF_out, W, do_stream, do_collide, st, grid); break;
-    case 3: MR_FORMS2(launch_stream_t, 3, g, B, LF_in, LF_out, W, do_stream, do_collide, st, grid); break;
-    case 4: MR_FORMS2(launch_stream_t, 4, g, B, LF_in, LF_out, W, do_stream, do_collide, st, grid); break;
+void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st) {
+  switch (G.scheme) {
+    case 0: MR_FORMS2(launch_stream_t, 0, G, dst, do_stream, do_collide, st); break;
+    case 1: MR_FORMS2(launch_stream_t, 1, G, dst, do_stream, do_collide, st); break;
+    case 2: MR_FORMS2(launch_stream_t, 2, G, dst, do_stream, do_collide, st); break;
+    case 3: MR_FORMS2(launch_stream_t, 3, G, dst, do_stream, do_collide, st); break;
+    case 4: MR_FORMS2(launch_stream_t, 4, G, dst, do_stream, do_collide, st); break;
   }
 }
 
 void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, void* LF, cudaStream_t st, int grid) {
+  const Geo& G = g;
   switch (g.scheme) {
     case 0: MR_FORMS2(launch_init_t, 0, g, B, cons, LF, st, grid); break;
     case 1: MR_FORMS2(launch_init_t, 1, g, B, cons, LF, st, grid); break;
@@ -924,6 +969,7 @@ static void launch_gather_t(const Geo& g, const MeshDev& B, const int32_t* inidx
 }
 void mr_launch_gather_input(const Geo& g, const MeshDev& B, const int32_t* inidx, long long n, const double* fin,
                             void* LF, cudaStream_t st, int grid) {
+  const Geo& G = g;
   MR_FORMS(launch_gather_t, g, B, inidx, n, fin, LF, st, grid);
 }
 
@@ -934,6 +980,7 @@ static void launch_out_t(const Geo& g, const MeshDev& B, const void* LF, long lo
 }
 void mr_launch_leaves_out(const Geo& g, const MeshDev& B, const void* LF, long long n, unsigned long long* keys,
                           signed char* levels, double* f, cudaStream_t st, int grid) {
+  const Geo& G = g;
   MR_FORMS(launch_out_t, g, B, LF, n, keys, levels, f, st, grid);
 }
 
@@ -944,6 +991,7 @@ static void launch_dense_t(const Geo& g, const MeshDev& B, const void* LF, int l
 }
 void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int level, const double* prev,
                              double* cur, cudaStream_t st, int grid) {
+  const Geo& G = g;
   if (g.d == 1) {
     MR_FORMS2(launch_dense_t, 1, g, B, LF, level, prev, cur, st, grid);
   } else {
@@ -951,4 +999,6 @@ void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int
   }
 }
 
-void mr_launch_count_updates(MeshCounts* cnt, cudaStream_t st) { k_count_updates<<<1, 1, 0, st>>>(cnt); }
+void mr_launch_count_updates(const Group& G, int dst, cudaStream_t st) {
+  k_count_updates<<<(G.n + 127) / 128, 128, 0, st>>>(G.dev, G.n, dst);
+}
