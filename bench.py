@@ -60,6 +60,11 @@ def _args():
     p.add_argument("--form", default="fp64", choices=["fp64", "fp32", "fp16", "bf16"],
                    help="storage / arithmetic form of the timed run")
     p.add_argument("--all-forms", action="store_true", help="also time every form (extra runs)")
+    p.add_argument("--serving-n", type=int, default=256,
+                   help="instances of the batched serving measurement (0: skip it)")
+    p.add_argument("--serving-steps", type=int, default=30)
+    p.add_argument("--serving-loop", type=int, default=1,
+                   help="also step every instance alone in the plain form (one-at-a-time baseline)")
     return p.parse_args()
 
 
@@ -191,6 +196,94 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- GPU
+def run_serving(args, stream, flush, local):
+    """Batched serving form: many independent instances (D2Q9 vortex flows and
+    D2Q4^4 Riemann problems, uneven levels and thresholds) stepped by shared
+    launches in FP32 with FP16 storage; against the same instances stepped one
+    at a time in the plain FP64 form."""
+    import numpy as np
+    import torch
+    from paper_2103_02903_gb300 import workloads
+    from paper_2103_02903_gb300.binding import Batch, Solver
+
+    cases = workloads.serving_batch(seed=args.seed, n=args.serving_n, precision="fp16")
+    t0 = time.perf_counter()
+    b = Batch([c for c, _ in cases], stream=stream.cuda_stream)
+    for s, (c, u) in zip(b.instances, cases):
+        s.init(u)
+    b.step(args.warmup)
+    b.synchronize()
+    setup_s = time.perf_counter() - t0
+    K = args.serving_steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    per0 = [s.counters()[0] for s in b.instances]
+    l0 = b.launch_count()
+    b.profile_enable(1)
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        b.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    kms, kn = b.profile_read()
+    b.profile_enable(0)
+    launches = b.launch_count() - l0
+    per1 = [s.counters()[0] for s in b.instances]
+    step_ms = np.array([a.elapsed_time(c) for a, c in ev])
+    upd = [y - x for x, y in zip(per0, per1)]
+    total = float(sum(upd))
+    # algorithmic bytes of the transport + collision kernels: read and write
+    # every leaf's populations (2 bytes each) plus its index entry and level
+    alg_bytes = sum(u_ * (2 * 2 * (9 if c["scheme"] == "d2q9_ns" else 16) + 5) for u_, (c, _) in zip(upd, cases))
+    peaks, peak_kind = _peaks()
+    ksec = kms / 1e3
+    gbs = alg_bytes / ksec / 1e9 if ksec > 0 else None
+    out = {
+        "workload": "%d instances: D2Q9 periodic vortices and D2Q4^4 Riemann quadrants, J in {6..10}, "
+                    "eps in {1e-3, 1e-4}, FP32 arithmetic with FP16 storage" % len(cases),
+        "value": total / (step_ms.sum() / 1e3), "unit": UNIT, "steps": K,
+        "ms_per_step": float(step_ms.mean()), "latency_ms_p50": float(np.percentile(step_ms, 50)),
+        "latency_ms_p99": float(np.percentile(step_ms, 99)),
+        "leaves_per_step_avg": total / K, "gpu_launches": launches,
+        "launches_per_step": launches / K, "setup_s": setup_s,
+        "roofline": {"kernel": "k_stream_collide (transport + collision), both schemes", "bound": "hbm",
+                     "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": (gbs / peaks["hbm_gbs"]) if gbs else None, "peak_kind": peak_kind,
+                     "traffic": None, "kernel_ms_per_step": kms / max(K, 1),
+                     "note": "kernel time summed over the scheme branches (concurrent), so frac is a lower bound"},
+    }
+    b.close()
+    if args.serving_loop:
+        # one instance at a time, plain FP64, each with its own CUDA graph
+        lat, leaves = [], 0.0
+        for c, u in cases:
+            c = dict(c, precision="fp64")
+            s = Solver(c, stream=stream.cuda_stream)
+            s.init(u)
+            s.step(args.warmup)
+            s.synchronize()
+            a0 = s.counters()[0]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n_it = 5
+            e0.record(stream)
+            s.step(n_it)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lat.append(e0.elapsed_time(e1) / n_it)
+            leaves += (s.counters()[0] - a0) / n_it
+            s.close()
+        lat = np.array(lat)
+        out["one_at_a_time_plain"] = {
+            "value": leaves / (lat.sum() / 1e3), "unit": UNIT, "ms_per_round": float(lat.sum()),
+            "instance_step_ms_p50": float(np.percentile(lat, 50)),
+            "instance_step_ms_p99": float(np.percentile(lat, 99)),
+            "note": "each instance stepped alone in FP64 (own CUDA graph), 5 steps after the warm-up; a round "
+                    "steps every instance once"}
+        out["speedup_vs_one_at_a_time_plain"] = out["value"] / out["one_at_a_time_plain"]["value"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -260,6 +353,8 @@ def run_ours(args):
                          "leaves_per_step_avg": lv, "transport_kernel_ms": 1e3 * ksec,
                          "transport_hbm_gbs_alg": bpl * lv / ksec / 1e9}
             s2.close()
+
+    serving = run_serving(args, stream, flush, local) if args.serving_n > 0 else None
 
     # whole-job aggregate: updates summed over ranks, time = max over ranks
     if dist is not None:
@@ -366,6 +461,8 @@ def run_ours(args):
             line["kernel_groups"] = groups
         if forms is not None:
             line["forms"] = forms
+        if serving is not None:
+            line["batched"] = serving
         print(json.dumps(line), flush=True)
     solver.close()
     if dist is not None:

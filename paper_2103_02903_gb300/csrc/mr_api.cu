@@ -282,6 +282,18 @@ void fill_desc(const mr_lbm* h, InstDev& d) {
   d.cls = h->cls;
   d.bcounts = h->bcounts;
   d.W = h->W;
+  d.Wf = h->Wf;
+  auto& k = d.g.f32;  // FP32 copies for the FP32 arithmetic of the forms
+  k.lambda = (float)d.g.lambda;
+  k.inv_lambda = (float)d.g.inv_lambda;
+  k.cross_sign = (float)d.g.cross_sign;
+  for (int i = 0; i < 16; ++i) k.s[i] = (float)d.g.s[i];
+  for (int i = 0; i < 8; ++i) k.phys[i] = (float)d.g.phys[i];
+  for (int p = 0; p < MR_MAXQ; ++p) {
+    k.off[p] = (float)d.g.off[p];
+    k.feq0[p] = (float)d.g.feq0[p];
+    k.bcv[p] = (float)d.g.bcv[p];
+  }
 }
 
 // Write the handle's descriptor to its device slot (stream-ordered).
@@ -662,7 +674,8 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   }
   std::vector<double> W;
   build_tables(g, W);
-  ok = ok && dalloc(h, &h->W, W.size());
+  ok = ok && dalloc(h, &h->W, W.size()) && dalloc(h, &h->Wf, W.size());
+  std::vector<float> Wf(W.begin(), W.end());
   int* dchunk = nullptr;
   ok = ok && dalloc(h, &h->dinst, 1) && dalloc(h, &dchunk, 2);
   if (!ok) {
@@ -679,6 +692,8 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
              cudaMemsetAsync(h->inidx, 0xff, dense * sizeof(int32_t), h->st) == cudaSuccess &&
              cudaMemsetAsync(h->mesh[0].map, 0xff, dense * sizeof(int32_t), h->st) == cudaSuccess &&
              cudaMemsetAsync(h->mesh[1].map, 0xff, dense * sizeof(int32_t), h->st) == cudaSuccess &&
+             cudaMemcpyAsync(h->Wf, Wf.data(), Wf.size() * sizeof(float), cudaMemcpyHostToDevice, h->st) ==
+                 cudaSuccess &&
              cudaMemcpyAsync(h->W, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, h->st) ==
                  cudaSuccess &&
              cudaStreamSynchronize(h->st) == cudaSuccess;

@@ -67,6 +67,24 @@ __device__ __forceinline__ __half mr_from_f<__half>(float v) { return __float2ha
 template <>
 __device__ __forceinline__ __nv_bfloat16 mr_from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
+// A constant of the geometry in the arithmetic type C: the FP64 value, or
+// its FP32 copy (MR_K(C, g, s[0]) and the like).
+template <class C>
+__device__ __forceinline__ C mr_k(double d, float f);
+template <>
+__device__ __forceinline__ double mr_k<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float mr_k<float>(double, float f) { return f; }
+#define MR_K(C, g, field) mr_k<C>((g).field, (g).f32.field)
+
+// The flattened-weight table in the arithmetic type C.
+template <class C>
+__device__ __forceinline__ const C* mr_wtab(const InstDev& si);
+template <>
+__device__ __forceinline__ const double* mr_wtab<double>(const InstDev& si) { return si.W; }
+template <>
+__device__ __forceinline__ const float* mr_wtab<float>(const InstDev& si) { return si.Wf; }
+
 // A cell's population array: element p is at p[p * stride].
 template <class S = double>
 struct ValPtr {
@@ -199,6 +217,17 @@ __device__ __forceinline__ void mr_inst_use(InstDev& si, int& have, const InstDe
   have = b;
 }
 
+// Group of one: start copying the only descriptor before the tile prefix,
+// whose barrier then publishes it (saves a round trip per kernel).
+__device__ __forceinline__ void mr_inst_prefetch(InstDev& si, int& have, const InstDev* __restrict__ IB, int n) {
+  if (n != 1) return;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int4* s = reinterpret_cast<const int4*>(IB);
+  int4* d = reinterpret_cast<int4*>(&si);
+  for (int k = tid; k < (int)(sizeof(InstDev) / sizeof(int4)); k += nt) d[k] = __ldg(s + k);
+  have = 0;
+}
+
 // Dense kernels: instance and chunk of this block, from the group's chunk
 // prefix (one block per dense chunk of every instance).
 __device__ __forceinline__ int mr_group_chunk(const int* __restrict__ chunk_pre, int n, int& chunk) {
@@ -234,6 +263,36 @@ __device__ __forceinline__ double mr_predict_canonical(const double* v, int ci, 
     t = __dadd_rn(t, __dmul_rn(sy, qy));
     t = __dadd_rn(t, __dmul_rn((double)cross_sign * sx * sy, q2));
     return t;
+  }
+}
+
+// All 2^D children of one stencil with the rounding of mr_predict_canonical:
+// the products with the signs +-1 are exact, so they become the signs of the
+// additions (x + (-y) and x - y round alike), and the partial sums that two
+// children share are formed once.  out[ci], ci = x bit | y bit << 1.
+template <int D>
+__device__ __forceinline__ void mr_predict_children_canonical(const double* v, int cross_sign, double* out) {
+  if (D == 1) {
+    const double q = __dmul_rn(MR_C1, __dsub_rn(v[2], v[0]));
+    out[0] = __dadd_rn(v[1], q);
+    out[1] = __dsub_rn(v[1], q);
+  } else {
+    const double qx = __dmul_rn(MR_C1, __dsub_rn(v[5], v[3]));
+    const double qy = __dmul_rn(MR_C1, __dsub_rn(v[7], v[1]));
+    const double q2 = __dmul_rn(MR_C1 * MR_C1, __dadd_rn(__dsub_rn(__dsub_rn(v[8], v[6]), v[2]), v[0]));
+    const double a = __dadd_rn(v[4], qx), b = __dsub_rn(v[4], qx);
+    const double t0 = __dadd_rn(a, qy), t1 = __dadd_rn(b, qy), t2 = __dsub_rn(a, qy), t3 = __dsub_rn(b, qy);
+    if (cross_sign > 0) {
+      out[0] = __dadd_rn(t0, q2);
+      out[1] = __dsub_rn(t1, q2);
+      out[2] = __dsub_rn(t2, q2);
+      out[3] = __dadd_rn(t3, q2);
+    } else {
+      out[0] = __dsub_rn(t0, q2);
+      out[1] = __dadd_rn(t1, q2);
+      out[2] = __dadd_rn(t2, q2);
+      out[3] = __dsub_rn(t3, q2);
+    }
   }
 }
 

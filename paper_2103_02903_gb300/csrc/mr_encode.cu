@@ -29,6 +29,8 @@ __global__ void __launch_bounds__(256) k_project(const InstDev* __restrict__ IB,
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
   __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, n);
   const int tiles = mr_group_prefix(pre, n, [&](int b) {
     const InstDev& I = IB[b];
     const int L = I.g.J - k;
@@ -37,7 +39,6 @@ __global__ void __launch_bounds__(256) k_project(const InstDev* __restrict__ IB,
     return (c->off[MR_CLS_INT][L + 1] - c->off[MR_CLS_INT][L] + 31) / 32;
   });
   const double scale = D == 1 ? 0.5 : 0.25;
-  int have = -1;
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int b = mr_group_find(pre, n, t);
     mr_inst_use(si, have, IB, b);
@@ -77,9 +78,12 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
   __shared__ InstDev si;
-  __shared__ double red[PY][32];
-  const int tiles = mr_group_prefix(pre, n, [&](int b) { return (IB[b].mesh[cur].cnt->total[MR_CLS_INT] + 31) / 32; });
+  // the group norm is a maximum of absolute values: compared as the integer
+  // bit patterns of non-negative doubles (same order), on the integer pipe
+  __shared__ unsigned long long red[PY][32];
   int have = -1;
+  mr_inst_prefetch(si, have, IB, n);
+  const int tiles = mr_group_prefix(pre, n, [&](int b) { return (IB[b].mesh[cur].cnt->total[MR_CLS_INT] + 31) / 32; });
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {  // uniform over the block
     const int b = mr_group_find(pre, n, t);
     mr_inst_use(si, have, IB, b);
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
     const void* LF = si.fstate;
     const int nI = A.cnt->total[MR_CLS_INT];
     const int i = (t - pre[b]) * 32 + threadIdx.x;
-    double gmax = 0.0;
+    unsigned long long gmax = 0ull;
     if (i < nI) {
       const int L = A.lvl[MR_CLS_INT][i];
       const uint32_t code = A.code[MR_CLS_INT][i];
@@ -118,10 +122,13 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
           for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) v[kk] = mr_ld(sv[kk], p);
 #pragma unroll
           for (int ci = 0; ci < (1 << D); ++ci) c[ci] = mr_ld(cv[ci], p);
+          double pr[1 << D];
+          mr_predict_children_canonical<D>(v, g.cross_sign, pr);
 #pragma unroll
           for (int ci = 0; ci < (1 << D); ++ci) {
-            double det = __dsub_rn(c[ci], mr_predict_canonical<D>(v, ci, g.cross_sign));
-            gmax = fmax(gmax, fabs(det));
+            const unsigned long long a =
+                (unsigned long long)__double_as_longlong(__dsub_rn(c[ci], pr[ci])) & 0x7fffffffffffffffull;
+            gmax = a > gmax ? a : gmax;
           }
         }
       }
@@ -129,9 +136,10 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
     red[threadIdx.y][threadIdx.x] = gmax;
     __syncthreads();
     if (threadIdx.y == 0 && i < nI) {
-      double m = red[0][threadIdx.x];
+      unsigned long long mb = red[0][threadIdx.x];
 #pragma unroll
-      for (int kk = 1; kk < PY; ++kk) m = fmax(m, red[kk][threadIdx.x]);
+      for (int kk = 1; kk < PY; ++kk) mb = red[kk][threadIdx.x] > mb ? red[kk][threadIdx.x] : mb;
+      const double m = __longlong_as_double((long long)mb);
       A.G[i] = m;
     }
     __syncthreads();

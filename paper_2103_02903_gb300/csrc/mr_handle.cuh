@@ -50,6 +50,7 @@ struct mr_lbm : Exec {
   int32_t* inidx = nullptr;
   unsigned long long* vol = nullptr;
   double* W = nullptr;
+  float* Wf = nullptr;
   double* dense[2] = {nullptr, nullptr};
   size_t dense_elems = 0;
   void* staging = nullptr;

@@ -67,6 +67,11 @@ struct Geo {
   double dxJ;                  // finest cell size
   double feq0[MR_MAXQ];        // equilibrium populations at (rho0, 0, 0)
   double bcv[MR_MAXQ];         // f^{h,eq} - f^{h dagger,eq} at (rho0, u0): bounce back with velocity
+  // FP32 copies of the constants used by FP32 arithmetic (no per-cell conversion)
+  struct {
+    float lambda, inv_lambda, cross_sign;
+    float s[16], phys[8], off[MR_MAXQ], feq0[MR_MAXQ], bcv[MR_MAXQ];
+  } f32;
 };
 
 // Storage / compute forms: populations are stored as S and transported and
@@ -192,6 +197,7 @@ struct __align__(16) InstDev {
   uint8_t* cls;       // dense: classification of the new mesh
   int* bcounts;       // per dense chunk: leaf / internal / ghost counts, then offsets
   const double* W;    // flattened weights, MR_WIDX layout
+  const float* Wf;    // the same in FP32
 };
 
 // Instances of one scheme and storage form, stepped by shared launches: every

@@ -23,9 +23,10 @@ __device__ __forceinline__ double level_eps(const Geo& g, int l) { return ldexp(
 #define MR_INT_TILES_BEGIN(IB, N, CUR, G_, A_, I_)                                              \
   extern __shared__ int pre[];                                                                \
   __shared__ InstDev si;                                                                      \
+  int have = -1;                                                                              \
+  mr_inst_prefetch(si, have, IB, N);                                                          \
   const int tiles =                                                                           \
       mr_group_prefix(pre, N, [&](int b) { return (IB[b].mesh[CUR].cnt->total[MR_CLS_INT] + 255) / 256; }); \
-  int have = -1;                                                                              \
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {                                        \
     const int b = mr_group_find(pre, N, t);                                                   \
     mr_inst_use(si, have, IB, b);                                                             \
@@ -92,12 +93,13 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
   // refined cells cluster, and interleaving spreads their cascades
   extern __shared__ int pre[];
   __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, n);
   const int tiles = mr_group_prefix(pre, n, [&](int b) {
     const Geo& gb = IB[b].g;
     return gb.J > gb.Jmin + 1 ? (int)((gb.base[gb.J] - gb.base[gb.Jmin + 1] + 255) / 256) : 0;
   });
   const int noff = D == 2 ? 9 : 3;
-  int have = -1;
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int b = mr_group_find(pre, n, t);
     mr_inst_use(si, have, IB, b);

@@ -37,10 +37,10 @@ struct Scheme<0> {
   __device__ static int sign(int p) { return p == 0 ? 1 : -1; }
   __device__ static int opp(int p) { return 1 - p; }
   template <class C>
-  __device__ static C meq1(const Geo& g, C m0) { return (C)g.phys[0] * m0; }
+  __device__ static C meq1(const Geo& g, C m0) { return MR_K(C, g, phys[0]) * m0; }
   template <class C>
   __device__ static void collide(const Geo& g, C* f) {
-    const C L = (C)g.lambda, s = (C)g.s[0];
+    const C L = MR_K(C, g, lambda), s = MR_K(C, g, s[0]);
     const C m0 = f[0] + f[1];
     C m1 = L * (f[0] - f[1]);
     m1 = ((C)1 - s) * m1 + s * meq1<C>(g, m0);
@@ -61,7 +61,7 @@ struct Scheme<1> : Scheme<0> {
   __device__ static C meq1(const Geo&, C m0) { return (C)0.5 * m0 * m0; }
   template <class C>
   __device__ static void collide(const Geo& g, C* f) {
-    const C L = (C)g.lambda, s = (C)g.s[0];
+    const C L = MR_K(C, g, lambda), s = MR_K(C, g, s[0]);
     const C m0 = f[0] + f[1];
     C m1 = L * (f[0] - f[1]);
     m1 = ((C)1 - s) * m1 + s * meq1<C>(g, m0);
@@ -85,7 +85,7 @@ struct Scheme<2> {
   __device__ static int opp(int p) { return p == 0 ? 0 : 3 - p; }
   template <class C>
   __device__ static void collide(const Geo& g, C* f) {
-    const C L = (C)g.lambda, s = (C)g.s[0], gr = (C)g.phys[0];
+    const C L = MR_K(C, g, lambda), s = MR_K(C, g, s[0]), gr = MR_K(C, g, phys[0]);
     const C m0 = f[0] + f[1] + f[2];
     const C m1 = L * (f[1] - f[2]);
     C m2 = L * L * (f[1] + f[2]);
@@ -114,7 +114,7 @@ struct Scheme<3> {
   __device__ static int opp(int p) { return (p & ~3) | ((p + 2) & 3); }
   template <class C>
   __device__ static void fluxes(const Geo& g, const C* u, C* fx, C* fy) {
-    const C rho = u[0], mx = u[1], my = u[2], E = u[3], gam = (C)g.phys[0];
+    const C rho = u[0], mx = u[1], my = u[2], E = u[3], gam = MR_K(C, g, phys[0]);
     const C irho = (C)1 / rho;  // one division per cell
     const C vx = mx * irho, vy = my * irho;
     const C pr = (gam - (C)1) * (E - (C)0.5 * (mx * vx + my * vy));
@@ -123,7 +123,7 @@ struct Scheme<3> {
   }
   template <class C>
   __device__ static void from_moments(const Geo& g, C m0, C m1, C m2, C m3, C* f) {
-    const C il = (C)g.inv_lambda, il2 = il * il;
+    const C il = MR_K(C, g, inv_lambda), il2 = il * il;
     const C a = (C)0.25 * m0, b = (C)0.5 * m1 * il, c = (C)0.5 * m2 * il, e = (C)0.25 * m3 * il2;
     f[0] = a + b + e;
     f[1] = a + c - e;
@@ -132,7 +132,7 @@ struct Scheme<3> {
   }
   template <class C>
   __device__ static void collide(const Geo& g, C* f) {
-    const C L = (C)g.lambda;
+    const C L = MR_K(C, g, lambda);
     C m[4][4], u[4], fx[4], fy[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -146,7 +146,7 @@ struct Scheme<3> {
     fluxes<C>(g, u, fx, fy);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const C sq = (C)g.s[i], sxy = (C)g.s[4 + i];
+      const C sq = MR_K(C, g, s[i]), sxy = MR_K(C, g, s[4 + i]);
       const C m1 = ((C)1 - sq) * m[i][1] + sq * fx[i];
       const C m2 = ((C)1 - sq) * m[i][2] + sq * fy[i];
       const C m3 = ((C)1 - sxy) * m[i][3];
@@ -225,7 +225,7 @@ struct Scheme<4> {
     mu[7] = (f[1] - f[2]) + (f[3] - f[4]);
     mu[8] = (f[5] - f[6]) + (f[7] - f[8]);
     equilibria<C>(mu[0], mu[1], mu[2], eq);
-    const C s1 = (C)g.s[0], s2 = (C)g.s[1];
+    const C s1 = MR_K(C, g, s[0]), s2 = MR_K(C, g, s[1]);
 #pragma unroll
     for (int r = 3; r < 9; ++r) {
       const C s = r < 7 ? s1 : s2;
@@ -258,7 +258,7 @@ __device__ __forceinline__ C bc_value(const Geo& g, int kind, const C* f, int p,
     case 1: return f[p];                    // copy
     case 2: return f[pd];                   // bounce back
     case 3: return -f[pd];                  // anti bounce back
-    case 4: return f[pd] + (C)g.bcv[p];     // bounce back with the wall velocity u0
+    case 4: return f[pd] + MR_K(C, g, bcv[p]);     // bounce back with the wall velocity u0
     default: return (C)0;
   }
 }
@@ -296,6 +296,24 @@ __device__ __forceinline__ float ld_c<float, __nv_bfloat16>(const ValPtr<__nv_bf
   return __bfloat162float(__ldg(v.p + (size_t)p * v.stride));
 }
 
+// Value of population p as arithmetic C, with the storage offset added back
+// in the 16-bit forms (no arithmetic at all in the others).
+template <int F>
+__device__ __forceinline__ typename FormT<F>::C ld_off(const ValPtr<typename FormT<F>::S>& v, int p,
+                                                       const typename FormT<F>::C* offv) {
+  using C = typename FormT<F>::C;
+  if constexpr (FormT<F>::offs)
+    return ld_c<C>(v, p) + offv[p];
+  else
+    return ld_c<C>(v, p);
+}
+
+// finiteness from the exponent bits (integer pipe, not the FP64 one)
+__device__ __forceinline__ bool is_finite_bits(double x) {
+  return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool is_finite_bits(float x) { return (__float_as_int(x) & 0x7f800000) != 0x7f800000; }
+
 template <int Q>
 struct PopRows {
   static constexpr int value = Q < 8 ? Q : 8;
@@ -310,11 +328,12 @@ __global__ void __launch_bounds__(256) k_remesh_copy(const InstDev* __restrict__
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
   __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, ngrp);
   const int tiles = mr_group_prefix(pre, ngrp, [&](int b) {
     const MeshCounts* c = IB[b].mesh[1 - cur].cnt;
     return (c->total[MR_CLS_LEAF] + c->total[MR_CLS_INT] + 31) / 32;
   });
-  int have = -1;
   for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
     const int b = mr_group_find(pre, ngrp, tt);
     mr_inst_use(si, have, IB, b);
@@ -356,6 +375,8 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
   __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, ngrp);
   const int tiles = mr_group_prefix(pre, ngrp, [&](int b) {
     const Geo& gb = IB[b].g;
     const int l = gb.Jmin + kl;
@@ -364,7 +385,6 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
     return (c->off[MR_CLS_GHOST][l + 1] - c->off[MR_CLS_GHOST][l] + c->off[MR_CLS_LEAF][l + 1] -
             c->off[MR_CLS_LEAF][l] + 31) / 32;
   });
-  int have = -1;
   for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
     const int b = mr_group_find(pre, ngrp, tt);
     mr_inst_use(si, have, IB, b);
@@ -375,7 +395,7 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
     const int gb = B.cnt->off[MR_CLS_GHOST][level], ge = B.cnt->off[MR_CLS_GHOST][level + 1];
     const int lb = B.cnt->off[MR_CLS_LEAF][level], le = B.cnt->off[MR_CLS_LEAF][level + 1];
     const int ng = ge - gb, total = ng + (le - lb);
-    const C cs = (C)g.cross_sign;
+    const C cs = MR_K(C, g, cross_sign);
     const int t = (tt - pre[b]) * 32 + threadIdx.x;
     if (t >= total) continue;
     uint32_t code;
@@ -420,13 +440,14 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
 // s > 0: R_{2k-1} - R_{2k+1} (the finest cell upwind of the leaf and the
 // leaf's last finest cell), s < 0: L_{2k+2} - L_{2k}.  The upwind term is
 // absent at a non-periodic boundary (that cell is outside the domain).
-__device__ __forceinline__ double corner_edge_weight(const Geo& g, const double* __restrict__ W, int l1, int a, int k,
+template <class C>
+__device__ __forceinline__ C corner_edge_weight(const Geo& g, const C* __restrict__ W, int l1, int a, int k,
                                                      int r, int s) {
   const int per = g.periodic[a], N1 = g.n[l1][a], N = g.n[l1 - 1][a];
   const int tab = s > 0 ? 2 : 3;
   const int cu = s > 0 ? 2 * k - 1 : 2 * k + 2, co = s > 0 ? 2 * k + 1 : 2 * k;
   const int du = 2 * k + r - cu, dd = 2 * k + r - co;
-  double w = 0.0;
+  C w = (C)0;
   if ((per || (s > 0 ? k > 0 : k < N - 1)) && du >= -2 && du <= 2)
     w += W[MR_WIDX(l1, a, mr_slot(per ? 2 : cu, N1, per), tab) + du + 2];
   if (dd >= -2 && dd <= 2) w -= W[MR_WIDX(l1, a, mr_slot(per ? 2 : co, N1, per), tab) + dd + 2];
@@ -450,7 +471,7 @@ __device__ __forceinline__ double corner_edge_weight(const Geo& g, const double*
 template <class Sc, int F>
 __device__ __forceinline__ void stream_corners(const Geo& g, const MeshDev& B,
                                                const typename FormT<F>::S* __restrict__ LFin,
-                                               const double* __restrict__ W, int l, int x, int y,
+                                               const typename FormT<F>::C* __restrict__ W, int l, int x, int y,
                                                const typename FormT<F>::C* f, const typename FormT<F>::C* offv,
                                                typename FormT<F>::C* out, typename FormT<F>::C scale2) {
   using S = typename FormT<F>::S;
@@ -458,8 +479,8 @@ __device__ __forceinline__ void stream_corners(const Geo& g, const MeshDev& B,
   constexpr int P0 = Sc::DIAG0;
   const int Nx = g.n[l][0], Ny = g.n[l][1];
   const int slx = mr_slot(x, Nx, g.periodic[0]), sly = mr_slot(y, Ny, g.periodic[1]);
-  const double* wx[2] = {W + MR_WIDX(l, 0, slx, 0), W + MR_WIDX(l, 0, slx, 1)};
-  const double* wy[2] = {W + MR_WIDX(l, 1, sly, 0), W + MR_WIDX(l, 1, sly, 1)};
+  const C* wx[2] = {W + MR_WIDX(l, 0, slx, 0), W + MR_WIDX(l, 0, slx, 1)};
+  const C* wy[2] = {W + MR_WIDX(l, 1, sly, 0), W + MR_WIDX(l, 1, sly, 1)};
   C acc[4] = {(C)0, (C)0, (C)0, (C)0};
   for (int b = 0; b < 5; ++b)
     for (int a = 0; a < 5; ++a) {
@@ -478,13 +499,13 @@ __device__ __forceinline__ void stream_corners(const Geo& g, const MeshDev& B,
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int p = P0 + t;
-        const double wab = wx[Sc::eta(p, 0) > 0 ? 0 : 1][a] * wy[Sc::eta(p, 1) > 0 ? 0 : 1][b];
-        const C v = self ? f[p] : ld_c<C>(vp, p) + offv[p];
-        acc[t] += (C)wab * v;
+        const C wab = wx[Sc::eta(p, 0) > 0 ? 0 : 1][a] * wy[Sc::eta(p, 1) > 0 ? 0 : 1][b];
+        const C v = self ? f[p] : ld_off<F>(vp, p, offv);
+        acc[t] += wab * v;
       }
     }
   if (l < g.J) {
-    const C cs = (C)g.cross_sign;
+    const C cs = MR_K(C, g, cross_sign);
     for (int nb = 0; nb < 9; ++nb) {
       if (nb == 4) continue;
       const int dx = nb % 3 - 1, dy = nb / 3 - 1;
@@ -504,7 +525,7 @@ __device__ __forceinline__ void stream_corners(const Geo& g, const MeshDev& B,
         mr_set_err(B.cnt, MR_DERR_INTERNAL);
         continue;
       }
-      double wcx[2][2], wcy[2][2];  // [sign index][child offset]
+      C wcx[2][2], wcy[2][2];  // [sign index][child offset]
 #pragma unroll
       for (int si = 0; si < 2; ++si)
 #pragma unroll
@@ -522,11 +543,11 @@ __device__ __forceinline__ void stream_corners(const Geo& g, const MeshDev& B,
         C corr = (C)0;
 #pragma unroll
         for (int ci = 0; ci < 4; ++ci) {
-          const double w = wcx[ix][ci & 1] * wcy[iy][ci >> 1];
-          if (w == 0.0) continue;
+          const C w = wcx[ix][ci & 1] * wcy[iy][ci >> 1];
+          if (w == (C)0) continue;
           // details are exact on constants: stored values suffice
           const C det = ld_c<C>(mr_resolve<S>(g, B, LFin, ce[ci]), p) - predict_c<2, C>(v, ci, cs);
-          corr += (C)w * det;
+          corr += w * det;
         }
         acc[t] += corr;
       }
@@ -612,9 +633,10 @@ __global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restric
   constexpr int D = Sc::D, Q = Sc::Q;
   extern __shared__ int pre[];
   __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, ngrp);
   const int tiles =
       mr_group_prefix(pre, ngrp, [&](int b) { return (IB[b].mesh[dst].cnt->total[MR_CLS_LEAF] + 127) / 128; });
-  int have = -1;
   for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
     const int b = mr_group_find(pre, ngrp, tt);
     mr_inst_use(si, have, IB, b);
@@ -622,8 +644,8 @@ __global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restric
     const MeshDev& B = si.mesh[dst];
     const S* __restrict__ LFin = (const S*)si.fscratch;
     S* __restrict__ LFout = (S*)si.fstate;
-    const double* __restrict__ W = si.W;
-    const C cs = (C)g.cross_sign;
+    const C* __restrict__ W = mr_wtab<C>(si);
+    const C cs = MR_K(C, g, cross_sign);
     const int i = (tt - pre[b]) * 128 + threadIdx.x;
     if (i >= B.cnt->total[MR_CLS_LEAF]) continue;
     const int l = B.lvl[MR_CLS_LEAF][i];
@@ -631,23 +653,23 @@ __global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restric
     C f[Q], out[Q], offv[Q];
 #pragma unroll
     for (int p = 0; p < Q; ++p) {
-      offv[p] = OFFS ? (C)g.off[p] : (C)0;
+      offv[p] = OFFS ? MR_K(C, g, off[p]) : (C)0;
       ValPtr<S> me{LFin + i, g.cap[0]};
-      f[p] = ld_c<C>(me, p) + offv[p];
+      f[p] = ld_off<F>(me, p, offv);
       out[p] = f[p];
     }
     if (do_stream) {
       int x, y;
       mr_decode(g, l, code, x, y);
-      const C scale = (C)ldexp(1.0, l - g.J);
+      const C scale = (C)__longlong_as_double((long long)(1023 + l - g.J) << 52);  // 2^{l-J}, exact
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         const int k = a == 0 ? x : y;
         const int N = g.n[l][a];
         const int per = g.periodic[a];
         const int slot = mr_slot(k, N, per);
-        const double* wP = W + MR_WIDX(l, a, slot, 0);
-        const double* wM = W + MR_WIDX(l, a, slot, 1);
+        const C* wP = W + MR_WIDX(l, a, slot, 0);
+        const C* wM = W + MR_WIDX(l, a, slot, 1);
         // window: delta = -2, -1, +1, +2 along a
         ValPtr<S> vp[4];
         bool has[4];
@@ -668,11 +690,11 @@ __global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restric
         for (int p = 0; p < Q; ++p) {
           const int sgn = eta_of<Sc>(p, a);
           if (sgn == 0) continue;
-          const double* w = sgn > 0 ? wP : wM;
-          C acc = (C)w[2] * f[p];
+          const C* w = sgn > 0 ? wP : wM;
+          C acc = w[2] * f[p];
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            if (has[q]) acc += (C)w[q < 2 ? q : q + 1] * (ld_c<C>(vp[q], p) + offv[p]);
+            if (has[q]) acc += w[q < 2 ? q : q + 1] * ld_off<F>(vp[q], p, offv);
           if (!per) {
             if (sgn > 0 && k == 0) acc += bc_value<C>(g, g.bc[2 * a], f, p, Sc::opp(p));
             if (sgn < 0 && k == N - 1) acc += bc_value<C>(g, g.bc[2 * a + 1], f, p, Sc::opp(p));
@@ -720,7 +742,7 @@ __global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restric
             else
               c = side > 0 ? 2 * k + 2 : 2 * k;
             const int cslot = mr_slot(per ? 2 : c, N1, per);
-            const double* wt = W + MR_WIDX(l + 1, a, cslot, sgn > 0 ? 2 : 3);
+            const C* wt = W + MR_WIDX(l + 1, a, cslot, sgn > 0 ? 2 : 3);
             // details are exact on constants: stored values suffice
             C v[D == 2 ? 9 : 3];
 #pragma unroll
@@ -732,7 +754,7 @@ __global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restric
               const int delta = 2 * (k + side) + sa - c;
               if (delta < -2 || delta > 2) continue;
               const C det = ld_c<C>(cv[ci], p) - predict_c<D, C>(v, ci, cs);
-              corr += (C)wt[delta + 2] * det;
+              corr += wt[delta + 2] * det;
             }
             corr *= (D == 2 ? (C)0.5 : (C)1);
             out[p] += scale * (incoming ? corr : -corr);
@@ -748,7 +770,7 @@ __global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restric
           const double phi = obstacle_fraction(g, l, code);
           if (phi > 0.0) {
 #pragma unroll
-            for (int p = 0; p < Q; ++p) out[p] = (C)phi * (C)g.feq0[p] + ((C)1 - (C)phi) * out[p];
+            for (int p = 0; p < Q; ++p) out[p] = (C)phi * MR_K(C, g, feq0[p]) + ((C)1 - (C)phi) * out[p];
           }
         }
       }
@@ -756,8 +778,11 @@ __global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restric
     bool finite = true;
 #pragma unroll
     for (int p = 0; p < Q; ++p) {
-      finite = finite && isfinite(out[p]);
-      LFout[(size_t)p * g.cap[0] + i] = mr_from_d<S>((double)(out[p] - offv[p]));
+      finite = finite && is_finite_bits(out[p]);
+      if constexpr (OFFS)
+        LFout[(size_t)p * g.cap[0] + i] = mr_from_f<S>((float)(out[p] - offv[p]));
+      else
+        LFout[(size_t)p * g.cap[0] + i] = (S)out[p];
     }
     if (!finite) mr_set_err(B.cnt, MR_DERR_NONFINITE);
   }

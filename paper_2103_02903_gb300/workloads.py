@@ -225,6 +225,27 @@ def vortices_2d(seed: int = 0, max_level: int = 8, min_level: int = 2, eps: floa
     return cfg, np.stack([rho, rho * ux, rho * uy]).astype(np.float64)
 
 
+def serving_batch(seed: int = 0, n: int = 256, levels=(6, 7, 8, 9, 10), eps=(1e-3, 1e-4),
+                  precision: str = "fp16"):
+    """Independent instances of a batched serving load: half D2Q9 periodic
+    vortex flows, half D2Q4^4 four-quadrant Riemann problems, each with a
+    finest level drawn from ``levels`` and a threshold from ``eps``.
+    Returns a list of (config, conserved)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        J = int(rng.choice(levels))
+        e = float(rng.choice(eps))
+        s = int(rng.integers(0, 2 ** 31))
+        if i % 2 == 0:
+            cfg, u = vortices_2d(seed=s, max_level=J, eps=e)
+        else:
+            cfg, u = euler_2d(seed=s, max_level=J, eps=e)
+        cfg["precision"] = precision
+        out.append((cfg, u))
+    return out
+
+
 WORKLOADS = {
     "advection_1d": advection_1d,
     "burgers_1d": burgers_1d,
