@@ -220,6 +220,33 @@ const char* mr_lbm_strerror(mr_status s);
 mr_status mr_lbm_flattened_weights(int roots, int level, int max_level, int periodic, int k,
                                    double* out);
 
+/* ------------------------------------------------------------------ adjoint
+ * Gradients of a functional of the trajectory through the time steps with
+ * the mesh of every step frozen (the adaptation decisions of the forward
+ * pass are replayed, not differentiated).  The transfer, ghost prediction,
+ * projection and transport are linear for a given mesh; their adjoints are
+ * transposed scatters, and the collision (and obstacle) Jacobians come from
+ * the scheme's own code on dual numbers.  Memory: a checkpoint of the leaves
+ * every `checkpoint_every` steps; the backward pass replays one segment at
+ * a time from its checkpoint, recording its meshes and pre-collision states.
+ *
+ * Functionals, with E(x) = sum over the leaves of |cell| |q|^2 / (2 rho)
+ * (conserved moments rho = u_0, q = (u_1, u_2); 1/2 u_0^2 for a scheme with
+ * one conserved moment; |cell| = dx^d 2^{d (J - level)}):
+ *   MR_FUNCTIONAL_KE_SUM:   J = sum_{n = 1..nsteps} E(x_n),
+ *   MR_FUNCTIONAL_KE_FINAL: J = E(x_nsteps). */
+typedef enum { MR_FUNCTIONAL_KE_SUM = 1, MR_FUNCTIONAL_KE_FINAL = 2 } mr_functional;
+
+/* Initialise from `conserved0` (layout and `on_device` as mr_lbm_init), run
+ * `nsteps` steps, and return J (*J_out, host), dJ/d conserved0
+ * (grad_conserved0, same layout and memory kind as conserved0) and dJ/d s
+ * (grad_s[16], host, for the 16 relaxation-rate slots of the config).  With
+ * both gradient pointers NULL only J is computed.  FP64 form only
+ * (MR_EINVAL otherwise); a batch member returns MR_ESTATE.  On return the
+ * handle holds the state after nsteps steps.  Synchronises. */
+mr_status mr_lbm_adjoint(mr_lbm_t h, const double* conserved0, int on_device, int nsteps, int checkpoint_every,
+                         int functional, double* J_out, double* grad_conserved0, double* grad_s);
+
 /* ------------------------------------------------------------------ batches
  * Many independent solvers (any mix of schemes, levels, thresholds and
  * forms) stepped together: every kernel of a time step runs once for all

@@ -23,6 +23,7 @@ SCHEMES = {"d1q2_advection": 0, "d1q2_burgers": 1, "d1q3_shallow_water": 2, "d2q
            "d2q9_ns": 4}
 BCS = {"periodic": 0, "copy": 1, "bounce_back": 2, "anti_bounce_back": 3, "bounce_back_velocity": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+FUNCTIONALS = {"ke_sum": 1, "ke_final": 2}
 NCONS = {0: 1, 1: 1, 2: 2, 3: 4, 4: 3}
 NPOP = {0: 2, 1: 2, 2: 3, 3: 16, 4: 9}
 DIM = {0: 1, 1: 1, 2: 1, 3: 2, 4: 2}
@@ -87,6 +88,8 @@ def library():
         L.mr_lbm_strerror.argtypes = [i]
         L.mr_lbm_strerror.restype = C.c_char_p
         L.mr_lbm_flattened_weights.argtypes = [i, i, i, i, i, vp]
+        L.mr_lbm_adjoint.argtypes = [vp, vp, i, i, i, i, C.POINTER(d), vp, vp]
+        L.mr_lbm_adjoint.restype = i
         L.mr_lbm_batch_create.argtypes = [C.POINTER(MrConfig), i, vp, C.POINTER(vp)]
         L.mr_lbm_batch_instance.argtypes = [vp, i, C.POINTER(vp)]
         L.mr_lbm_batch_step.argtypes = [vp, i]
@@ -285,6 +288,26 @@ class Solver:
 
     def synchronize(self):
         _check(library().mr_lbm_synchronize(self.h), "mr_lbm_synchronize")
+
+    def adjoint(self, conserved0, nsteps: int, checkpoint_every: int = 100, functional: str = "ke_sum",
+                gradients: bool = True):
+        """mr_lbm_adjoint: (J, dJ/d conserved0 [ncons, N_J], dJ/d s [16]).
+        conserved0 is a numpy array (gradient returned as numpy) or a CUDA
+        tensor (gradient returned as a CUDA tensor)."""
+        kind = FUNCTIONALS[functional] if isinstance(functional, str) else int(functional)
+        if isinstance(conserved0, np.ndarray):
+            conserved0 = np.ascontiguousarray(conserved0, np.float64)
+            grad = np.zeros_like(conserved0) if gradients else None
+        else:
+            import torch
+            grad = torch.zeros_like(conserved0) if gradients else None
+        gs = np.zeros(16, np.float64)
+        J = C.c_double()
+        p, dev = _ptr(conserved0)
+        gp, _ = _ptr(grad)
+        _check(library().mr_lbm_adjoint(self.h, p, dev, int(nsteps), int(checkpoint_every), kind, C.byref(J), gp,
+                                        gs.ctypes.data if gradients else None), "mr_lbm_adjoint")
+        return J.value, grad, (gs if gradients else None)
 
 
 class Batch:

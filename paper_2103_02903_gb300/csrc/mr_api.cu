@@ -990,6 +990,196 @@ mr_status mr_lbm_synchronize(mr_lbm_t h) {
 
 }  // extern "C"
 
+// ----------------------------------------------------------------- adjoint
+namespace {
+
+// Device memory owned by one adjoint run, released on every return path.
+struct AdjArena {
+  std::vector<void*> blocks;
+  ~AdjArena() {
+    for (void* p : blocks) cudaFree(p);
+  }
+  template <class T>
+  T* get(size_t count) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, (count ? count : 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    blocks.push_back(p);
+    return (T*)p;
+  }
+};
+
+// Structure of one mesh (what the adjoint kernels read), copied aside.
+struct MeshSnap {
+  MeshDev m;
+};
+
+bool snap_alloc(AdjArena& ar, const Geo& g, MeshSnap& s) {
+  const size_t dense = g.base[g.J + 1];
+  memset(&s.m, 0, sizeof(s.m));
+  bool ok = (s.m.map = ar.get<int32_t>(dense)) && (s.m.src = ar.get<int32_t>(g.cap[0])) &&
+            (s.m.cnt = ar.get<MeshCounts>(1));
+  for (int c = 0; c < 3 && ok; ++c) ok = (s.m.code[c] = ar.get<uint32_t>(g.cap[c])) && (s.m.lvl[c] = ar.get<uint8_t>(g.cap[c]));
+  return ok;
+}
+
+bool snap_copy(const Geo& g, const MeshDev& from, MeshSnap& s, cudaStream_t st) {
+  const size_t dense = g.base[g.J + 1];
+  bool ok = cudaMemcpyAsync(s.m.map, from.map, dense * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(s.m.src, from.src, g.cap[0] * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(s.m.cnt, from.cnt, sizeof(MeshCounts), cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+  for (int c = 0; c < 3 && ok; ++c)
+    ok = cudaMemcpyAsync(s.m.code[c], from.code[c], g.cap[c] * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) ==
+             cudaSuccess &&
+         cudaMemcpyAsync(s.m.lvl[c], from.lvl[c], g.cap[c], cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+  return ok;
+}
+
+// A saved state: the leaves of the current mesh (keys, levels, FP64 values).
+struct Checkpoint {
+  unsigned long long* keys = nullptr;
+  signed char* levels = nullptr;
+  double* f = nullptr;
+  long long n = 0;
+};
+
+mr_status save_state(mr_lbm* h, AdjArena& ar, Checkpoint& c) {
+  MeshCounts hc[2];
+  mr_status s = read_counts(h, hc);
+  if (s != MR_OK) return s;
+  c.n = hc[h->cur].total[MR_CLS_LEAF];
+  if (!c.keys) {
+    c.keys = ar.get<unsigned long long>(h->g.cap[0]);
+    c.levels = ar.get<signed char>(h->g.cap[0]);
+    c.f = ar.get<double>((size_t)h->g.Q * h->g.cap[0]);
+    if (!c.keys || !c.levels || !c.f) return fail(h, MR_ENOMEM);
+  }
+  mr_launch_leaves_out(h->g, h->mesh[h->cur], h->fstate, c.n, c.keys, c.levels, c.f, h->st, grid_for(h));
+  h->launches += 1;
+  return check_launch(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+mr_status mr_lbm_adjoint(mr_lbm_t h, const double* conserved0, int on_device, int nsteps, int checkpoint_every,
+                         int functional, double* J_out, double* grad_conserved0, double* grad_s) {
+  if (!h || !conserved0 || nsteps < 1 || checkpoint_every < 1) return MR_EINVAL;
+  if (functional != MR_FUNCTIONAL_KE_SUM && functional != MR_FUNCTIONAL_KE_FINAL) return MR_EINVAL;
+  if (h->sticky != MR_OK) return h->sticky;
+  if (h->batch) return MR_ESTATE;
+  const Geo& g = h->g;
+  if (g.form != MR_FORM_F64) return MR_EINVAL;
+  AdjArena ar;
+  const size_t NJ = g.ncode[g.J], ncb = (size_t)g.ncons * NJ;
+  // the initial field, kept on the device for the equilibrium's adjoint
+  double* cons = ar.get<double>(ncb);
+  double* dJ = ar.get<double>(1);
+  double* ds = ar.get<double>(16);
+  if (!cons || !dJ || !ds) return fail(h, MR_ENOMEM);
+  if (!cuda_ok(h, cudaMemcpyAsync(cons, conserved0, ncb * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st)) ||
+      !cuda_ok(h, cudaMemsetAsync(dJ, 0, sizeof(double), h->st)) ||
+      !cuda_ok(h, cudaMemsetAsync(ds, 0, 16 * sizeof(double), h->st)))
+    return MR_ECUDA;
+  mr_status s = mr_lbm_init(h, cons, 1);
+  if (s != MR_OK) return s;
+  const int K = checkpoint_every, nseg = (nsteps + K - 1) / K;
+  const double vol_J = g.d == 1 ? g.dxJ : g.dxJ * g.dxJ;
+  const int grid = grid_for(h, 4);
+  std::vector<Checkpoint> cps(nseg + 1);
+  // forward pass: the functional and a checkpoint every K steps
+  for (int n = 0; n < nsteps; ++n) {
+    if (n % K == 0 && (s = save_state(h, ar, cps[n / K])) != MR_OK) return s;
+    queue_steps(*h, 1, [h]() { run_step(*h, h->grp, h->cur); });
+    if (functional == MR_FUNCTIONAL_KE_SUM || n == nsteps - 1) {
+      mr_kinetic_energy(g, h->mesh[h->cur], (const double*)h->fstate, vol_J, dJ, h->st, grid);
+      h->launches += 1;
+    }
+  }
+  if ((s = check_launch(h)) != MR_OK) return s;
+  if (J_out && !cuda_ok(h, cudaMemcpyAsync(J_out, dJ, sizeof(double), cudaMemcpyDeviceToHost, h->st))) return MR_ECUDA;
+  if (!grad_conserved0 && !grad_s) return mr_lbm_synchronize(h);
+  if ((s = save_state(h, ar, cps[nseg])) != MR_OK) return s;  // the final state, restored at the end
+
+  // backward pass, one segment at a time: replay the segment from its
+  // checkpoint recording meshes and pre-collision states, then sweep back
+  const size_t QL = (size_t)g.Q * g.cap[0];
+  double* lam = ar.get<double>(QL);
+  double* aLB = ar.get<double>(QL);
+  double* aIB = ar.get<double>((size_t)g.Q * g.cap[1]);
+  double* aGB = ar.get<double>((size_t)g.Q * g.cap[2]);
+  double* aIA = ar.get<double>((size_t)g.Q * g.cap[1]);
+  double* aLA = ar.get<double>(QL);
+  std::vector<MeshSnap> tape(K + 1);
+  std::vector<double*> z(K);
+  bool ok = lam && aLB && aIB && aGB && aIA && aLA;
+  for (int j = 0; j <= K && ok; ++j) ok = snap_alloc(ar, g, tape[j]) && (j == K || (z[j] = ar.get<double>(QL)));
+  if (!ok) return fail(h, MR_ENOMEM);
+  if (!cuda_ok(h, cudaMemsetAsync(lam, 0, QL * sizeof(double), h->st))) return MR_ECUDA;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int n0 = sg * K, n1 = std::min(nsteps, n0 + K);
+    const Checkpoint& c = cps[sg];
+    if ((s = mr_lbm_set_leaves(h, c.n, c.keys, c.levels, c.f, 1)) != MR_OK) return s;
+    if (!snap_copy(g, h->mesh[h->cur], tape[0], h->st)) return fail(h, MR_ECUDA);
+    for (int n = n0; n < n1; ++n) {
+      const int j = n - n0;
+      run_adapt(*h, h->grp, h->cur);
+      mr_launch_stream_collide(h->grp, 1 - h->cur, 1, 0, h->st);  // stored state <- transport only
+      if (!cuda_ok(h, cudaMemcpyAsync(z[j], h->fstate, QL * sizeof(double), cudaMemcpyDeviceToDevice, h->st)) ||
+          !cuda_ok(h, cudaMemcpyAsync(h->fscratch, h->fstate, QL * sizeof(double), cudaMemcpyDeviceToDevice, h->st)))
+        return MR_ECUDA;
+      mr_launch_stream_collide(h->grp, 1 - h->cur, 0, 1, h->st);  // collision (and obstacle) of it
+      h->launches += 2;
+      h->cur = 1 - h->cur;
+      if (!snap_copy(g, h->mesh[h->cur], tape[j + 1], h->st)) return fail(h, MR_ECUDA);
+    }
+    for (int n = n1 - 1; n >= n0; --n) {
+      const int j = n - n0;
+      const MeshDev& A = tape[j].m;
+      const MeshDev& B = tape[j + 1].m;
+      const int src = functional == MR_FUNCTIONAL_KE_SUM || n == nsteps - 1;
+      mr_adj_collide(g, B, z[j], lam, ds, src, vol_J, h->st, grid);
+      bool zok = cudaMemsetAsync(aLB, 0, QL * sizeof(double), h->st) == cudaSuccess &&
+                 cudaMemsetAsync(aIB, 0, (size_t)g.Q * g.cap[1] * sizeof(double), h->st) == cudaSuccess &&
+                 cudaMemsetAsync(aGB, 0, (size_t)g.Q * g.cap[2] * sizeof(double), h->st) == cudaSuccess &&
+                 cudaMemsetAsync(aLA, 0, QL * sizeof(double), h->st) == cudaSuccess &&
+                 cudaMemsetAsync(aIA, 0, (size_t)g.Q * g.cap[1] * sizeof(double), h->st) == cudaSuccess;
+      if (!cuda_ok(h, zok ? cudaSuccess : cudaErrorUnknown)) return MR_ECUDA;
+      mr_adj_transport(g, B, h->W, lam, aLB, aIB, aGB, h->st, grid);
+      for (int l = g.J; l > g.Jmin; --l) mr_adj_predict(g, B, l, aLB, aIB, aGB, h->st, grid);
+      mr_adj_transfer(g, A, B, aLB, aIB, aLA, aIA, h->st, grid);
+      for (int l = g.Jmin; l < g.J; ++l) mr_adj_project(g, A, l, aLA, aIA, h->st, grid);
+      h->launches += 3 + 2 * (g.J - g.Jmin);
+      std::swap(lam, aLA);
+    }
+    if ((s = check_launch(h)) != MR_OK) return s;
+  }
+  // lam: adjoint of the initial populations on the full finest mesh
+  double* grad = ar.get<double>(ncb);
+  if (!grad) return fail(h, MR_ENOMEM);
+  mr_adj_init(g, tape[0].m, cons, lam, grad, h->st, grid);
+  h->launches += 1;
+  if (grad_conserved0 &&
+      !cuda_ok(h, cudaMemcpyAsync(grad_conserved0, grad, ncb * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st)))
+    return MR_ECUDA;
+  if (grad_s && !cuda_ok(h, cudaMemcpyAsync(grad_s, ds, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->st)))
+    return MR_ECUDA;
+  // device errors of the tape meshes (the adjoint kernels flag there)
+  std::vector<MeshCounts> tc(K + 1);
+  for (int j = 0; j <= K; ++j)
+    if (!cuda_ok(h, cudaMemcpyAsync(&tc[j], tape[j].m.cnt, sizeof(MeshCounts), cudaMemcpyDeviceToHost, h->st)))
+      return MR_ECUDA;
+  if (!cuda_ok(h, cudaStreamSynchronize(h->st))) return MR_ECUDA;
+  for (int j = 0; j <= K; ++j)
+    if (tc[j].err & MR_DERR_INTERNAL) return fail(h, MR_EINTERNAL);
+  const Checkpoint& last = cps[nseg];
+  return mr_lbm_set_leaves(h, last.n, last.keys, last.levels, last.f, 1);
+}
+
+}  // extern "C"
+
 // ----------------------------------------------------------------- batches
 struct mr_lbm_batch : Exec {
   std::vector<mr_lbm*> inst;  // in the caller's order

@@ -70,9 +70,9 @@ __device__ __forceinline__ __nv_bfloat16 mr_from_f<__nv_bfloat16>(float v) { ret
 // A constant of the geometry in the arithmetic type C: the FP64 value, or
 // its FP32 copy (MR_K(C, g, s[0]) and the like).
 template <class C>
-__device__ __forceinline__ C mr_k(double d, float f);
-template <>
-__device__ __forceinline__ double mr_k<double>(double d, float) { return d; }
+__device__ __forceinline__ C mr_k(double d, float) {
+  return C(d);
+}
 template <>
 __device__ __forceinline__ float mr_k<float>(double, float f) { return f; }
 #define MR_K(C, g, field) mr_k<C>((g).field, (g).f32.field)

@@ -262,3 +262,19 @@ void mr_launch_leaves_out(const Geo& g, const MeshDev& B, const void* LF, long l
 void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int level,
                              const double* prev, double* cur, cudaStream_t st, int grid);
 size_t mr_form_bytes(int form);  // bytes per stored population value
+
+// Adjoint kernels (mr_adjoint.cu), FP64, one instance; A = mesh of step n,
+// B = mesh of step n + 1, adjoint arrays in the layout of the value arrays.
+void mr_adj_collide(const Geo& g, const MeshDev& B, const double* z, double* lam, double* ds, int source,
+                    double vol_J, cudaStream_t st, int grid);
+void mr_adj_transport(const Geo& g, const MeshDev& B, const double* W, const double* mu, double* aL, double* aI,
+                      double* aG, cudaStream_t st, int grid);
+void mr_adj_predict(const Geo& g, const MeshDev& B, int level, double* aL, double* aI, double* aG, cudaStream_t st,
+                    int grid);
+void mr_adj_transfer(const Geo& g, const MeshDev& A, const MeshDev& B, const double* aLB, const double* aIB,
+                     double* aLA, double* aIA, cudaStream_t st, int grid);
+void mr_adj_project(const Geo& g, const MeshDev& A, int level, double* aLA, double* aIA, cudaStream_t st, int grid);
+void mr_adj_init(const Geo& g, const MeshDev& B, const double* cons, const double* lam, double* grad,
+                 cudaStream_t st, int grid);
+void mr_kinetic_energy(const Geo& g, const MeshDev& B, const double* LF, double vol_J, double* J, cudaStream_t st,
+                       int grid);
