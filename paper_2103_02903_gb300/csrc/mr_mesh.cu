@@ -45,6 +45,8 @@ __global__ void __launch_bounds__(256) k_flags_T(const InstDev* __restrict__ IB,
     int l = L;
     uint32_t c = A.code[MR_CLS_INT][i];
     for (;;) {
+      // a plain load first: most ancestors are already marked
+      if (flags[g.base[l] + c] & MR_F_T) break;
       uint32_t old = mr_atomic_or_byte(flags, g.base[l] + c, MR_F_T);
       if ((old & MR_F_T) || l == g.Jmin) break;
       --l;
@@ -71,7 +73,8 @@ __global__ void __launch_bounds__(256) k_flags_H(const InstDev* __restrict__ IB,
       for (int h = 0; h < g.q; ++h) {
         int nx = cx - g.eta[h][0], ny = D == 2 ? cy - g.eta[h][1] : 0;
         if (!mr_nbr_mesh(g, L + 1, nx, ny)) continue;
-        mr_atomic_or_byte(flags, g.base[L] + mr_encode(g, L, nx >> 1, ny >> 1), MR_F_H);
+        const uint32_t gi = g.base[L] + mr_encode(g, L, nx >> 1, ny >> 1);
+        if (!(flags[gi] & MR_F_H)) mr_atomic_or_byte(flags, gi, MR_F_H);
       }
     }
     // refinement rule (Sec. 5.1): J_min < L+1 < J and group norm >= 2^{mu+d} eps_{L+1}
@@ -129,7 +132,9 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
       if (!mr_nbr_mesh(g, L, nx, ny)) continue;
       const int tl = L - 1;
       const int px = nx >> 1, py = ny >> 1;
-      const uint32_t old = mr_atomic_or_byte(flags, g.base[tl] + mr_encode(g, tl, px, py), MR_F_G);
+      const uint32_t gt = g.base[tl] + mr_encode(g, tl, px, py);
+      if (flags[gt] & (MR_F_H | MR_F_G)) continue;  // refined already: nothing to cascade
+      const uint32_t old = mr_atomic_or_byte(flags, gt, MR_F_G);
       if (!(old & (MR_F_H | MR_F_G)) && tl > g.Jmin && sp < MR_MAXL) {
         sl[sp] = tl;
         sx[sp] = px;
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
       }
       if (!mr_nbr_mesh(g, l, nx, ny)) continue;
       const uint32_t gw = g.base[l] + mr_encode(g, l, nx, ny);
-      if (cls[gw] & 3u) continue;
+      if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree, or marked already
       const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
       if (old & MR_C_GHOST) continue;
       // cascade: the stencil of the ghost's parent, towards coarser levels
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
         int ax = sx[t] + (kk % 3) - 1, ay = D == 2 ? sy[t] + (kk / 3) - 1 : 0;
         if (!mr_nbr_mesh(g, L, ax, ay)) continue;
         const uint32_t ga = g.base[L] + mr_encode(g, L, ax, ay);
-        if (cls[ga] & 3u) continue;
+        if (cls[ga] & (3u | MR_C_GHOST)) continue;
         const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
         if ((o2 & MR_C_GHOST) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
         sl[sp] = L - 1;
