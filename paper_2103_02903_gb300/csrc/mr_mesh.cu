@@ -89,7 +89,23 @@ __global__ void __launch_bounds__(256) k_flags_H(const InstDev* __restrict__ IB,
 // Every refined cell p of level L >= J_min+1 needs the 3^d stencil of its
 // children (the cells around p on level L) in the tree, i.e. the parents of
 // those cells refined on level L-1.  The thread that newly refines a cell
-// continues the cascade from it, depth first, towards J_min.
+// continues the cascade from it, depth first, towards J_min.  Each frame of
+// the cascade first reads the flags of all its parents together (independent
+// loads) and keeps a bit mask of those not refined yet; only those are then
+// set one by one with the atomic OR.
+template <int D>
+__device__ __forceinline__ uint32_t grade_need(const Geo& g, const uint8_t* flags, int L, int x, int y) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int k = 0; k < (D == 2 ? 9 : 3); ++k) {
+    int nx = x + (k % 3) - 1, ny = D == 2 ? y + (k / 3) - 1 : 0;
+    if (!mr_nbr_mesh(g, L, nx, ny)) continue;
+    const uint32_t gt = g.base[L - 1] + mr_encode(g, L - 1, nx >> 1, ny >> 1);
+    if (!(flags[gt] & (MR_F_H | MR_F_G))) m |= 1u << k;
+  }
+  return m;
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, int n) {
   // tiles of 256 cells strided over the grid (not one block per chunk):
@@ -102,7 +118,6 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
     const Geo& gb = IB[b].g;
     return gb.J > gb.Jmin + 1 ? (int)((gb.base[gb.J] - gb.base[gb.Jmin + 1] + 255) / 256) : 0;
   });
-  const int noff = D == 2 ? 9 : 3;
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int b = mr_group_find(pre, n, t);
     mr_inst_use(si, have, IB, b);
@@ -114,32 +129,31 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
     const int l0 = mr_level_of(g, gi);
     const uint32_t c0 = gi - g.base[l0];
     if (c0 >= g.ncode[l0]) continue;
-    int sl[MR_MAXL], sx[MR_MAXL], sy[MR_MAXL], sk[MR_MAXL];
+    int sl[MR_MAXL], sx[MR_MAXL], sy[MR_MAXL];
+    uint32_t sm[MR_MAXL];
     int sp = 1;
     sl[0] = l0;
     mr_decode(g, l0, c0, sx[0], sy[0]);
-    sk[0] = 0;
+    sm[0] = grade_need<D>(g, flags, l0, sx[0], sy[0]);
     while (sp > 0) {
       const int t = sp - 1;
-      const int k = sk[t];
-      if (k == noff) {
+      if (sm[t] == 0u) {
         --sp;
         continue;
       }
-      sk[t] = k + 1;
+      const int k = __ffs(sm[t]) - 1;
+      sm[t] &= sm[t] - 1u;
       const int L = sl[t];
       int nx = sx[t] + (k % 3) - 1, ny = D == 2 ? sy[t] + (k / 3) - 1 : 0;
-      if (!mr_nbr_mesh(g, L, nx, ny)) continue;
+      mr_nbr_mesh(g, L, nx, ny);  // inside: only such cells enter the mask
       const int tl = L - 1;
       const int px = nx >> 1, py = ny >> 1;
-      const uint32_t gt = g.base[tl] + mr_encode(g, tl, px, py);
-      if (flags[gt] & (MR_F_H | MR_F_G)) continue;  // refined already: nothing to cascade
-      const uint32_t old = mr_atomic_or_byte(flags, gt, MR_F_G);
+      const uint32_t old = mr_atomic_or_byte(flags, g.base[tl] + mr_encode(g, tl, px, py), MR_F_G);
       if (!(old & (MR_F_H | MR_F_G)) && tl > g.Jmin && sp < MR_MAXL) {
         sl[sp] = tl;
         sx[sp] = px;
         sy[sp] = py;
-        sk[sp] = 0;
+        sm[sp] = grade_need<D>(g, flags, tl, px, py);
         ++sp;
       }
     }
@@ -176,6 +190,35 @@ __global__ void __launch_bounds__(256) k_full_mesh(Geo g, uint8_t* cls) {
 // window), and, for a lattice with diagonal velocities, the whole 5 x 5
 // block around the leaf.  Those outside R(Lambda) are ghosts: predicted from
 // level l-1, whose stencil cells outside R(Lambda) are ghosts in turn.
+// The classes of a window (and of each stencil of the cascade) are read
+// together first, as independent loads; only the cells still unmarked are
+// then marked one by one with the atomic OR.
+template <int D>
+__device__ __forceinline__ uint32_t ghost_stencil_need(const Geo& g, const uint8_t* cls, int L, int x, int y) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int k = 0; k < (D == 2 ? 9 : 3); ++k) {
+    int ax = x + (k % 3) - 1, ay = D == 2 ? y + (k / 3) - 1 : 0;
+    if (!mr_nbr_mesh(g, L, ax, ay)) continue;
+    if (!(cls[g.base[L] + mr_encode(g, L, ax, ay)] & (3u | MR_C_GHOST))) m |= 1u << k;
+  }
+  return m;
+}
+
+// window cell w of a leaf at (x, y): the 5 x 5 block (w = 5 row + column)
+// or the axis windows (w = 4 axis + k, offsets -2, -1, +1, +2)
+__device__ __forceinline__ void ghost_window_cell(bool block, int w, int x, int y, int& nx, int& ny) {
+  if (block) {
+    nx = x + w % 5 - 2;
+    ny = y + w / 5 - 2;
+  } else {
+    const int axis = w >> 2, k = w & 3;
+    const int off = k < 2 ? k - 2 : k - 1;
+    nx = x + (axis == 0 ? off : 0);
+    ny = y + (axis == 1 ? off : 0);
+  }
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__ IB,
                                                      const int* __restrict__ chunk_pre, int n) {
@@ -185,58 +228,62 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
   const Geo& g = si.g;
   uint8_t* cls = si.cls;
   const bool block = D == 2 && g.diag;
-  const int nwin = block ? 25 : 4 * D;
   MR_DENSE_CHUNK_BEGIN(g, chunk, l, c, gi)
     if ((cls[gi] & 3u) != MR_C_LEAF) continue;
     int x, y;
     mr_decode(g, l, c, x, y);
-    for (int w = 0; w < nwin; ++w) {
-      int nx, ny;
-      if (block) {
+    uint32_t need = 0;
+    if (block) {
+#pragma unroll
+      for (int w = 0; w < 25; ++w) {
         if (w == 12) continue;  // the leaf itself
-        nx = x + w % 5 - 2;
-        ny = y + w / 5 - 2;
-      } else {
-        const int axis = w >> 2, k = w & 3;
-        const int off = k < 2 ? k - 2 : k - 1;  // -2, -1, +1, +2
-        nx = x + (axis == 0 ? off : 0);
-        ny = y + (axis == 1 ? off : 0);
+        int nx, ny;
+        ghost_window_cell(true, w, x, y, nx, ny);
+        if (!mr_nbr_mesh(g, l, nx, ny)) continue;
+        if (!(cls[g.base[l] + mr_encode(g, l, nx, ny)] & (3u | MR_C_GHOST))) need |= 1u << w;
       }
-      if (!mr_nbr_mesh(g, l, nx, ny)) continue;
-      const uint32_t gw = g.base[l] + mr_encode(g, l, nx, ny);
-      if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree, or marked already
-      const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
-      if (old & MR_C_GHOST) continue;
+    } else {
+#pragma unroll
+      for (int w = 0; w < 4 * D; ++w) {
+        int nx, ny;
+        ghost_window_cell(false, w, x, y, nx, ny);
+        if (!mr_nbr_mesh(g, l, nx, ny)) continue;
+        if (!(cls[g.base[l] + mr_encode(g, l, nx, ny)] & (3u | MR_C_GHOST))) need |= 1u << w;
+      }
+    }
+    while (need) {
+      const int w = __ffs(need) - 1;
+      need &= need - 1u;
+      int nx, ny;
+      ghost_window_cell(block, w, x, y, nx, ny);
+      mr_nbr_mesh(g, l, nx, ny);  // inside: only such cells enter the mask
+      const uint32_t old = mr_atomic_or_byte(cls, g.base[l] + mr_encode(g, l, nx, ny), MR_C_GHOST);
+      if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
       // cascade: the stencil of the ghost's parent, towards coarser levels
-      int sl[MR_MAXL], sx[MR_MAXL], sy[MR_MAXL], sk[MR_MAXL];
-      int sp = 0;
-      if (l - 1 > g.Jmin - 1) {
-        sl[0] = l - 1;
-        sx[0] = nx >> 1;
-        sy[0] = ny >> 1;
-        sk[0] = 0;
-        sp = 1;
-      }
-      const int noff = D == 2 ? 9 : 3;
+      int sl[MR_MAXL], sx[MR_MAXL], sy[MR_MAXL];
+      uint32_t sm[MR_MAXL];
+      sl[0] = l - 1;
+      sx[0] = nx >> 1;
+      sy[0] = ny >> 1;
+      sm[0] = ghost_stencil_need<D>(g, cls, l - 1, sx[0], sy[0]);
+      int sp = 1;
       while (sp > 0) {
         const int t = sp - 1;
-        const int kk = sk[t];
-        if (kk == noff) {
+        if (sm[t] == 0u) {
           --sp;
           continue;
         }
-        sk[t] = kk + 1;
+        const int k = __ffs(sm[t]) - 1;
+        sm[t] &= sm[t] - 1u;
         const int L = sl[t];
-        int ax = sx[t] + (kk % 3) - 1, ay = D == 2 ? sy[t] + (kk / 3) - 1 : 0;
-        if (!mr_nbr_mesh(g, L, ax, ay)) continue;
-        const uint32_t ga = g.base[L] + mr_encode(g, L, ax, ay);
-        if (cls[ga] & (3u | MR_C_GHOST)) continue;
-        const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
+        int ax = sx[t] + (k % 3) - 1, ay = D == 2 ? sy[t] + (k / 3) - 1 : 0;
+        mr_nbr_mesh(g, L, ax, ay);
+        const uint32_t o2 = mr_atomic_or_byte(cls, g.base[L] + mr_encode(g, L, ax, ay), MR_C_GHOST);
         if ((o2 & MR_C_GHOST) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
         sl[sp] = L - 1;
         sx[sp] = ax >> 1;
         sy[sp] = ay >> 1;
-        sk[sp] = 0;
+        sm[sp] = ghost_stencil_need<D>(g, cls, L - 1, sx[sp], sy[sp]);
         ++sp;
       }
     }

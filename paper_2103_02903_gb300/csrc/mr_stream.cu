@@ -140,68 +140,230 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
 }
 
 // ------------------------------------------------------------------ diagonal velocities
+// Transport of a leaf of a lattice with diagonal velocities (D2Q9).
+//
+// Every cell the leaf reads lies in the 5 x 5 block of level-l cells around
+// it: the flattened windows of both axes, the four single finest cells of
+// each diagonal velocity, and the prediction stencil of any refined cell
+// among the 8 neighbours.  The block's 24 map entries are looked up once,
+// all loads issued together, and kept in shared memory, so that every later
+// read of an entry is a shared-memory load instead of a dependent global
+// one.
+//
 // Diagonal velocities eta = (sx, sy) (Eq. AdaptiveAdvectionPhase).  The sum
-// over E minus the sum over A is the strip term of each axis, evaluated
-// above as for an axis velocity, plus four single finest cells at the ends
-// of the strips: + the cell diagonally upwind of the leaf, + the leaf's own
+// over E minus the sum over A is the strip term of each axis, evaluated as
+// for an axis velocity, plus four single finest cells at the ends of the
+// strips: + the cell diagonally upwind of the leaf, + the leaf's own
 // downwind corner cell, - the two cells that mix the two.  With the
 // tensor-product prediction a finest value is the product of the
 // one-dimensional reconstructions, so the four cells are the product of the
-// two axes' in-minus-out flattened weights applied to the 5 x 5 block of
-// level-l values around the leaf.  A refined cell among the 8 neighbours
-// adds the details of its children through the level-(l+1) edge weights
-// (the critical case of Sec. 6.1; grading keeps deeper levels away).  At a
-// corner of a non-periodic domain the outside cells take the boundary value
-// of the face crossed first along x, so after the two strips the four
-// cells leave minus the value of the y face.
+// two axes' in-minus-out flattened weights applied to the block of level-l
+// values.  A refined cell among the 8 neighbours adds the details of its
+// children through the level-(l+1) edge weights (the critical case of Sec.
+// 6.1; grading keeps deeper levels away).  At a corner of a non-periodic
+// domain the outside cells take the boundary value of the face crossed first
+// along x, so after the two strips the four cells leave minus the value of
+// the y face.
+#define MR_WIN_OUT ((int32_t)0xC0000000)  // block cell outside a non-periodic domain
+#define MR_WIN_TPB 128                   // threads per block of the transport kernel
+
+__device__ __forceinline__ bool win_valid(int32_t e) { return (((uint32_t)e) >> 30) != 3u; }
+
+// Prediction stencil (3 x 3, x fastest) of the level-l neighbour at offset
+// (ox, oy) from the leaf at (x, y), read from the block: periodic axes wrap
+// (the block entries were looked up wrapped), the others take the nearest
+// cell of the level, as the prediction operator does at a boundary.
+__device__ __forceinline__ bool win_stencil(const Geo& g, int l, int x, int y, int ox, int oy,
+                                            const int32_t (*win)[MR_WIN_TPB], int32_t* st) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      int X = ox + i - 1, Y = oy + j - 1;
+      if (!g.periodic[0]) {
+        const int ax = x + X;
+        if (ax < 0) X = -x;
+        else if (ax >= g.n[l][0]) X = g.n[l][0] - 1 - x;
+      }
+      if (!g.periodic[1]) {
+        const int ay = y + Y;
+        if (ay < 0) Y = -y;
+        else if (ay >= g.n[l][1]) Y = g.n[l][1] - 1 - y;
+      }
+      const int32_t e = win[(Y + 2) * 5 + X + 2][threadIdx.x];
+      st[j * 3 + i] = e;
+      ok = ok && win_valid(e);
+    }
+  return ok;
+}
+
 template <class Sc, int F>
-__device__ __forceinline__ void stream_corners(const Geo& g, const MeshDev& B,
-                                               const typename FormT<F>::S* __restrict__ LFin,
-                                               const typename FormT<F>::C* __restrict__ W, int l, int x, int y,
-                                               const typename FormT<F>::C* f, const typename FormT<F>::C* offv,
-                                               typename FormT<F>::C* out, typename FormT<F>::C scale2) {
+__device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
+                                                 const typename FormT<F>::S* __restrict__ LFin,
+                                                 const typename FormT<F>::C* __restrict__ W, int l, int x, int y,
+                                                 int i, const typename FormT<F>::C* f,
+                                                 const typename FormT<F>::C* offv, typename FormT<F>::C* out,
+                                                 typename FormT<F>::C scale, int32_t (*win)[MR_WIN_TPB]) {
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
+  constexpr int Q = Sc::Q;
+  const C cs = MR_K(C, g, cross_sign);
+  const int tid = threadIdx.x;
+  {
+    int32_t e[25];
+#pragma unroll
+    for (int w = 0; w < 25; ++w) {
+      if (w == 12) {
+        e[w] = (int32_t)((MR_CLS_LEAF << 30) | (uint32_t)i);
+        continue;
+      }
+      int nx = x + w % 5 - 2, ny = y + w / 5 - 2;
+      e[w] = mr_nbr_mesh(g, l, nx, ny) ? B.map[g.base[l] + mr_encode(g, l, nx, ny)] : MR_WIN_OUT;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int w = 0; w < 25; ++w) {
+      bad = bad || e[w] == MR_MAP_NONE;
+      win[w][tid] = e[w];
+    }
+    if (bad) mr_set_err(B.cnt, MR_DERR_INTERNAL);  // a cell the transport reads is neither in the tree nor a ghost
+  }
+
+  // ---- axis strips and their critical-case corrections
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int k = a == 0 ? x : y;
+    const int N = g.n[l][a];
+    const int per = g.periodic[a];
+    const int slot = mr_slot(k, N, per);
+    const C* wP = W + MR_WIDX(l, a, slot, 0);
+    const C* wM = W + MR_WIDX(l, a, slot, 1);
+    ValPtr<S> vp[4];
+    bool has[4];
+    int32_t ent[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int off = w < 2 ? w - 2 : w - 1;  // -2, -1, +1, +2 along a
+      ent[w] = win[a == 0 ? 12 + off : 12 + 5 * off][tid];
+      has[w] = win_valid(ent[w]);
+      vp[w] = mr_resolve<S>(g, B, LFin, has[w] ? ent[w] : 0);
+    }
+#pragma unroll
+    for (int p = 0; p < Q; ++p) {
+      const int sgn = eta_of<Sc>(p, a);
+      if (sgn == 0) continue;
+      const C* w = sgn > 0 ? wP : wM;
+      C acc = w[2] * f[p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (has[q]) acc += w[q < 2 ? q : q + 1] * ld_off<F>(vp[q], p, offv);
+      if (!per) {
+        if (sgn > 0 && k == 0) acc += bc_value<C>(g, g.bc[2 * a], f, p, Sc::opp(p));
+        if (sgn < 0 && k == N - 1) acc += bc_value<C>(g, g.bc[2 * a + 1], f, p, Sc::opp(p));
+      }
+      out[p] += scale * acc;
+    }
+#pragma unroll
+    for (int side = -1; side <= 1; side += 2) {
+      const int wi = side < 0 ? 1 : 2;
+      if (!has[wi] || (((uint32_t)ent[wi]) >> 30) != MR_CLS_INT) continue;
+      const int ox = a == 0 ? side : 0, oy = a == 1 ? side : 0;
+      int32_t st[9];
+      if (!win_stencil(g, l, x, y, ox, oy, win, st)) {
+        mr_set_err(B.cnt, MR_DERR_INTERNAL);
+        continue;
+      }
+      int nx = x + ox, ny = y + oy;
+      mr_nbr_mesh(g, l, nx, ny);
+      const uint32_t ncode = mr_encode(g, l, nx, ny);
+      ValPtr<S> sv[9], cv[4];
+      bool ok = true;
+#pragma unroll
+      for (int ci = 0; ci < 4; ++ci) {
+        const int32_t e = B.map[g.base[l + 1] + ((ncode << 2) | (uint32_t)ci)];
+        ok = ok && e != MR_MAP_NONE;
+        cv[ci] = mr_resolve<S>(g, B, LFin, e);
+      }
+#pragma unroll
+      for (int kk = 0; kk < 9; ++kk) sv[kk] = mr_resolve<S>(g, B, LFin, st[kk]);
+      if (!ok) {
+        mr_set_err(B.cnt, MR_DERR_INTERNAL);
+        continue;
+      }
+      const int N1 = g.n[l + 1][a];
+#pragma unroll
+      for (int p = 0; p < Q; ++p) {
+        const int sgn = eta_of<Sc>(p, a);
+        if (sgn == 0) continue;
+        // the strip on the neighbour's side: incoming part if the
+        // neighbour is upwind, outgoing part otherwise
+        const bool incoming = (sgn > 0) == (side < 0);
+        int c;  // child-level cell whose edge value is corrected
+        if (sgn > 0)
+          c = side < 0 ? 2 * k - 1 : 2 * k + 1;
+        else
+          c = side > 0 ? 2 * k + 2 : 2 * k;
+        const int cslot = mr_slot(per ? 2 : c, N1, per);
+        const C* wt = W + MR_WIDX(l + 1, a, cslot, sgn > 0 ? 2 : 3);
+        // details are exact on constants: stored values suffice
+        C v[9];
+#pragma unroll
+        for (int kk = 0; kk < 9; ++kk) v[kk] = ld_c<C>(sv[kk], p);
+        C corr = (C)0;
+#pragma unroll
+        for (int ci = 0; ci < 4; ++ci) {
+          const int sa = (ci >> a) & 1;
+          const int delta = 2 * (k + side) + sa - c;
+          if (delta < -2 || delta > 2) continue;
+          const C det = ld_c<C>(cv[ci], p) - predict_c<2, C>(v, ci, cs);
+          corr += wt[delta + 2] * det;
+        }
+        corr *= (C)0.5;
+        out[p] += scale * (incoming ? corr : -corr);
+      }
+    }
+  }
+
+  // ---- the four single finest cells of each diagonal velocity
   constexpr int P0 = Sc::DIAG0;
   const int Nx = g.n[l][0], Ny = g.n[l][1];
   const int slx = mr_slot(x, Nx, g.periodic[0]), sly = mr_slot(y, Ny, g.periodic[1]);
   const C* wx[2] = {W + MR_WIDX(l, 0, slx, 0), W + MR_WIDX(l, 0, slx, 1)};
   const C* wy[2] = {W + MR_WIDX(l, 1, sly, 0), W + MR_WIDX(l, 1, sly, 1)};
   C acc[4] = {(C)0, (C)0, (C)0, (C)0};
-  for (int b = 0; b < 5; ++b)
+  for (int b = 0; b < 5; ++b) {
+    const C wy0 = wy[0][b], wy1 = wy[1][b];
+    if (wy0 == (C)0 && wy1 == (C)0) continue;  // zero row: adds nothing
+#pragma unroll
     for (int a = 0; a < 5; ++a) {
+      const C wx0 = wx[0][a], wx1 = wx[1][a];
+      if (wx0 == (C)0 && wx1 == (C)0) continue;
+      const int32_t e = win[b * 5 + a][tid];
       const bool self = a == 2 && b == 2;
-      ValPtr<S> vp{LFin, 0};
-      if (!self) {
-        int nx = x + a - 2, ny = y + b - 2;
-        if (!mr_nbr_mesh(g, l, nx, ny)) continue;  // outside: zero weight
-        const int32_t e = B.map[g.base[l] + mr_encode(g, l, nx, ny)];
-        if (e == MR_MAP_NONE) {
-          mr_set_err(B.cnt, MR_DERR_INTERNAL);
-          continue;
-        }
-        vp = mr_resolve<S>(g, B, LFin, e);
-      }
+      if (!self && !win_valid(e)) continue;  // outside: zero weight
+      const ValPtr<S> vp = mr_resolve<S>(g, B, LFin, self ? 0 : e);
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int p = P0 + t;
-        const C wab = wx[Sc::eta(p, 0) > 0 ? 0 : 1][a] * wy[Sc::eta(p, 1) > 0 ? 0 : 1][b];
+        const C wab = (Sc::eta(p, 0) > 0 ? wx0 : wx1) * (Sc::eta(p, 1) > 0 ? wy0 : wy1);
+        if (wab == (C)0) continue;
         const C v = self ? f[p] : ld_off<F>(vp, p, offv);
         acc[t] += wab * v;
       }
     }
+  }
   if (l < g.J) {
-    const C cs = MR_K(C, g, cross_sign);
     for (int nb = 0; nb < 9; ++nb) {
       if (nb == 4) continue;
       const int dx = nb % 3 - 1, dy = nb / 3 - 1;
-      int nx = x + dx, ny = y + dy;
-      if (!mr_nbr_mesh(g, l, nx, ny)) continue;
-      const uint32_t ncode = mr_encode(g, l, nx, ny);
-      const int32_t e = B.map[g.base[l] + ncode];
-      if (e == MR_MAP_NONE || (((uint32_t)e) >> 30) != MR_CLS_INT) continue;
+      const int32_t e = win[(dy + 2) * 5 + dx + 2][tid];
+      if (!win_valid(e) || (((uint32_t)e) >> 30) != MR_CLS_INT) continue;
       int32_t st[9], ce[4];
-      bool ok = mr_stencil_entries<2>(g, B, l, nx, ny, st);
+      bool ok = win_stencil(g, l, x, y, dx, dy, win, st);
+      int nx = x + dx, ny = y + dy;
+      mr_nbr_mesh(g, l, nx, ny);
+      const uint32_t ncode = mr_encode(g, l, nx, ny);
 #pragma unroll
       for (int ci = 0; ci < 4; ++ci) {
         ce[ci] = B.map[g.base[l + 1] + ((ncode << 2) | (uint32_t)ci)];
@@ -239,6 +401,7 @@ __device__ __forceinline__ void stream_corners(const Geo& g, const MeshDev& B,
       }
     }
   }
+  const C scale2 = scale * scale;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     const int p = P0 + t;
@@ -252,7 +415,7 @@ __device__ __forceinline__ void stream_corners(const Geo& g, const MeshDev& B,
 
 // ------------------------------------------------------------------ transport + collision
 template <int SC, int F>
-__global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restrict__ IB, int ngrp, int dst,
+__global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __restrict__ IB, int ngrp, int dst,
                                                         int do_stream, int do_collide) {
   using Sc = Scheme<SC>;
   using S = typename FormT<F>::S;
@@ -290,106 +453,110 @@ __global__ void __launch_bounds__(128) k_stream_collide(const InstDev* __restric
       int x, y;
       mr_decode(g, l, code, x, y);
       const C scale = (C)__longlong_as_double((long long)(1023 + l - g.J) << 52);  // 2^{l-J}, exact
+      if constexpr (Sc::DIAG) {
+        __shared__ int32_t win[25][MR_WIN_TPB];
+        stream_window_d2<Sc, F>(g, B, LFin, W, l, x, y, i, f, offv, out, scale, win);
+      } else {
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const int k = a == 0 ? x : y;
-        const int N = g.n[l][a];
-        const int per = g.periodic[a];
-        const int slot = mr_slot(k, N, per);
-        const C* wP = W + MR_WIDX(l, a, slot, 0);
-        const C* wM = W + MR_WIDX(l, a, slot, 1);
-        // window: delta = -2, -1, +1, +2 along a
-        ValPtr<S> vp[4];
-        bool has[4];
-        int32_t ent[4];
+        for (int a = 0; a < D; ++a) {
+          const int k = a == 0 ? x : y;
+          const int N = g.n[l][a];
+          const int per = g.periodic[a];
+          const int slot = mr_slot(k, N, per);
+          const C* wP = W + MR_WIDX(l, a, slot, 0);
+          const C* wM = W + MR_WIDX(l, a, slot, 1);
+          // window: delta = -2, -1, +1, +2 along a
+          ValPtr<S> vp[4];
+          bool has[4];
+          int32_t ent[4];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int off = w < 2 ? w - 2 : w - 1;
-          int nx = x + (a == 0 ? off : 0), ny = y + (a == 1 ? off : 0);
-          has[w] = mr_nbr_mesh(g, l, nx, ny);
-          ent[w] = has[w] ? B.map[g.base[l] + mr_encode(g, l, nx, ny)] : MR_MAP_NONE;
-          if (has[w] && ent[w] == MR_MAP_NONE) {
-            mr_set_err(B.cnt, MR_DERR_INTERNAL);
-            has[w] = false;
+          for (int w = 0; w < 4; ++w) {
+            const int off = w < 2 ? w - 2 : w - 1;
+            int nx = x + (a == 0 ? off : 0), ny = y + (a == 1 ? off : 0);
+            has[w] = mr_nbr_mesh(g, l, nx, ny);
+            ent[w] = has[w] ? B.map[g.base[l] + mr_encode(g, l, nx, ny)] : MR_MAP_NONE;
+            if (has[w] && ent[w] == MR_MAP_NONE) {
+              mr_set_err(B.cnt, MR_DERR_INTERNAL);
+              has[w] = false;
+            }
+            vp[w] = mr_resolve<S>(g, B, LFin, has[w] ? ent[w] : 0);
           }
-          vp[w] = mr_resolve<S>(g, B, LFin, has[w] ? ent[w] : 0);
-        }
-#pragma unroll
-        for (int p = 0; p < Q; ++p) {
-          const int sgn = eta_of<Sc>(p, a);
-          if (sgn == 0) continue;
-          const C* w = sgn > 0 ? wP : wM;
-          C acc = w[2] * f[p];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (has[q]) acc += w[q < 2 ? q : q + 1] * ld_off<F>(vp[q], p, offv);
-          if (!per) {
-            if (sgn > 0 && k == 0) acc += bc_value<C>(g, g.bc[2 * a], f, p, Sc::opp(p));
-            if (sgn < 0 && k == N - 1) acc += bc_value<C>(g, g.bc[2 * a + 1], f, p, Sc::opp(p));
-          }
-          out[p] += scale * acc;
-        }
-        // critical case: a refined neighbour on either side along a
-#pragma unroll
-        for (int side = -1; side <= 1; side += 2) {
-          const int wi = side < 0 ? 1 : 2;
-          if (!has[wi] || (((uint32_t)ent[wi]) >> 30) != MR_CLS_INT) continue;
-          int nx = x + (a == 0 ? side : 0), ny = y + (a == 1 ? side : 0);
-          mr_nbr_mesh(g, l, nx, ny);
-          int32_t st[9];
-          if (!mr_stencil_entries<D>(g, B, l, nx, ny, st)) {
-            mr_set_err(B.cnt, MR_DERR_INTERNAL);
-            continue;
-          }
-          ValPtr<S> sv[D == 2 ? 9 : 3], cv[1 << D];
-#pragma unroll
-          for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) sv[kk] = mr_resolve<S>(g, B, LFin, st[kk]);
-          const uint32_t ncode = mr_encode(g, l, nx, ny);
-          bool ok = true;
-#pragma unroll
-          for (int ci = 0; ci < (1 << D); ++ci) {
-            const int32_t e = B.map[g.base[l + 1] + ((ncode << D) | (uint32_t)ci)];
-            ok = ok && e != MR_MAP_NONE;
-            cv[ci] = mr_resolve<S>(g, B, LFin, e);
-          }
-          if (!ok) {
-            mr_set_err(B.cnt, MR_DERR_INTERNAL);
-            continue;
-          }
-          const int N1 = g.n[l + 1][a];
 #pragma unroll
           for (int p = 0; p < Q; ++p) {
             const int sgn = eta_of<Sc>(p, a);
             if (sgn == 0) continue;
-            // the strip on the neighbour's side: incoming part if the
-            // neighbour is upwind, outgoing part otherwise
-            const bool incoming = (sgn > 0) == (side < 0);
-            int c;  // child-level cell whose edge value is corrected
-            if (sgn > 0)
-              c = side < 0 ? 2 * k - 1 : 2 * k + 1;
-            else
-              c = side > 0 ? 2 * k + 2 : 2 * k;
-            const int cslot = mr_slot(per ? 2 : c, N1, per);
-            const C* wt = W + MR_WIDX(l + 1, a, cslot, sgn > 0 ? 2 : 3);
-            // details are exact on constants: stored values suffice
-            C v[D == 2 ? 9 : 3];
+            const C* w = sgn > 0 ? wP : wM;
+            C acc = w[2] * f[p];
 #pragma unroll
-            for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) v[kk] = ld_c<C>(sv[kk], p);
-            C corr = (C)0;
+            for (int q = 0; q < 4; ++q)
+              if (has[q]) acc += w[q < 2 ? q : q + 1] * ld_off<F>(vp[q], p, offv);
+            if (!per) {
+              if (sgn > 0 && k == 0) acc += bc_value<C>(g, g.bc[2 * a], f, p, Sc::opp(p));
+              if (sgn < 0 && k == N - 1) acc += bc_value<C>(g, g.bc[2 * a + 1], f, p, Sc::opp(p));
+            }
+            out[p] += scale * acc;
+          }
+          // critical case: a refined neighbour on either side along a
+#pragma unroll
+          for (int side = -1; side <= 1; side += 2) {
+            const int wi = side < 0 ? 1 : 2;
+            if (!has[wi] || (((uint32_t)ent[wi]) >> 30) != MR_CLS_INT) continue;
+            int nx = x + (a == 0 ? side : 0), ny = y + (a == 1 ? side : 0);
+            mr_nbr_mesh(g, l, nx, ny);
+            int32_t st[9];
+            if (!mr_stencil_entries<D>(g, B, l, nx, ny, st)) {
+              mr_set_err(B.cnt, MR_DERR_INTERNAL);
+              continue;
+            }
+            ValPtr<S> sv[D == 2 ? 9 : 3], cv[1 << D];
+#pragma unroll
+            for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) sv[kk] = mr_resolve<S>(g, B, LFin, st[kk]);
+            const uint32_t ncode = mr_encode(g, l, nx, ny);
+            bool ok = true;
 #pragma unroll
             for (int ci = 0; ci < (1 << D); ++ci) {
-              const int sa = (ci >> a) & 1;
-              const int delta = 2 * (k + side) + sa - c;
-              if (delta < -2 || delta > 2) continue;
-              const C det = ld_c<C>(cv[ci], p) - predict_c<D, C>(v, ci, cs);
-              corr += wt[delta + 2] * det;
+              const int32_t e = B.map[g.base[l + 1] + ((ncode << D) | (uint32_t)ci)];
+              ok = ok && e != MR_MAP_NONE;
+              cv[ci] = mr_resolve<S>(g, B, LFin, e);
             }
-            corr *= (D == 2 ? (C)0.5 : (C)1);
-            out[p] += scale * (incoming ? corr : -corr);
+            if (!ok) {
+              mr_set_err(B.cnt, MR_DERR_INTERNAL);
+              continue;
+            }
+            const int N1 = g.n[l + 1][a];
+#pragma unroll
+            for (int p = 0; p < Q; ++p) {
+              const int sgn = eta_of<Sc>(p, a);
+              if (sgn == 0) continue;
+              // the strip on the neighbour's side: incoming part if the
+              // neighbour is upwind, outgoing part otherwise
+              const bool incoming = (sgn > 0) == (side < 0);
+              int c;  // child-level cell whose edge value is corrected
+              if (sgn > 0)
+                c = side < 0 ? 2 * k - 1 : 2 * k + 1;
+              else
+                c = side > 0 ? 2 * k + 2 : 2 * k;
+              const int cslot = mr_slot(per ? 2 : c, N1, per);
+              const C* wt = W + MR_WIDX(l + 1, a, cslot, sgn > 0 ? 2 : 3);
+              // details are exact on constants: stored values suffice
+              C v[D == 2 ? 9 : 3];
+#pragma unroll
+              for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) v[kk] = ld_c<C>(sv[kk], p);
+              C corr = (C)0;
+#pragma unroll
+              for (int ci = 0; ci < (1 << D); ++ci) {
+                const int sa = (ci >> a) & 1;
+                const int delta = 2 * (k + side) + sa - c;
+                if (delta < -2 || delta > 2) continue;
+                const C det = ld_c<C>(cv[ci], p) - predict_c<D, C>(v, ci, cs);
+                corr += wt[delta + 2] * det;
+              }
+              corr *= (D == 2 ? (C)0.5 : (C)1);
+              out[p] += scale * (incoming ? corr : -corr);
+            }
           }
         }
       }
-      if constexpr (Sc::DIAG) stream_corners<Sc, F>(g, B, LFin, W, l, x, y, f, offv, out, scale * scale);
     }
     if (do_collide) {
       Sc::template collide<C>(g, out);
