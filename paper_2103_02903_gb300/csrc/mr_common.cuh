@@ -85,6 +85,14 @@ __device__ __forceinline__ const double* mr_wtab<double>(const InstDev& si) { re
 template <>
 __device__ __forceinline__ const float* mr_wtab<float>(const InstDev& si) { return si.Wf; }
 
+// Prologue of a step kernel launched with mr_launch_pdl: wait for the
+// preceding grid (a no-op when there is none in flight), then allow the
+// next one to be scheduled.
+__device__ __forceinline__ void mr_grid_dep() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // A cell's population array: element p is at p[p * stride].
 template <class S = double>
 struct ValPtr {

@@ -25,6 +25,7 @@ struct PopRows {
 
 template <int D, int Q, int F>
 __global__ void __launch_bounds__(256) k_project(const InstDev* __restrict__ IB, int n, int cur, int k) {
+  mr_grid_dep();
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(256) k_project(const InstDev* __restrict__ IB,
 
 template <int D, int Q, int F>
 __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB, int n, int cur) {
+  mr_grid_dep();
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
@@ -148,13 +150,13 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
 
 template <int D, int Q, int F>
 void launch_project_t(const Group& G, int cur, int k, cudaStream_t st) {
-  k_project<D, Q, F><<<mr_tile_grid(G, G.proj_cells[k], 32, 8), dim3(32, PopRows<Q>::value), mr_pre_bytes(G), st>>>(G.dev, G.n,
-                                                                                                    cur, k);
+  mr_launch_pdl(k_project<D, Q, F>, mr_tile_grid(G, G.proj_cells[k], 32, 8), dim3(32, PopRows<Q>::value),
+                mr_pre_bytes(G), st, G.dev, G.n, cur, k);
 }
 template <int D, int Q, int F>
 void launch_details_t(const Group& G, int cur, cudaStream_t st) {
-  k_details<D, Q, F><<<mr_tile_grid(G, G.capI, 32, 8), dim3(32, PopRows<Q>::value), mr_pre_bytes(G), st>>>(G.dev, G.n,
-                                                                                                    cur);
+  mr_launch_pdl(k_details<D, Q, F>, mr_tile_grid(G, G.capI, 32, 8), dim3(32, PopRows<Q>::value), mr_pre_bytes(G),
+                st, G.dev, G.n, cur);
 }
 
 }  // namespace

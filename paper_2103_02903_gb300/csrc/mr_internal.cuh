@@ -217,6 +217,27 @@ struct Group {
   int nsm;
 };
 
+// Launch of a step kernel with programmatic dependent launch: the next
+// kernel of the stream may be scheduled while this one drains.  Every
+// kernel launched this way begins with mr_grid_dep(), which waits for the
+// grid before it to complete and its writes to be visible, so the order of
+// the stream is kept; only the launch latency is overlapped.
+template <typename... KArgs, typename... Args>
+inline cudaError_t mr_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                 Args... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Grid of a tiled step kernel: at most `per_sm` blocks per SM, and no more
 // blocks than the tiles the group can have for `max_items` items.
 inline int mr_tile_grid(const Group& G, long long max_items, int items_per_tile, int per_sm) {

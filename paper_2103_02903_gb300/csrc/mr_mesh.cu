@@ -38,6 +38,7 @@ __device__ __forceinline__ double level_eps(const Geo& g, int l) { return ldexp(
 
 template <int D>
 __global__ void __launch_bounds__(256) k_flags_T(const InstDev* __restrict__ IB, int n, int cur) {
+  mr_grid_dep();
   MR_INT_TILES_BEGIN(IB, n, cur, g, A, i)
     uint8_t* flags = si.flags;
     const int L = A.lvl[MR_CLS_INT][i];
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(256) k_flags_T(const InstDev* __restrict__ IB,
 // ---------------------------------------------------------------- H_eps
 template <int D>
 __global__ void __launch_bounds__(256) k_flags_H(const InstDev* __restrict__ IB, int n, int cur) {
+  mr_grid_dep();
   MR_INT_TILES_BEGIN(IB, n, cur, g, A, i)
     uint8_t* flags = si.flags;
     const int L = A.lvl[MR_CLS_INT][i];
@@ -108,6 +110,7 @@ __device__ __forceinline__ uint32_t grade_need(const Geo& g, const uint8_t* flag
 
 template <int D>
 __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, int n) {
+  mr_grid_dep();
   // tiles of 256 cells strided over the grid (not one block per chunk):
   // refined cells cluster, and interleaving spreads their cascades
   extern __shared__ int pre[];
@@ -164,6 +167,7 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
 template <int D>
 __global__ void __launch_bounds__(256) k_classify(const InstDev* __restrict__ IB,
                                                   const int* __restrict__ chunk_pre, int n) {
+  mr_grid_dep();
   __shared__ InstDev si;
   int chunk, have = -1;
   mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
@@ -222,6 +226,7 @@ __device__ __forceinline__ void ghost_window_cell(bool block, int w, int x, int 
 template <int D>
 __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__ IB,
                                                      const int* __restrict__ chunk_pre, int n) {
+  mr_grid_dep();
   __shared__ InstDev si;
   int chunk, have = -1;
   mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
@@ -303,6 +308,7 @@ __device__ __forceinline__ int cls_of(uint8_t c) {
 
 __global__ void __launch_bounds__(1024) k_count(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
                                                 int n) {
+  mr_grid_dep();
   int chunk;
   const int b = mr_group_chunk(chunk_pre, n, chunk);
   const uint8_t* __restrict__ cls = IB[b].cls;
@@ -320,6 +326,7 @@ __global__ void __launch_bounds__(1024) k_count(const InstDev* __restrict__ IB, 
 }
 
 __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict__ IB, int dst) {
+  mr_grid_dep();
   __shared__ int warp_sums[32];
   __shared__ int carry;
   __shared__ InstDev si;
@@ -386,6 +393,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict_
 
 __global__ void __launch_bounds__(1024) k_scatter(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
                                                   int n, int dst) {
+  mr_grid_dep();
   __shared__ int wcount[32][3];
   __shared__ int woff[32][3];
   __shared__ InstDev si;
@@ -475,37 +483,45 @@ __global__ void __launch_bounds__(256) k_leaves_check(Geo g, const uint8_t* __re
     else                                                         \
       KER<2><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);            \
   } while (0)
+// step kernels (they begin with mr_grid_dep)
+#define MR_DISPATCH_D_PDL(KER, GRID, BLOCK, SMEM, ST, ...)                 \
+  do {                                                                     \
+    if (D_ == 1)                                                           \
+      mr_launch_pdl(KER<1>, GRID, BLOCK, SMEM, ST, __VA_ARGS__);           \
+    else                                                                   \
+      mr_launch_pdl(KER<2>, GRID, BLOCK, SMEM, ST, __VA_ARGS__);           \
+  } while (0)
 
 void mr_launch_flags_T(const Group& G, int cur, cudaStream_t st) {
   const int D_ = G.d;
-  MR_DISPATCH_D(k_flags_T, mr_tile_grid(G, G.capI, 256, 4), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
+  MR_DISPATCH_D_PDL(k_flags_T, mr_tile_grid(G, G.capI, 256, 4), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
 }
 void mr_launch_flags_H(const Group& G, int cur, cudaStream_t st) {
   const int D_ = G.d;
-  MR_DISPATCH_D(k_flags_H, mr_tile_grid(G, G.capI, 256, 4), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
+  MR_DISPATCH_D_PDL(k_flags_H, mr_tile_grid(G, G.capI, 256, 4), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
 }
 void mr_launch_grade(const Group& G, cudaStream_t st) {
   const int D_ = G.d;
   if (G.grade)
-    MR_DISPATCH_D(k_grade, mr_tile_grid(G, (long long)G.chunks * MR_DENSE_ALIGN, 256, 4), 256, mr_pre_bytes(G), st,
+    MR_DISPATCH_D_PDL(k_grade, mr_tile_grid(G, (long long)G.chunks * MR_DENSE_ALIGN, 256, 4), 256, mr_pre_bytes(G), st,
                   G.dev, G.n);
 }
 // dense kernels: one block per 1024-cell chunk of every instance
 void mr_launch_classify(const Group& G, cudaStream_t st) {
   const int D_ = G.d;
-  MR_DISPATCH_D(k_classify, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+  MR_DISPATCH_D_PDL(k_classify, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
 }
 void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int) {
   k_full_mesh<<<(int)(g.base[g.J + 1] / MR_DENSE_ALIGN), 256, 0, st>>>(g, cls);
 }
 void mr_launch_mark_ghosts(const Group& G, cudaStream_t st) {
   const int D_ = G.d;
-  MR_DISPATCH_D(k_mark_ghosts, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+  MR_DISPATCH_D_PDL(k_mark_ghosts, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
 }
 void mr_launch_compact(const Group& G, int dst, cudaStream_t st) {
-  k_count<<<G.chunks, 1024, 0, st>>>(G.dev, G.chunk_pre, G.n);
-  k_scan_blocks<<<G.n, 1024, 0, st>>>(G.dev, dst);
-  k_scatter<<<G.chunks, 1024, 0, st>>>(G.dev, G.chunk_pre, G.n, dst);
+  mr_launch_pdl(k_count, G.chunks, 1024, 0, st, G.dev, G.chunk_pre, G.n);
+  mr_launch_pdl(k_scan_blocks, G.n, 1024, 0, st, G.dev, dst);
+  mr_launch_pdl(k_scatter, G.chunks, 1024, 0, st, G.dev, G.chunk_pre, G.n, dst);
 }
 void mr_launch_leaves_in(const Geo& g, long long n, const unsigned long long* keys,
                          const signed char* levels, int32_t* inidx, uint8_t* cls, MeshCounts* cnt,

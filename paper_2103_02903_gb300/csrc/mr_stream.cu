@@ -29,6 +29,7 @@ namespace {
 // populations (threadIdx.y), one population per warp.
 template <int Q, int F>
 __global__ void __launch_bounds__(256) k_remesh_copy(const InstDev* __restrict__ IB, int ngrp, int cur) {
+  mr_grid_dep();
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(256) k_remesh_copy(const InstDev* __restrict__
 // applied to level-1 values of the new mesh (all present by construction).
 template <int D, int Q, int F>
 __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict__ IB, int ngrp, int dst, int kl) {
+  mr_grid_dep();
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
   constexpr int PY = PopRows<Q>::value;
@@ -417,6 +419,7 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
 template <int SC, int F>
 __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __restrict__ IB, int ngrp, int dst,
                                                         int do_stream, int do_collide) {
+  mr_grid_dep();
   using Sc = Scheme<SC>;
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
@@ -427,7 +430,9 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
   int have = -1;
   mr_inst_prefetch(si, have, IB, ngrp);
   const int tiles =
-      mr_group_prefix(pre, ngrp, [&](int b) { return (IB[b].mesh[dst].cnt->total[MR_CLS_LEAF] + 127) / 128; });
+      mr_group_prefix(pre, ngrp, [&](int b) {
+        return (IB[b].mesh[dst].cnt->total[MR_CLS_LEAF] + MR_WIN_TPB - 1) / MR_WIN_TPB;
+      });
   for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
     const int b = mr_group_find(pre, ngrp, tt);
     mr_inst_use(si, have, IB, b);
@@ -437,7 +442,7 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
     S* __restrict__ LFout = (S*)si.fstate;
     const C* __restrict__ W = mr_wtab<C>(si);
     const C cs = MR_K(C, g, cross_sign);
-    const int i = (tt - pre[b]) * 128 + threadIdx.x;
+    const int i = (tt - pre[b]) * MR_WIN_TPB + threadIdx.x;
     if (i >= B.cnt->total[MR_CLS_LEAF]) continue;
     const int l = B.lvl[MR_CLS_LEAF][i];
     const uint32_t code = B.code[MR_CLS_LEAF][i];
@@ -684,6 +689,7 @@ __global__ void __launch_bounds__(256) k_project_dense(Geo g, MeshDev B, const v
 }
 
 __global__ void k_count_updates(const InstDev* __restrict__ IB, int ngrp, int dst) {
+  mr_grid_dep();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= ngrp) return;
   MeshCounts* cnt = IB[b].mesh[dst].cnt;
@@ -693,18 +699,19 @@ __global__ void k_count_updates(const InstDev* __restrict__ IB, int ngrp, int ds
 
 template <int Q, int F>
 void launch_remesh_t(const Group& G, int cur, cudaStream_t st) {
-  k_remesh_copy<Q, F><<<mr_tile_grid(G, G.capL + G.capI, 32, 8), dim3(32, PopRows<Q>::value), mr_pre_bytes(G), st>>>(
-      G.dev, G.n, cur);
+  mr_launch_pdl(k_remesh_copy<Q, F>, mr_tile_grid(G, G.capL + G.capI, 32, 8), dim3(32, PopRows<Q>::value),
+                mr_pre_bytes(G), st, G.dev, G.n, cur);
 }
 template <int D, int Q, int F>
 void launch_predict_t(const Group& G, int dst, int kl, cudaStream_t st) {
   // ghosts and leaves of one level: at most twice its cells
-  k_predict_level<D, Q, F><<<mr_tile_grid(G, 2 * G.pred_cells[kl], 32, 8), dim3(32, PopRows<Q>::value),
-                             mr_pre_bytes(G), st>>>(G.dev, G.n, dst, kl);
+  mr_launch_pdl(k_predict_level<D, Q, F>, mr_tile_grid(G, 2 * G.pred_cells[kl], 32, 8), dim3(32, PopRows<Q>::value),
+                mr_pre_bytes(G), st, G.dev, G.n, dst, kl);
 }
 template <int SC, int F>
 void launch_stream_t(const Group& G, int dst, int ds, int dc, cudaStream_t st) {
-  k_stream_collide<SC, F><<<mr_tile_grid(G, G.capL, 128, 8), 128, mr_pre_bytes(G), st>>>(G.dev, G.n, dst, ds, dc);
+  mr_launch_pdl(k_stream_collide<SC, F>, mr_tile_grid(G, G.capL, MR_WIN_TPB, 8), MR_WIN_TPB, mr_pre_bytes(G), st, G.dev,
+                G.n, dst, ds, dc);
 }
 template <int SC, int F>
 void launch_init_t(const Geo& g, const MeshDev& B, const double* cons, void* LF, cudaStream_t st, int grid) {
@@ -820,5 +827,5 @@ void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int
 }
 
 void mr_launch_count_updates(const Group& G, int dst, cudaStream_t st) {
-  k_count_updates<<<(G.n + 127) / 128, 128, 0, st>>>(G.dev, G.n, dst);
+  mr_launch_pdl(k_count_updates, (G.n + 127) / 128, 128, 0, st, G.dev, G.n, dst);
 }
