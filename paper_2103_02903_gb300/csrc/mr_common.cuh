@@ -93,6 +93,16 @@ __device__ __forceinline__ void mr_grid_dep() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Storage offsets of the populations (Geo::off) in the arithmetic C.
+template <class C>
+__device__ __forceinline__ const C* mr_offv(const Geo& g) {
+  return g.off;
+}
+template <>
+__device__ __forceinline__ const float* mr_offv<float>(const Geo& g) {
+  return g.f32.off;
+}
+
 // A cell's population array: element p is at p[p * stride].
 template <class S = double>
 struct ValPtr {

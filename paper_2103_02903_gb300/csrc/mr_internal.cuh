@@ -144,16 +144,25 @@ __host__ __device__ inline void mr_decode(const Geo& g, int l, uint32_t code, in
   y = (ry << l) | (int)mr_compact2(local >> 1);
 }
 
+// periodic wrap of a cell index a few cells outside [0, n): every caller
+// steps at most two cells from a cell inside, so each loop runs at most a
+// few times (short code instead of an integer division)
+__host__ __device__ inline int mr_wrap(int x, int n) {
+  while (x < 0) x += n;
+  while (x >= n) x -= n;
+  return x;
+}
+
 // neighbour for the mesh rules: periodic wrap, false outside the domain
 __host__ __device__ inline bool mr_nbr_mesh(const Geo& g, int l, int& x, int& y) {
   int nx = g.n[l][0], ny = g.n[l][1];
   if (x < 0 || x >= nx) {
     if (!g.periodic[0]) return false;
-    x = ((x % nx) + nx) % nx;
+    x = mr_wrap(x, nx);
   }
   if (g.d >= 2 && (y < 0 || y >= ny)) {
     if (!g.periodic[1]) return false;
-    y = ((y % ny) + ny) % ny;
+    y = mr_wrap(y, ny);
   }
   if (g.d == 1) y = 0;
   return true;
@@ -163,9 +172,9 @@ __host__ __device__ inline bool mr_nbr_mesh(const Geo& g, int l, int& x, int& y)
 // nearest cell of the same level (constant extension)
 __host__ __device__ inline void mr_nbr_stencil(const Geo& g, int l, int& x, int& y) {
   int nx = g.n[l][0], ny = g.n[l][1];
-  if (x < 0 || x >= nx) x = g.periodic[0] ? ((x % nx) + nx) % nx : (x < 0 ? 0 : nx - 1);
+  if (x < 0 || x >= nx) x = g.periodic[0] ? mr_wrap(x, nx) : (x < 0 ? 0 : nx - 1);
   if (g.d >= 2) {
-    if (y < 0 || y >= ny) y = g.periodic[1] ? ((y % ny) + ny) % ny : (y < 0 ? 0 : ny - 1);
+    if (y < 0 || y >= ny) y = g.periodic[1] ? mr_wrap(y, ny) : (y < 0 ? 0 : ny - 1);
   } else {
     y = 0;
   }

@@ -162,6 +162,16 @@ struct Scheme<3> {
   }
 };
 
+// nine small integers (t + bias, each below 2^bits) packed into one word
+struct MrNine {
+  int v[9];
+};
+__host__ __device__ constexpr unsigned long long mr_pack9(MrNine t, int bias, int bits) {
+  unsigned long long r = 0;
+  for (int i = 0; i < 9; ++i) r |= (unsigned long long)(t.v[i] + bias) << (bits * i);
+  return r;
+}
+
 // D2Q9 of Sec. 7.2.2: eta^0 = 0, eta^{1..4} = (1,0), (0,1), (-1,0), (0,-1),
 // eta^{5..8} = (1,1), (-1,1), (-1,-1), (1,-1).  The rows of M are mutually
 // orthogonal; divided by their power of lambda they are the integer rows
@@ -173,15 +183,14 @@ struct Scheme<4> {
   static constexpr int NR = 2;
   static constexpr bool DIAG = true;
   static constexpr int DIAG0 = 5;  // first diagonal population
-  __device__ static int eta(int p, int a) {
-    constexpr int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    constexpr int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    return a == 0 ? ex[p] : ey[p];
-  }
-  __device__ static int opp(int p) {
-    constexpr int o[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-    return o[p];
-  }
+  // velocities and opposites packed into integer constants (2 and 4 bits
+  // per population), so that a population index known only at run time
+  // needs no table in memory
+  static constexpr uint32_t EXP = (uint32_t)mr_pack9({0, 1, 0, -1, 0, 1, -1, -1, 1}, 1, 2);
+  static constexpr uint32_t EYP = (uint32_t)mr_pack9({0, 0, 1, 0, -1, 1, 1, -1, -1}, 1, 2);
+  static constexpr unsigned long long OPPP = mr_pack9({0, 3, 4, 1, 2, 7, 8, 5, 6}, 0, 4);
+  __device__ static int eta(int p, int a) { return (int)(((a == 0 ? EXP : EYP) >> (2 * p)) & 3u) - 1; }
+  __device__ static int opp(int p) { return (int)((OPPP >> (4 * p)) & 15ull); }
   // f = sum_r R_r mu_r / |R_r|^2
   template <class C>
   __device__ static void from_moments(const C* mu, C* f) {

@@ -141,6 +141,160 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
   }
 }
 
+// ------------------------------------------------------------------ axis strips
+// The parts of the transport that few leaves take (a non-periodic face, a
+// refined neighbour) loop over the populations at run time and leave their
+// terms in a per-thread shared-memory buffer `tmp`; the caller adds them to
+// the register accumulators at the same point of the sum as an inline term
+// would be.  One short loop body instead of one copy per population keeps
+// the kernel's code small enough for the instruction cache.
+#define MR_WIN_TPB 128  // threads per block of the transport kernel
+
+// stride of the per-thread shared buffers: odd, so that 32 threads (or 16
+// for 8-byte values) hit distinct banks
+template <int Q>
+struct ThreadStride {
+  static constexpr int value = Q | 1;
+};
+
+// Boundary values of the populations entering through the face crossed
+// upwind along a (lo: the face before cell 0, hi: the one after N-1).
+template <class Sc, class C>
+__device__ __forceinline__ void bc_terms(const Geo& g, int a, bool lo, bool hi, const C* fs, C* tmp) {
+#pragma unroll 1
+  for (int p = 0; p < Sc::Q; ++p) {
+    const int sgn = eta_of<Sc>(p, a);
+    if (sgn > 0 && lo)
+      tmp[p] = bc_value<C>(g, g.bc[2 * a], fs, p, Sc::opp(p));
+    else if (sgn < 0 && hi)
+      tmp[p] = bc_value<C>(g, g.bc[2 * a + 1], fs, p, Sc::opp(p));
+  }
+}
+
+// Critical case (Sec. 6.1) along axis a: the neighbour on `side` is
+// refined, so the finest value at the shared edge is its children's, not
+// the prediction from level l.  tmp[p] = the term to add for population p
+// (scaled): the edge cell's detail through the level-(l+1) edge weights,
+// with the sign of the strip part (incoming if the neighbour is upwind).
+template <class Sc, int F>
+__device__ __forceinline__ void crit_axis_terms(const Geo& g, const typename FormT<F>::C* __restrict__ W, int l,
+                                                int a, int k, int side, int per,
+                                                const ValPtr<typename FormT<F>::S>* sv,
+                                                const ValPtr<typename FormT<F>::S>* cv, typename FormT<F>::C scale,
+                                                typename FormT<F>::C* tmp) {
+  using C = typename FormT<F>::C;
+  constexpr int D = Sc::D, NS = D == 2 ? 9 : 3;
+  const C cs = MR_K(C, g, cross_sign);
+  const int N1 = g.n[l + 1][a];
+#pragma unroll 1
+  for (int p = 0; p < Sc::Q; ++p) {
+    const int sgn = eta_of<Sc>(p, a);
+    if (sgn == 0) continue;
+    const bool incoming = (sgn > 0) == (side < 0);
+    int c;  // child-level cell whose edge value is corrected
+    if (sgn > 0)
+      c = side < 0 ? 2 * k - 1 : 2 * k + 1;
+    else
+      c = side > 0 ? 2 * k + 2 : 2 * k;
+    const int cslot = mr_slot(per ? 2 : c, N1, per);
+    const C* wt = W + MR_WIDX(l + 1, a, cslot, sgn > 0 ? 2 : 3);
+    // details are exact on constants: stored values suffice
+    C v[NS];
+#pragma unroll
+    for (int kk = 0; kk < NS; ++kk) v[kk] = ld_c<C>(sv[kk], p);
+    C corr = (C)0;
+#pragma unroll
+    for (int ci = 0; ci < (1 << D); ++ci) {
+      const int sa = (ci >> a) & 1;
+      const int delta = 2 * (k + side) + sa - c;
+      if (delta < -2 || delta > 2) continue;
+      const C det = ld_c<C>(cv[ci], p) - predict_c<D, C>(v, ci, cs);
+      corr += wt[delta + 2] * det;
+    }
+    corr *= (D == 2 ? (C)0.5 : (C)1);
+    tmp[p] = scale * (incoming ? corr : -corr);
+  }
+}
+
+__device__ __forceinline__ bool win_stencil(const Geo& g, int l, int x, int y, int ox, int oy,
+                                            const int32_t (*win)[MR_WIN_TPB], int32_t* st);
+
+// Strip term of axis a for every population moving along a: the flattened
+// weights of the leaf's slot applied to the level-l window (cells -2, -1,
+// +1, +2 in vp, present where has), the boundary values of a non-periodic
+// face, and the critical-case corrections of a refined neighbour on either
+// side.  The neighbour's prediction stencil comes from the 5 x 5 block in
+// shared memory (win) when there is one, from the index map otherwise.
+template <class Sc, int F>
+__device__ __forceinline__ void stream_axis(const Geo& g, const MeshDev& B,
+                                            const typename FormT<F>::S* __restrict__ LFin,
+                                            const typename FormT<F>::C* __restrict__ W, int l, int a, int x, int y,
+                                            const ValPtr<typename FormT<F>::S>* vp, const bool* has,
+                                            const int32_t* ent, const typename FormT<F>::C* fs,
+                                            const typename FormT<F>::C* offv, typename FormT<F>::C* out,
+                                            typename FormT<F>::C scale, typename FormT<F>::C* tmp,
+                                            const int32_t (*win)[MR_WIN_TPB]) {
+  using S = typename FormT<F>::S;
+  using C = typename FormT<F>::C;
+  constexpr int D = Sc::D, Q = Sc::Q;
+  const int k = a == 0 ? x : y;
+  const int N = g.n[l][a];
+  const int per = g.periodic[a];
+  const int slot = mr_slot(k, N, per);
+  const C* wP = W + MR_WIDX(l, a, slot, 0);
+  const C* wM = W + MR_WIDX(l, a, slot, 1);
+  const bool lo = !per && k == 0, hi = !per && k == N - 1;
+  if (lo || hi) bc_terms<Sc, C>(g, a, lo, hi, fs, tmp);
+#pragma unroll
+  for (int p = 0; p < Q; ++p) {
+    const int sgn = eta_of<Sc>(p, a);
+    if (sgn == 0) continue;
+    const C* w = sgn > 0 ? wP : wM;
+    C acc = w[2] * fs[p];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (has[q]) acc += w[q < 2 ? q : q + 1] * ld_off<F>(vp[q], p, offv);
+    if (sgn > 0 && lo) acc += tmp[p];
+    if (sgn < 0 && hi) acc += tmp[p];
+    out[p] += scale * acc;
+  }
+  // refined neighbours at -1 (bit 0) and +1 (bit 1); one rolled loop over them
+  const uint32_t refined = (has[1] && (((uint32_t)ent[1]) >> 30) == MR_CLS_INT ? 1u : 0u) |
+                           (has[2] && (((uint32_t)ent[2]) >> 30) == MR_CLS_INT ? 2u : 0u);
+#pragma unroll 1
+  for (int si = 0; si < 2; ++si) {
+    if (!((refined >> si) & 1u)) continue;
+    const int side = si == 0 ? -1 : 1;
+    const int ox = a == 0 ? side : 0, oy = a == 1 ? side : 0;
+    int nx = x + ox, ny = y + oy;
+    mr_nbr_mesh(g, l, nx, ny);
+    int32_t st[D == 2 ? 9 : 3];
+    bool ok;
+    if constexpr (D == 2)
+      ok = win ? win_stencil(g, l, x, y, ox, oy, win, st) : mr_stencil_entries<D>(g, B, l, nx, ny, st);
+    else
+      ok = mr_stencil_entries<D>(g, B, l, nx, ny, st);
+    const uint32_t ncode = mr_encode(g, l, nx, ny);
+    ValPtr<S> sv[D == 2 ? 9 : 3], cv[1 << D];
+#pragma unroll
+    for (int ci = 0; ci < (1 << D); ++ci) {
+      const int32_t e = B.map[g.base[l + 1] + ((ncode << D) | (uint32_t)ci)];
+      ok = ok && e != MR_MAP_NONE;
+      cv[ci] = mr_resolve<S>(g, B, LFin, e);
+    }
+    if (!ok) {
+      mr_set_err(B.cnt, MR_DERR_INTERNAL);
+      continue;
+    }
+#pragma unroll
+    for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) sv[kk] = mr_resolve<S>(g, B, LFin, st[kk]);
+    crit_axis_terms<Sc, F>(g, W, l, a, k, side, per, sv, cv, scale, tmp);
+#pragma unroll
+    for (int p = 0; p < Q; ++p)
+      if (eta_of<Sc>(p, a) != 0) out[p] += tmp[p];
+  }
+}
+
 // ------------------------------------------------------------------ diagonal velocities
 // Transport of a leaf of a lattice with diagonal velocities (D2Q9).
 //
@@ -167,7 +321,6 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
 // along x, so after the two strips the four cells leave minus the value of
 // the y face.
 #define MR_WIN_OUT ((int32_t)0xC0000000)  // block cell outside a non-periodic domain
-#define MR_WIN_TPB 128                   // threads per block of the transport kernel
 
 __device__ __forceinline__ bool win_valid(int32_t e) { return (((uint32_t)e) >> 30) != 3u; }
 
@@ -204,24 +357,50 @@ template <class Sc, int F>
 __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
                                                  const typename FormT<F>::S* __restrict__ LFin,
                                                  const typename FormT<F>::C* __restrict__ W, int l, int x, int y,
-                                                 int i, const typename FormT<F>::C* f,
+                                                 int i, const typename FormT<F>::C* fs,
                                                  const typename FormT<F>::C* offv, typename FormT<F>::C* out,
-                                                 typename FormT<F>::C scale, int32_t (*win)[MR_WIN_TPB]) {
+                                                 typename FormT<F>::C scale, typename FormT<F>::C* tmp,
+                                                 int32_t (*win)[MR_WIN_TPB]) {
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
-  constexpr int Q = Sc::Q;
   const C cs = MR_K(C, g, cross_sign);
   const int tid = threadIdx.x;
   {
+    // The Morton code of cell (X, Y) of level l is
+    // (root << 2l) | spread(X mod 2^l) | spread(Y mod 2^l) << 1 with
+    // root = X >> l + roots_x (Y >> l): separable, so the block's 25 codes
+    // come from 5 column parts and 5 row parts.
+    const int Nx = g.n[l][0], Ny = g.n[l][1];
+    const uint32_t mask = (1u << l) - 1u;
+    uint32_t px[5], rx[5], py[5], ry[5];
+    bool ix[5], iy[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+      int X = x + o - 2, Y = y + o - 2;
+      ix[o] = X >= 0 && X < Nx;
+      if (!ix[o] && g.periodic[0]) {
+        X = mr_wrap(X, Nx);
+        ix[o] = true;
+      }
+      iy[o] = Y >= 0 && Y < Ny;
+      if (!iy[o] && g.periodic[1]) {
+        Y = mr_wrap(Y, Ny);
+        iy[o] = true;
+      }
+      px[o] = mr_spread2((uint32_t)X & mask);
+      rx[o] = (uint32_t)X >> l;
+      py[o] = mr_spread2((uint32_t)Y & mask) << 1;
+      ry[o] = (uint32_t)g.roots[0] * ((uint32_t)Y >> l);
+    }
+    const int32_t* map = B.map + g.base[l];
     int32_t e[25];
 #pragma unroll
     for (int w = 0; w < 25; ++w) {
-      if (w == 12) {
+      const int a = w % 5, b = w / 5;
+      if (w == 12)
         e[w] = (int32_t)((MR_CLS_LEAF << 30) | (uint32_t)i);
-        continue;
-      }
-      int nx = x + w % 5 - 2, ny = y + w / 5 - 2;
-      e[w] = mr_nbr_mesh(g, l, nx, ny) ? B.map[g.base[l] + mr_encode(g, l, nx, ny)] : MR_WIN_OUT;
+      else
+        e[w] = ix[a] && iy[b] ? map[((rx[a] + ry[b]) << (2 * l)) | px[a] | py[b]] : MR_WIN_OUT;
     }
     bool bad = false;
 #pragma unroll
@@ -232,15 +411,9 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
     if (bad) mr_set_err(B.cnt, MR_DERR_INTERNAL);  // a cell the transport reads is neither in the tree nor a ghost
   }
 
-  // ---- axis strips and their critical-case corrections
+  // ---- axis strips, boundary values and critical-case corrections
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
-    const int k = a == 0 ? x : y;
-    const int N = g.n[l][a];
-    const int per = g.periodic[a];
-    const int slot = mr_slot(k, N, per);
-    const C* wP = W + MR_WIDX(l, a, slot, 0);
-    const C* wM = W + MR_WIDX(l, a, slot, 1);
     ValPtr<S> vp[4];
     bool has[4];
     int32_t ent[4];
@@ -251,80 +424,7 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
       has[w] = win_valid(ent[w]);
       vp[w] = mr_resolve<S>(g, B, LFin, has[w] ? ent[w] : 0);
     }
-#pragma unroll
-    for (int p = 0; p < Q; ++p) {
-      const int sgn = eta_of<Sc>(p, a);
-      if (sgn == 0) continue;
-      const C* w = sgn > 0 ? wP : wM;
-      C acc = w[2] * f[p];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (has[q]) acc += w[q < 2 ? q : q + 1] * ld_off<F>(vp[q], p, offv);
-      if (!per) {
-        if (sgn > 0 && k == 0) acc += bc_value<C>(g, g.bc[2 * a], f, p, Sc::opp(p));
-        if (sgn < 0 && k == N - 1) acc += bc_value<C>(g, g.bc[2 * a + 1], f, p, Sc::opp(p));
-      }
-      out[p] += scale * acc;
-    }
-#pragma unroll
-    for (int side = -1; side <= 1; side += 2) {
-      const int wi = side < 0 ? 1 : 2;
-      if (!has[wi] || (((uint32_t)ent[wi]) >> 30) != MR_CLS_INT) continue;
-      const int ox = a == 0 ? side : 0, oy = a == 1 ? side : 0;
-      int32_t st[9];
-      if (!win_stencil(g, l, x, y, ox, oy, win, st)) {
-        mr_set_err(B.cnt, MR_DERR_INTERNAL);
-        continue;
-      }
-      int nx = x + ox, ny = y + oy;
-      mr_nbr_mesh(g, l, nx, ny);
-      const uint32_t ncode = mr_encode(g, l, nx, ny);
-      ValPtr<S> sv[9], cv[4];
-      bool ok = true;
-#pragma unroll
-      for (int ci = 0; ci < 4; ++ci) {
-        const int32_t e = B.map[g.base[l + 1] + ((ncode << 2) | (uint32_t)ci)];
-        ok = ok && e != MR_MAP_NONE;
-        cv[ci] = mr_resolve<S>(g, B, LFin, e);
-      }
-#pragma unroll
-      for (int kk = 0; kk < 9; ++kk) sv[kk] = mr_resolve<S>(g, B, LFin, st[kk]);
-      if (!ok) {
-        mr_set_err(B.cnt, MR_DERR_INTERNAL);
-        continue;
-      }
-      const int N1 = g.n[l + 1][a];
-#pragma unroll
-      for (int p = 0; p < Q; ++p) {
-        const int sgn = eta_of<Sc>(p, a);
-        if (sgn == 0) continue;
-        // the strip on the neighbour's side: incoming part if the
-        // neighbour is upwind, outgoing part otherwise
-        const bool incoming = (sgn > 0) == (side < 0);
-        int c;  // child-level cell whose edge value is corrected
-        if (sgn > 0)
-          c = side < 0 ? 2 * k - 1 : 2 * k + 1;
-        else
-          c = side > 0 ? 2 * k + 2 : 2 * k;
-        const int cslot = mr_slot(per ? 2 : c, N1, per);
-        const C* wt = W + MR_WIDX(l + 1, a, cslot, sgn > 0 ? 2 : 3);
-        // details are exact on constants: stored values suffice
-        C v[9];
-#pragma unroll
-        for (int kk = 0; kk < 9; ++kk) v[kk] = ld_c<C>(sv[kk], p);
-        C corr = (C)0;
-#pragma unroll
-        for (int ci = 0; ci < 4; ++ci) {
-          const int sa = (ci >> a) & 1;
-          const int delta = 2 * (k + side) + sa - c;
-          if (delta < -2 || delta > 2) continue;
-          const C det = ld_c<C>(cv[ci], p) - predict_c<2, C>(v, ci, cs);
-          corr += wt[delta + 2] * det;
-        }
-        corr *= (C)0.5;
-        out[p] += scale * (incoming ? corr : -corr);
-      }
-    }
+    stream_axis<Sc, F>(g, B, LFin, W, l, a, x, y, vp, has, ent, fs, offv, out, scale, tmp, win);
   }
 
   // ---- the four single finest cells of each diagonal velocity
@@ -350,7 +450,7 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
         const int p = P0 + t;
         const C wab = (Sc::eta(p, 0) > 0 ? wx0 : wx1) * (Sc::eta(p, 1) > 0 ? wy0 : wy1);
         if (wab == (C)0) continue;
-        const C v = self ? f[p] : ld_off<F>(vp, p, offv);
+        const C v = self ? fs[p] : ld_off<F>(vp, p, offv);
         acc[t] += wab * v;
       }
     }
@@ -410,7 +510,7 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
     const int sx = Sc::eta(p, 0), sy = Sc::eta(p, 1);
     const bool outx = !g.periodic[0] && (sx > 0 ? x == 0 : x == Nx - 1);
     const bool outy = !g.periodic[1] && (sy > 0 ? y == 0 : y == Ny - 1);
-    if (outx && outy) acc[t] -= bc_value<C>(g, g.bc[sy > 0 ? 2 : 3], f, p, Sc::opp(p));
+    if (outx && outy) acc[t] -= bc_value<C>(g, g.bc[sy > 0 ? 2 : 3], fs, p, Sc::opp(p));
     out[p] += scale2 * acc[t];
   }
 }
@@ -427,6 +527,11 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
   constexpr int D = Sc::D, Q = Sc::Q;
   extern __shared__ int pre[];
   __shared__ InstDev si;
+  // per-thread buffers: the leaf's populations and the rolled loops' terms
+  constexpr int STR = ThreadStride<Q>::value;
+  __shared__ C fsh[MR_WIN_TPB * STR], tsh[MR_WIN_TPB * STR];
+  C* fs = fsh + threadIdx.x * STR;
+  C* tmp = tsh + threadIdx.x * STR;
   int have = -1;
   mr_inst_prefetch(si, have, IB, ngrp);
   const int tiles =
@@ -441,18 +546,19 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
     const S* __restrict__ LFin = (const S*)si.fscratch;
     S* __restrict__ LFout = (S*)si.fstate;
     const C* __restrict__ W = mr_wtab<C>(si);
-    const C cs = MR_K(C, g, cross_sign);
     const int i = (tt - pre[b]) * MR_WIN_TPB + threadIdx.x;
     if (i >= B.cnt->total[MR_CLS_LEAF]) continue;
     const int l = B.lvl[MR_CLS_LEAF][i];
     const uint32_t code = B.code[MR_CLS_LEAF][i];
-    C f[Q], out[Q], offv[Q];
+    // the leaf's own populations stay in shared memory (fs) beside the
+    // register accumulators, and the storage offsets are read where used
+    const C* offv = mr_offv<C>(g);
+    C out[Q];
 #pragma unroll
     for (int p = 0; p < Q; ++p) {
-      offv[p] = OFFS ? MR_K(C, g, off[p]) : (C)0;
       ValPtr<S> me{LFin + i, g.cap[0]};
-      f[p] = ld_off<F>(me, p, offv);
-      out[p] = f[p];
+      out[p] = ld_off<F>(me, p, offv);
+      fs[p] = out[p];
     }
     if (do_stream) {
       int x, y;
@@ -460,23 +566,16 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
       const C scale = (C)__longlong_as_double((long long)(1023 + l - g.J) << 52);  // 2^{l-J}, exact
       if constexpr (Sc::DIAG) {
         __shared__ int32_t win[25][MR_WIN_TPB];
-        stream_window_d2<Sc, F>(g, B, LFin, W, l, x, y, i, f, offv, out, scale, win);
+        stream_window_d2<Sc, F>(g, B, LFin, W, l, x, y, i, fs, offv, out, scale, tmp, win);
       } else {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          const int k = a == 0 ? x : y;
-          const int N = g.n[l][a];
-          const int per = g.periodic[a];
-          const int slot = mr_slot(k, N, per);
-          const C* wP = W + MR_WIDX(l, a, slot, 0);
-          const C* wM = W + MR_WIDX(l, a, slot, 1);
-          // window: delta = -2, -1, +1, +2 along a
           ValPtr<S> vp[4];
           bool has[4];
           int32_t ent[4];
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
-            const int off = w < 2 ? w - 2 : w - 1;
+            const int off = w < 2 ? w - 2 : w - 1;  // -2, -1, +1, +2 along a
             int nx = x + (a == 0 ? off : 0), ny = y + (a == 1 ? off : 0);
             has[w] = mr_nbr_mesh(g, l, nx, ny);
             ent[w] = has[w] ? B.map[g.base[l] + mr_encode(g, l, nx, ny)] : MR_MAP_NONE;
@@ -486,80 +585,7 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
             }
             vp[w] = mr_resolve<S>(g, B, LFin, has[w] ? ent[w] : 0);
           }
-#pragma unroll
-          for (int p = 0; p < Q; ++p) {
-            const int sgn = eta_of<Sc>(p, a);
-            if (sgn == 0) continue;
-            const C* w = sgn > 0 ? wP : wM;
-            C acc = w[2] * f[p];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (has[q]) acc += w[q < 2 ? q : q + 1] * ld_off<F>(vp[q], p, offv);
-            if (!per) {
-              if (sgn > 0 && k == 0) acc += bc_value<C>(g, g.bc[2 * a], f, p, Sc::opp(p));
-              if (sgn < 0 && k == N - 1) acc += bc_value<C>(g, g.bc[2 * a + 1], f, p, Sc::opp(p));
-            }
-            out[p] += scale * acc;
-          }
-          // critical case: a refined neighbour on either side along a
-#pragma unroll
-          for (int side = -1; side <= 1; side += 2) {
-            const int wi = side < 0 ? 1 : 2;
-            if (!has[wi] || (((uint32_t)ent[wi]) >> 30) != MR_CLS_INT) continue;
-            int nx = x + (a == 0 ? side : 0), ny = y + (a == 1 ? side : 0);
-            mr_nbr_mesh(g, l, nx, ny);
-            int32_t st[9];
-            if (!mr_stencil_entries<D>(g, B, l, nx, ny, st)) {
-              mr_set_err(B.cnt, MR_DERR_INTERNAL);
-              continue;
-            }
-            ValPtr<S> sv[D == 2 ? 9 : 3], cv[1 << D];
-#pragma unroll
-            for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) sv[kk] = mr_resolve<S>(g, B, LFin, st[kk]);
-            const uint32_t ncode = mr_encode(g, l, nx, ny);
-            bool ok = true;
-#pragma unroll
-            for (int ci = 0; ci < (1 << D); ++ci) {
-              const int32_t e = B.map[g.base[l + 1] + ((ncode << D) | (uint32_t)ci)];
-              ok = ok && e != MR_MAP_NONE;
-              cv[ci] = mr_resolve<S>(g, B, LFin, e);
-            }
-            if (!ok) {
-              mr_set_err(B.cnt, MR_DERR_INTERNAL);
-              continue;
-            }
-            const int N1 = g.n[l + 1][a];
-#pragma unroll
-            for (int p = 0; p < Q; ++p) {
-              const int sgn = eta_of<Sc>(p, a);
-              if (sgn == 0) continue;
-              // the strip on the neighbour's side: incoming part if the
-              // neighbour is upwind, outgoing part otherwise
-              const bool incoming = (sgn > 0) == (side < 0);
-              int c;  // child-level cell whose edge value is corrected
-              if (sgn > 0)
-                c = side < 0 ? 2 * k - 1 : 2 * k + 1;
-              else
-                c = side > 0 ? 2 * k + 2 : 2 * k;
-              const int cslot = mr_slot(per ? 2 : c, N1, per);
-              const C* wt = W + MR_WIDX(l + 1, a, cslot, sgn > 0 ? 2 : 3);
-              // details are exact on constants: stored values suffice
-              C v[D == 2 ? 9 : 3];
-#pragma unroll
-              for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) v[kk] = ld_c<C>(sv[kk], p);
-              C corr = (C)0;
-#pragma unroll
-              for (int ci = 0; ci < (1 << D); ++ci) {
-                const int sa = (ci >> a) & 1;
-                const int delta = 2 * (k + side) + sa - c;
-                if (delta < -2 || delta > 2) continue;
-                const C det = ld_c<C>(cv[ci], p) - predict_c<D, C>(v, ci, cs);
-                corr += wt[delta + 2] * det;
-              }
-              corr *= (D == 2 ? (C)0.5 : (C)1);
-              out[p] += scale * (incoming ? corr : -corr);
-            }
-          }
+          stream_axis<Sc, F>(g, B, LFin, W, l, a, x, y, vp, has, ent, fs, offv, out, scale, tmp, nullptr);
         }
       }
     }
