@@ -167,6 +167,54 @@ __device__ __forceinline__ int mr_level_of(const Geo& g, uint32_t gi) {
   }                        \
   }
 
+// ------------------------------------------------------------------ boxes
+// Morton codes of a box of cells around (x, y) on level l (d = 2).  The code
+// of cell (X, Y) is (root << 2l) | spread(X mod 2^l) | spread(Y mod 2^l) << 1
+// with root = (X >> l) + roots_x (Y >> l): a sum of a part of X and a part
+// of Y, so the (2R+1)^2 codes of the box come from 2R+1 column parts and
+// 2R+1 row parts (a few integer operations per cell instead of a full
+// interleave).  Columns and rows are x + o - R, o = 0..2R, wrapped on a
+// periodic axis; ix / iy are false for one outside a non-periodic domain.
+// With `half` the codes are those of the parents (X >> 1, Y >> 1), on level
+// l - 1, of the (wrapped) level-l cells.
+template <int R>
+struct MortonBox {
+  static constexpr int W = 2 * R + 1;
+  uint32_t px[W], rx[W], py[W], ry[W];
+  bool ix[W], iy[W];
+  int sh;
+  __device__ __forceinline__ void init(const Geo& g, int l, int x, int y, bool half = false) {
+    const int Nx = g.n[l][0], Ny = g.n[l][1];
+    const int lc = half ? l - 1 : l;
+    const uint32_t mask = (1u << lc) - 1u;
+    sh = 2 * lc;
+#pragma unroll
+    for (int o = 0; o < W; ++o) {
+      int X = x + o - R, Y = y + o - R;
+      ix[o] = X >= 0 && X < Nx;
+      if (!ix[o] && g.periodic[0]) {
+        X = mr_wrap(X, Nx);
+        ix[o] = true;
+      }
+      iy[o] = Y >= 0 && Y < Ny;
+      if (!iy[o] && g.periodic[1]) {
+        Y = mr_wrap(Y, Ny);
+        iy[o] = true;
+      }
+      if (half) {
+        X >>= 1;
+        Y >>= 1;
+      }
+      px[o] = mr_spread2((uint32_t)X & mask);
+      rx[o] = (uint32_t)X >> lc;
+      py[o] = mr_spread2((uint32_t)Y & mask) << 1;
+      ry[o] = (uint32_t)g.roots[0] * ((uint32_t)Y >> lc);
+    }
+  }
+  __device__ __forceinline__ bool in(int a, int b) const { return ix[a] && iy[b]; }
+  __device__ __forceinline__ uint32_t code(int a, int b) const { return ((rx[a] + ry[b]) << sh) | px[a] | py[b]; }
+};
+
 // ------------------------------------------------------------------ groups
 // A step kernel runs one phase for every instance of a group.  The phase's
 // work in instance b is count(b) passes of the block ("tiles"); the tiles of

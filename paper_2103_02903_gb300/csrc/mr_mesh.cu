@@ -98,12 +98,20 @@ __global__ void __launch_bounds__(256) k_flags_H(const InstDev* __restrict__ IB,
 template <int D>
 __device__ __forceinline__ uint32_t grade_need(const Geo& g, const uint8_t* flags, int L, int x, int y) {
   uint32_t m = 0;
+  const uint8_t* fl = flags + g.base[L - 1];
+  if constexpr (D == 2) {
+    MortonBox<1> bx;
+    bx.init(g, L, x, y, true);
 #pragma unroll
-  for (int k = 0; k < (D == 2 ? 9 : 3); ++k) {
-    int nx = x + (k % 3) - 1, ny = D == 2 ? y + (k / 3) - 1 : 0;
-    if (!mr_nbr_mesh(g, L, nx, ny)) continue;
-    const uint32_t gt = g.base[L - 1] + mr_encode(g, L - 1, nx >> 1, ny >> 1);
-    if (!(flags[gt] & (MR_F_H | MR_F_G))) m |= 1u << k;
+    for (int k = 0; k < 9; ++k)
+      if (bx.in(k % 3, k / 3) && !(fl[bx.code(k % 3, k / 3)] & (MR_F_H | MR_F_G))) m |= 1u << k;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      int nx = x + k - 1, ny = 0;
+      if (!mr_nbr_mesh(g, L, nx, ny)) continue;
+      if (!(fl[mr_encode(g, L - 1, nx >> 1, 0)] & (MR_F_H | MR_F_G))) m |= 1u << k;
+    }
   }
   return m;
 }
@@ -200,11 +208,20 @@ __global__ void __launch_bounds__(256) k_full_mesh(Geo g, uint8_t* cls) {
 template <int D>
 __device__ __forceinline__ uint32_t ghost_stencil_need(const Geo& g, const uint8_t* cls, int L, int x, int y) {
   uint32_t m = 0;
+  const uint8_t* cl = cls + g.base[L];
+  if constexpr (D == 2) {
+    MortonBox<1> bx;
+    bx.init(g, L, x, y);
 #pragma unroll
-  for (int k = 0; k < (D == 2 ? 9 : 3); ++k) {
-    int ax = x + (k % 3) - 1, ay = D == 2 ? y + (k / 3) - 1 : 0;
-    if (!mr_nbr_mesh(g, L, ax, ay)) continue;
-    if (!(cls[g.base[L] + mr_encode(g, L, ax, ay)] & (3u | MR_C_GHOST))) m |= 1u << k;
+    for (int k = 0; k < 9; ++k)
+      if (bx.in(k % 3, k / 3) && !(cl[bx.code(k % 3, k / 3)] & (3u | MR_C_GHOST))) m |= 1u << k;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      int ax = x + k - 1, ay = 0;
+      if (!mr_nbr_mesh(g, L, ax, ay)) continue;
+      if (!(cl[mr_encode(g, L, ax, 0)] & (3u | MR_C_GHOST))) m |= 1u << k;
+    }
   }
   return m;
 }
@@ -238,22 +255,32 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
     int x, y;
     mr_decode(g, l, c, x, y);
     uint32_t need = 0;
-    if (block) {
+    const uint8_t* cl = cls + g.base[l];
+    if constexpr (D == 2) {
+      MortonBox<2> bx;
+      bx.init(g, l, x, y);
+      if (block) {
 #pragma unroll
-      for (int w = 0; w < 25; ++w) {
-        if (w == 12) continue;  // the leaf itself
-        int nx, ny;
-        ghost_window_cell(true, w, x, y, nx, ny);
-        if (!mr_nbr_mesh(g, l, nx, ny)) continue;
-        if (!(cls[g.base[l] + mr_encode(g, l, nx, ny)] & (3u | MR_C_GHOST))) need |= 1u << w;
+        for (int w = 0; w < 25; ++w) {
+          if (w == 12) continue;  // the leaf itself
+          if (bx.in(w % 5, w / 5) && !(cl[bx.code(w % 5, w / 5)] & (3u | MR_C_GHOST))) need |= 1u << w;
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          const int axis = w >> 2, k = w & 3;
+          const int off = k < 2 ? k - 2 : k - 1;
+          const int a = axis == 0 ? 2 + off : 2, b = axis == 1 ? 2 + off : 2;
+          if (bx.in(a, b) && !(cl[bx.code(a, b)] & (3u | MR_C_GHOST))) need |= 1u << w;
+        }
       }
     } else {
 #pragma unroll
-      for (int w = 0; w < 4 * D; ++w) {
+      for (int w = 0; w < 4; ++w) {
         int nx, ny;
         ghost_window_cell(false, w, x, y, nx, ny);
         if (!mr_nbr_mesh(g, l, nx, ny)) continue;
-        if (!(cls[g.base[l] + mr_encode(g, l, nx, ny)] & (3u | MR_C_GHOST))) need |= 1u << w;
+        if (!(cl[mr_encode(g, l, nx, ny)] & (3u | MR_C_GHOST))) need |= 1u << w;
       }
     }
     while (need) {

@@ -366,32 +366,8 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
   const C cs = MR_K(C, g, cross_sign);
   const int tid = threadIdx.x;
   {
-    // The Morton code of cell (X, Y) of level l is
-    // (root << 2l) | spread(X mod 2^l) | spread(Y mod 2^l) << 1 with
-    // root = X >> l + roots_x (Y >> l): separable, so the block's 25 codes
-    // come from 5 column parts and 5 row parts.
-    const int Nx = g.n[l][0], Ny = g.n[l][1];
-    const uint32_t mask = (1u << l) - 1u;
-    uint32_t px[5], rx[5], py[5], ry[5];
-    bool ix[5], iy[5];
-#pragma unroll
-    for (int o = 0; o < 5; ++o) {
-      int X = x + o - 2, Y = y + o - 2;
-      ix[o] = X >= 0 && X < Nx;
-      if (!ix[o] && g.periodic[0]) {
-        X = mr_wrap(X, Nx);
-        ix[o] = true;
-      }
-      iy[o] = Y >= 0 && Y < Ny;
-      if (!iy[o] && g.periodic[1]) {
-        Y = mr_wrap(Y, Ny);
-        iy[o] = true;
-      }
-      px[o] = mr_spread2((uint32_t)X & mask);
-      rx[o] = (uint32_t)X >> l;
-      py[o] = mr_spread2((uint32_t)Y & mask) << 1;
-      ry[o] = (uint32_t)g.roots[0] * ((uint32_t)Y >> l);
-    }
+    MortonBox<2> bx;
+    bx.init(g, l, x, y);
     const int32_t* map = B.map + g.base[l];
     int32_t e[25];
 #pragma unroll
@@ -400,7 +376,7 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
       if (w == 12)
         e[w] = (int32_t)((MR_CLS_LEAF << 30) | (uint32_t)i);
       else
-        e[w] = ix[a] && iy[b] ? map[((rx[a] + ry[b]) << (2 * l)) | px[a] | py[b]] : MR_WIN_OUT;
+        e[w] = bx.in(a, b) ? map[bx.code(a, b)] : MR_WIN_OUT;
     }
     bool bad = false;
 #pragma unroll
