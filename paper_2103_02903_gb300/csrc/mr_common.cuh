@@ -215,6 +215,15 @@ struct MortonBox {
   __device__ __forceinline__ uint32_t code(int a, int b) const { return ((rx[a] + ry[b]) << sh) | px[a] | py[b]; }
 };
 
+// Entry e (x fastest) of the 3^D prediction stencil of cell (x, y) on level
+// l, with the stencil's boundary rule (periodic wrap, else the nearest cell).
+template <int D>
+__device__ __forceinline__ int32_t mr_stencil_entry(const Geo& g, const MeshDev& M, int l, int x, int y, int e) {
+  int sx = x + (e % 3) - 1, sy = D == 2 ? y + (e / 3) - 1 : 0;
+  mr_nbr_stencil(g, l, sx, sy);
+  return M.map[g.base[l] + mr_encode(g, l, sx, sy)];
+}
+
 // ------------------------------------------------------------------ groups
 // A step kernel runs one phase for every instance of a group.  The phase's
 // work in instance b is count(b) passes of the block ("tiles"); the tiles of

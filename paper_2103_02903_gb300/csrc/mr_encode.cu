@@ -83,6 +83,10 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
   // the group norm is a maximum of absolute values: compared as the integer
   // bit patterns of non-negative doubles (same order), on the integer pipe
   __shared__ unsigned long long red[PY][32];
+  // the cell's 3^D stencil entries and 2^D child entries, looked up once per
+  // cell (spread over the population rows) and shared through the block
+  constexpr int NS = D == 2 ? 9 : 3, NE = NS + (1 << D);
+  __shared__ int32_t sent[NE][32];
   int have = -1;
   mr_inst_prefetch(si, have, IB, n);
   const int tiles = mr_group_prefix(pre, n, [&](int b) { return (IB[b].mesh[cur].cnt->total[MR_CLS_INT] + 31) / 32; });
@@ -94,23 +98,29 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
     const void* LF = si.fstate;
     const int nI = A.cnt->total[MR_CLS_INT];
     const int i = (t - pre[b]) * 32 + threadIdx.x;
-    unsigned long long gmax = 0ull;
     if (i < nI) {
       const int L = A.lvl[MR_CLS_INT][i];
       const uint32_t code = A.code[MR_CLS_INT][i];
       int x, y;
       mr_decode(g, L, code, x, y);
-      int32_t st[9];
-      bool ok = mr_stencil_entries<D>(g, A, L, x, y, st);
-      ValPtr<S> sv[D == 2 ? 9 : 3], cv[1 << D];
+      for (int e = threadIdx.y; e < NE; e += PY)
+        sent[e][threadIdx.x] = e < NS ? mr_stencil_entry<D>(g, A, L, x, y, e)
+                                      : A.map[g.base[L + 1] + ((code << D) | (uint32_t)(e - NS))];
+    }
+    __syncthreads();
+    unsigned long long gmax = 0ull;
+    if (i < nI) {
+      bool ok = true;
+      ValPtr<S> sv[NS], cv[1 << D];
 #pragma unroll
-      for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) {
-        ok = ok && (((uint32_t)st[kk]) >> 30) <= MR_CLS_INT;
-        sv[kk] = mr_resolve<S>(g, A, LF, st[kk]);
+      for (int kk = 0; kk < NS; ++kk) {
+        const int32_t e = sent[kk][threadIdx.x];
+        ok = ok && (((uint32_t)e) >> 30) <= MR_CLS_INT;
+        sv[kk] = mr_resolve<S>(g, A, LF, e);
       }
 #pragma unroll
       for (int ci = 0; ci < (1 << D); ++ci) {
-        int32_t e = A.map[g.base[L + 1] + ((code << D) | (uint32_t)ci)];
+        const int32_t e = sent[NS + ci][threadIdx.x];
         ok = ok && e != MR_MAP_NONE && (((uint32_t)e) >> 30) <= MR_CLS_INT;
         cv[ci] = mr_resolve<S>(g, A, LF, e);
       }
@@ -119,9 +129,9 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
       } else {
 #pragma unroll
         for (int p = threadIdx.y; p < Q; p += PY) {
-          double v[D == 2 ? 9 : 3], c[1 << D];
+          double v[NS], c[1 << D];
 #pragma unroll
-          for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) v[kk] = mr_ld(sv[kk], p);
+          for (int kk = 0; kk < NS; ++kk) v[kk] = mr_ld(sv[kk], p);
 #pragma unroll
           for (int ci = 0; ci < (1 << D); ++ci) c[ci] = mr_ld(cv[ci], p);
           double pr[1 << D];

@@ -92,7 +92,11 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
     return (c->off[MR_CLS_GHOST][l + 1] - c->off[MR_CLS_GHOST][l] + c->off[MR_CLS_LEAF][l + 1] -
             c->off[MR_CLS_LEAF][l] + 31) / 32;
   });
-  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+  // the parent's 3^D stencil entries, looked up once per cell (spread over
+  // the population rows) and shared through the block
+  constexpr int NS = D == 2 ? 9 : 3;
+  __shared__ int32_t sent[NS][32];
+  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {  // uniform over the block
     const int b = mr_group_find(pre, ngrp, tt);
     mr_inst_use(si, have, IB, b);
     const Geo& g = si.g;
@@ -104,38 +108,50 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
     const int ng = ge - gb, total = ng + (le - lb);
     const C cs = MR_K(C, g, cross_sign);
     const int t = (tt - pre[b]) * 32 + threadIdx.x;
-    if (t >= total) continue;
-    uint32_t code;
-    S* out;
-    size_t ostride;
-    if (t < ng) {
-      const int i = gb + t;
-      code = B.code[MR_CLS_GHOST][i];
-      out = (S*)B.GF + i;
-      ostride = g.cap[2];
-    } else {
-      const int i = lb + (t - ng);
-      if (B.src[i] >= 0) continue;
-      code = B.code[MR_CLS_LEAF][i];
-      out = (S*)LF + i;
-      ostride = g.cap[0];
+    bool active = t < total;
+    uint32_t code = 0;
+    S* out = nullptr;
+    size_t ostride = 0;
+    if (active) {
+      if (t < ng) {
+        const int i = gb + t;
+        code = B.code[MR_CLS_GHOST][i];
+        out = (S*)B.GF + i;
+        ostride = g.cap[2];
+      } else {
+        const int i = lb + (t - ng);
+        active = B.src[i] < 0;  // a leaf carried over keeps its transferred values
+        code = B.code[MR_CLS_LEAF][i];
+        out = (S*)LF + i;
+        ostride = g.cap[0];
+      }
     }
-    int px, py;
-    mr_decode(g, level - 1, code >> D, px, py);
-    int32_t st[9];
-    if (!mr_stencil_entries<D>(g, B, level - 1, px, py, st)) {
+    __syncthreads();  // the previous tile's readers of sent are done
+    if (active) {
+      int px, py;
+      mr_decode(g, level - 1, code >> D, px, py);
+      for (int e = threadIdx.y; e < NS; e += PY) sent[e][threadIdx.x] = mr_stencil_entry<D>(g, B, level - 1, px, py, e);
+    }
+    __syncthreads();
+    if (!active) continue;
+    ValPtr<S> sv[NS];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const int32_t e = sent[k][threadIdx.x];
+      ok = ok && e != MR_MAP_NONE;
+      sv[k] = mr_resolve<S>(g, B, LF, e);
+    }
+    if (!ok) {
       if (threadIdx.y == 0) mr_set_err(B.cnt, MR_DERR_INTERNAL);
       continue;
     }
-    ValPtr<S> sv[D == 2 ? 9 : 3];
-#pragma unroll
-    for (int k = 0; k < (D == 2 ? 9 : 3); ++k) sv[k] = mr_resolve<S>(g, B, LF, st[k]);
     const int ci = (int)(code & ((1u << D) - 1u));
 #pragma unroll
     for (int p = threadIdx.y; p < Q; p += PY) {
-      C v[D == 2 ? 9 : 3];
+      C v[NS];
 #pragma unroll
-      for (int k = 0; k < (D == 2 ? 9 : 3); ++k) v[k] = ld_c<C>(sv[k], p);
+      for (int k = 0; k < NS; ++k) v[k] = ld_c<C>(sv[k], p);
       out[(size_t)p * ostride] = mr_from_d<S>((double)predict_c<D, C>(v, ci, cs));
     }
   }
