@@ -73,6 +73,66 @@ __global__ void __launch_bounds__(256) k_project(const InstDev* __restrict__ IB,
   }
 }
 
+// Details of one population of a sibling group in FP16 storage, on the
+// integer pipe.  A finite half is an integer multiple of 2^-24 below 2^16 in
+// magnitude, so every operation of the canonical FP64 prediction (sums of at
+// most four values, products with 1/8 and 1/64) and the difference with
+// the child are exact in FP64: the details are these exact values, which
+// 64-bit integers in units of 2^-30 reproduce (|value| < 2^50).  The largest
+// |detail| is folded into imax.  Returns false (nothing done) when a value
+// is not finite: the FP64 path then handles that population.
+__device__ __forceinline__ long long half_units30(__half h) {
+  const unsigned int b = __half_as_ushort(h);
+  const int e = (int)((b >> 10) & 31u), m = (int)(b & 1023u);
+  const long long a = e ? (long long)(1024 | m) << (e - 1) : (long long)m;  // |h| 2^24
+  return (b & 0x8000u) ? -64 * a : 64 * a;
+}
+
+template <int D>
+__device__ __forceinline__ bool half_details(const ValPtr<__half>* sv, const ValPtr<__half>* cv, int p,
+                                             double cross_sign, long long& imax) {
+  constexpr int NS = D == 2 ? 9 : 3;
+  __half hv[NS], hc[1 << D];
+  unsigned int nonfinite = 0;
+#pragma unroll
+  for (int kk = 0; kk < NS; ++kk) {
+    hv[kk] = __ldg(sv[kk].p + (size_t)p * sv[kk].stride);
+    nonfinite |= ((__half_as_ushort(hv[kk]) & 0x7c00u) == 0x7c00u);
+  }
+#pragma unroll
+  for (int ci = 0; ci < (1 << D); ++ci) {
+    hc[ci] = __ldg(cv[ci].p + (size_t)p * cv[ci].stride);
+    nonfinite |= ((__half_as_ushort(hc[ci]) & 0x7c00u) == 0x7c00u);
+  }
+  if (nonfinite) return false;
+  long long w[NS], pr[1 << D];
+#pragma unroll
+  for (int kk = 0; kk < NS; ++kk) w[kk] = half_units30(hv[kk]);
+  // the canonical prediction, exactly: c1 = -1/8, c1^2 = 1/64 (the operands
+  // are multiples of 64, so the shifts divide exactly)
+  if constexpr (D == 1) {
+    const long long q = -((w[2] - w[0]) >> 3);
+    pr[0] = w[1] + q;
+    pr[1] = w[1] - q;
+  } else {
+    const long long qx = -((w[5] - w[3]) >> 3), qy = -((w[7] - w[1]) >> 3);
+    const long long q2 = (((w[8] - w[6]) - w[2]) + w[0]) >> 6;
+    const long long a = w[4] + qx, b = w[4] - qx;
+    const long long s = cross_sign > 0 ? q2 : -q2;
+    pr[0] = a + qy + s;
+    pr[1] = b + qy - s;
+    pr[2] = a - qy - s;
+    pr[3] = b - qy + s;
+  }
+#pragma unroll
+  for (int ci = 0; ci < (1 << D); ++ci) {
+    long long d = half_units30(hc[ci]) - pr[ci];
+    d = d < 0 ? -d : d;
+    imax = d > imax ? d : imax;
+  }
+  return true;
+}
+
 template <int D, int Q, int F>
 __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB, int n, int cur) {
   mr_grid_dep();
@@ -127,8 +187,12 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
       if (!ok) {
         if (threadIdx.y == 0) mr_set_err(A.cnt, MR_DERR_INTERNAL);
       } else {
+        long long imax = 0;  // FP16 storage: largest |detail| in units of 2^-30
 #pragma unroll
         for (int p = threadIdx.y; p < Q; p += PY) {
+          if constexpr (F == MR_FORM_F32_F16) {
+            if (half_details<D>(sv, cv, p, g.cross_sign, imax)) continue;
+          }
           double v[NS], c[1 << D];
 #pragma unroll
           for (int kk = 0; kk < NS; ++kk) v[kk] = mr_ld(sv[kk], p);
@@ -142,6 +206,12 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
                 (unsigned long long)__double_as_longlong(__dsub_rn(c[ci], pr[ci])) & 0x7fffffffffffffffull;
             gmax = a > gmax ? a : gmax;
           }
+        }
+        if (imax > 0) {
+          // exact: imax < 2^50, and the scaling is a power of two
+          const unsigned long long a =
+              (unsigned long long)__double_as_longlong(__dmul_rn(__ll2double_rn(imax), 0x1p-30));
+          gmax = a > gmax ? a : gmax;
         }
       }
     }
