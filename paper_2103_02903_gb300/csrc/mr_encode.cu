@@ -25,13 +25,13 @@ struct PopRows {
 
 template <int D, int Q, int F>
 __global__ void __launch_bounds__(256) k_project(const InstDev* __restrict__ IB, int n, int cur, int k) {
-  mr_grid_dep();
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
   __shared__ InstDev si;
   int have = -1;
   mr_inst_prefetch(si, have, IB, n);
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const int tiles = mr_group_prefix(pre, n, [&](int b) {
     const InstDev& I = IB[b];
     const int L = I.g.J - k;
@@ -135,7 +135,6 @@ __device__ __forceinline__ bool half_details(const ValPtr<__half>* sv, const Val
 
 template <int D, int Q, int F>
 __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB, int n, int cur) {
-  mr_grid_dep();
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
@@ -149,6 +148,7 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
   __shared__ int32_t sent[NE][32];
   int have = -1;
   mr_inst_prefetch(si, have, IB, n);
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const int tiles = mr_group_prefix(pre, n, [&](int b) { return (IB[b].mesh[cur].cnt->total[MR_CLS_INT] + 31) / 32; });
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {  // uniform over the block
     const int b = mr_group_find(pre, n, t);

@@ -228,9 +228,11 @@ struct Group {
 
 // Launch of a step kernel with programmatic dependent launch: the next
 // kernel of the stream may be scheduled while this one drains.  Every
-// kernel launched this way begins with mr_grid_dep(), which waits for the
-// grid before it to complete and its writes to be visible, so the order of
-// the stream is kept; only the launch latency is overlapped.
+// kernel launched this way calls mr_grid_dep(), which waits for the grid
+// before it to complete and its writes to be visible, before it reads
+// anything an earlier kernel writes (only the copy of its instance
+// descriptor, written by the host before the step, comes first), so the
+// order of the stream is kept; only the launch latency is overlapped.
 template <typename... KArgs, typename... Args>
 inline cudaError_t mr_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                                  Args... args) {

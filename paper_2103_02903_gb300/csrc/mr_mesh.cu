@@ -25,6 +25,7 @@ __device__ __forceinline__ double level_eps(const Geo& g, int l) { return ldexp(
   __shared__ InstDev si;                                                                      \
   int have = -1;                                                                              \
   mr_inst_prefetch(si, have, IB, N);                                                          \
+  mr_grid_dep();                                                                              \
   const int tiles =                                                                           \
       mr_group_prefix(pre, N, [&](int b) { return (IB[b].mesh[CUR].cnt->total[MR_CLS_INT] + 255) / 256; }); \
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {                                        \
@@ -38,7 +39,6 @@ __device__ __forceinline__ double level_eps(const Geo& g, int l) { return ldexp(
 
 template <int D>
 __global__ void __launch_bounds__(256) k_flags_T(const InstDev* __restrict__ IB, int n, int cur) {
-  mr_grid_dep();
   MR_INT_TILES_BEGIN(IB, n, cur, g, A, i)
     uint8_t* flags = si.flags;
     const int L = A.lvl[MR_CLS_INT][i];
@@ -59,7 +59,6 @@ __global__ void __launch_bounds__(256) k_flags_T(const InstDev* __restrict__ IB,
 // ---------------------------------------------------------------- H_eps
 template <int D>
 __global__ void __launch_bounds__(256) k_flags_H(const InstDev* __restrict__ IB, int n, int cur) {
-  mr_grid_dep();
   MR_INT_TILES_BEGIN(IB, n, cur, g, A, i)
     uint8_t* flags = si.flags;
     const int L = A.lvl[MR_CLS_INT][i];
@@ -118,13 +117,13 @@ __device__ __forceinline__ uint32_t grade_need(const Geo& g, const uint8_t* flag
 
 template <int D>
 __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, int n) {
-  mr_grid_dep();
   // tiles of 256 cells strided over the grid (not one block per chunk):
   // refined cells cluster, and interleaving spreads their cascades
   extern __shared__ int pre[];
   __shared__ InstDev si;
   int have = -1;
   mr_inst_prefetch(si, have, IB, n);
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const int tiles = mr_group_prefix(pre, n, [&](int b) {
     const Geo& gb = IB[b].g;
     return gb.J > gb.Jmin + 1 ? (int)((gb.base[gb.J] - gb.base[gb.Jmin + 1] + 255) / 256) : 0;
@@ -175,10 +174,10 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
 template <int D>
 __global__ void __launch_bounds__(256) k_classify(const InstDev* __restrict__ IB,
                                                   const int* __restrict__ chunk_pre, int n) {
-  mr_grid_dep();
   __shared__ InstDev si;
   int chunk, have = -1;
   mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const Geo& g = si.g;
   const uint8_t* flags = si.flags;
   uint8_t* cls = si.cls;
@@ -243,10 +242,10 @@ __device__ __forceinline__ void ghost_window_cell(bool block, int w, int x, int 
 template <int D>
 __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__ IB,
                                                      const int* __restrict__ chunk_pre, int n) {
-  mr_grid_dep();
   __shared__ InstDev si;
   int chunk, have = -1;
   mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const Geo& g = si.g;
   uint8_t* cls = si.cls;
   const bool block = D == 2 && g.diag;
@@ -353,12 +352,12 @@ __global__ void __launch_bounds__(1024) k_count(const InstDev* __restrict__ IB, 
 }
 
 __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict__ IB, int dst) {
-  mr_grid_dep();
   __shared__ int warp_sums[32];
   __shared__ int carry;
   __shared__ InstDev si;
   int have = -1;
   mr_inst_use(si, have, IB, blockIdx.x);
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const Geo& g = si.g;
   int* bc = si.bcounts;
   const int nblocks = (int)(g.base[g.J + 1] / MR_DENSE_ALIGN);
@@ -420,12 +419,12 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict_
 
 __global__ void __launch_bounds__(1024) k_scatter(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
                                                   int n, int dst) {
-  mr_grid_dep();
   __shared__ int wcount[32][3];
   __shared__ int woff[32][3];
   __shared__ InstDev si;
   int chunk, have = -1;
   mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const Geo& g = si.g;
   uint8_t* cls = si.cls;
   uint8_t* flags = si.flags;
@@ -510,7 +509,7 @@ __global__ void __launch_bounds__(256) k_leaves_check(Geo g, const uint8_t* __re
     else                                                         \
       KER<2><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);            \
   } while (0)
-// step kernels (they begin with mr_grid_dep)
+// step kernels (they call mr_grid_dep before reading what an earlier kernel writes)
 #define MR_DISPATCH_D_PDL(KER, GRID, BLOCK, SMEM, ST, ...)                 \
   do {                                                                     \
     if (D_ == 1)                                                           \

@@ -29,13 +29,13 @@ namespace {
 // populations (threadIdx.y), one population per warp.
 template <int Q, int F>
 __global__ void __launch_bounds__(256) k_remesh_copy(const InstDev* __restrict__ IB, int ngrp, int cur) {
-  mr_grid_dep();
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
   __shared__ InstDev si;
   int have = -1;
   mr_inst_prefetch(si, have, IB, ngrp);
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const int tiles = mr_group_prefix(pre, ngrp, [&](int b) {
     const MeshCounts* c = IB[b].mesh[1 - cur].cnt;
     return (c->total[MR_CLS_LEAF] + c->total[MR_CLS_INT] + 31) / 32;
@@ -76,7 +76,6 @@ __global__ void __launch_bounds__(256) k_remesh_copy(const InstDev* __restrict__
 // applied to level-1 values of the new mesh (all present by construction).
 template <int D, int Q, int F>
 __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict__ IB, int ngrp, int dst, int kl) {
-  mr_grid_dep();
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
   constexpr int PY = PopRows<Q>::value;
@@ -84,6 +83,7 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
   __shared__ InstDev si;
   int have = -1;
   mr_inst_prefetch(si, have, IB, ngrp);
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const int tiles = mr_group_prefix(pre, ngrp, [&](int b) {
     const Geo& gb = IB[b].g;
     const int l = gb.Jmin + kl;
@@ -511,7 +511,6 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
 template <int SC, int F>
 __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __restrict__ IB, int ngrp, int dst,
                                                         int do_stream, int do_collide) {
-  mr_grid_dep();
   using Sc = Scheme<SC>;
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
@@ -526,6 +525,7 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
   C* tmp = tsh + threadIdx.x * STR;
   int have = -1;
   mr_inst_prefetch(si, have, IB, ngrp);
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const int tiles =
       mr_group_prefix(pre, ngrp, [&](int b) {
         return (IB[b].mesh[dst].cnt->total[MR_CLS_LEAF] + MR_WIN_TPB - 1) / MR_WIN_TPB;
