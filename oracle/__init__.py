@@ -32,6 +32,7 @@ class OrConfig(C.Structure):
         ("bc", C.c_int * 6),
         ("cross_sign", C.c_int),
         ("obstacle", C.c_int),
+        ("exact_collision", C.c_int),
     ]
 
 
@@ -94,6 +95,7 @@ def make_config(cfg: dict) -> OrConfig:
         c.bc[i] = BCS[b] if isinstance(b, str) else int(b)
     c.cross_sign = int(cfg.get("cross_sign", 1))
     c.obstacle = int(cfg.get("obstacle", 0))
+    c.exact_collision = int(cfg.get("exact_collision", 0))
     return c
 
 

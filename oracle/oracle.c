@@ -20,7 +20,9 @@
  * under tests/ (prediction: Table 1, Appendix 2, polynomial exactness,
  * consistency Eq. ConsistencyPrediction; details: Eq. DetailRedundancy;
  * step: epsilon = 0 reduces to Eq. StreamFinest; conservation; Eq.
- * PredictionWithMatrix; brute-force minimal grading).
+ * PredictionWithMatrix; brute-force minimal grading; the exact collision:
+ * linear equilibria, finest leaves, mass, closed-form D1Q2 composition in
+ * tests/test_oracle_exact_collision.py).
  */
 #include "oracle.h"
 
@@ -763,6 +765,45 @@ static double boundary_value(const or_state* S, int face, const double* fleaf, i
   }
 }
 
+/* The "original adaptive" collision (Sec. 5.3, the right-hand side of
+ * Eq. sourceoferror): instead of colliding the leaf's own averages
+ * (Eq. AdaptiveCollision), reconstruct the post-transport data on every
+ * finest cell (the reconstruction operator of Sec. 4.4), collide each finest
+ * cell of B_{j,k} (Eq. CellSplitting) and give the leaf the average,
+ * 2^{-d(J-j)} times the sum over B_{j,k} taken x fastest, then y, then z. */
+static int exact_collision_impl(or_state* S) {
+  const int Q = S->Q, d = S->d, J = S->J;
+  double* F[MAXL];
+  unsigned char* inR[MAXL];
+  if (alloc_F(S, F) || alloc_u8(S, inR)) return -1;
+  reconstruct_all(S, S->leaf, S->val, F, inR);
+  double* g = (double*)malloc(sizeof(double) * Q);
+  double* acc = (double*)malloc(sizeof(double) * Q);
+  for (int j = S->Jmin; j <= J; ++j)
+    for (long long c = 0; c < S->nc[j]; ++c) {
+      if (!S->leaf[j][c]) continue;
+      int kx, ky, kz;
+      cell_coords(S, j, c, &kx, &ky, &kz);
+      const int w = 1 << (J - j);
+      const int wy = d >= 2 ? w : 1, wz = d >= 3 ? w : 1;
+      for (int p = 0; p < Q; ++p) acc[p] = 0.0;
+      for (int cz = 0; cz < wz; ++cz)
+        for (int cy = 0; cy < wy; ++cy)
+          for (int cx = 0; cx < w; ++cx) {
+            const long long k = cidx(S, J, kx * w + cx, d >= 2 ? ky * wy + cy : 0, d >= 3 ? kz * wz + cz : 0);
+            memcpy(g, &F[J][k * Q], sizeof(double) * Q);
+            collide_cell(S, g);
+            for (int p = 0; p < Q; ++p) acc[p] += g[p];
+          }
+      for (int p = 0; p < Q; ++p) S->val[j][c * Q + p] = acc[p] * ldexp(1.0, -d * (J - j));
+    }
+  free(g);
+  free(acc);
+  free_F(S, F);
+  free_u8(S, inR);
+  return 0;
+}
+
 /* Eq. AdaptiveAdvectionPhase with Eq. AdvectionOnBoundary, literally: the sums
  * run over the finest cells of E = (B - eta) \ B and A = B \ (B - eta). */
 static int stream_impl(or_state* S, int do_collide) {
@@ -824,12 +865,13 @@ static int stream_impl(or_state* S, int do_collide) {
             }
         out[p] = fl[p] + ldexp(1.0, d * (j - J)) * ((sumE - sumA) + sumB);
       }
-      if (do_collide) collide_cell(S, out);
+      if (do_collide && !S->cfg.exact_collision) collide_cell(S, out);
       memcpy(&S->val[j][c * Q], out, sizeof(double) * Q);
     }
   free(out);
   free_F(S, F);
   free_u8(S, inR);
+  if (do_collide && S->cfg.exact_collision && exact_collision_impl(S)) return -1;
   if (do_collide && S->cfg.obstacle) {
     /* Sec. 7.2.2 penalisation.  Reading: the volume fraction is the share of
      * finest-cell centres of B inside the disc. */

@@ -44,6 +44,7 @@ typedef struct {
   int bc[6];           /* -x,+x,-y,+y,-z,+z */
   int cross_sign;      /* +1 tensor-product prediction, -1 diagonal term as printed */
   int obstacle;        /* 1: volume-fraction penalisation after collision (Sec. 7.2) */
+  int exact_collision; /* 1: collide the reconstructed finest data, then average (Eq. sourceoferror) */
 } or_config;
 
 typedef struct or_state or_state;
