@@ -113,6 +113,13 @@ typedef struct {
   int obstacle;          /* 1: penalisation of Sec. 7.2.2 after each collision (D2Q9 only):
                             f <- phi f^eq(rho0, 0) + (1 - phi) f, phi = share of the leaf's
                             finest-cell centres inside the disc; xmin / xmax place the disc */
+  int exact_collision;   /* 1: the "original adaptive" collision of Sec. 5.3 (the right-hand
+                            side of Eq. sourceoferror): the post-transport data are
+                            reconstructed on every finest cell, collided there and averaged
+                            back onto each leaf, instead of colliding the leaf's averages
+                            (Eq. AdaptiveCollision).  FP64 form only, single solvers only (not
+                            in a batch, not with mr_lbm_adjoint); allocates a dense FP64
+                            buffer of Q values per cell of levels min_level..max_level. */
 } mr_lbm_config;
 
 typedef struct mr_lbm* mr_lbm_t;

@@ -54,6 +54,7 @@ class MrConfig(C.Structure):
         ("precision", C.c_int),
         ("leaf_capacity", C.c_longlong),
         ("obstacle", C.c_int),
+        ("exact_collision", C.c_int),
     ]
 
 
@@ -142,6 +143,7 @@ def make_config(cfg: Dict, leaf_capacity: int = 0) -> MrConfig:
     c.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     c.leaf_capacity = int(cfg.get("leaf_capacity", leaf_capacity))
     c.obstacle = int(cfg.get("obstacle", 0))
+    c.exact_collision = int(cfg.get("exact_collision", 0))
     return c
 
 

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmrlbm.so")
-SOURCES = ["mr_api.cu", "mr_encode.cu", "mr_mesh.cu", "mr_stream.cu", "mr_noalloc.cu", "mr_adjoint.cu"]
+SOURCES = ["mr_api.cu", "mr_encode.cu", "mr_mesh.cu", "mr_stream.cu", "mr_noalloc.cu", "mr_adjoint.cu",
+           "mr_exact.cu"]
 HEADERS = ["mr_internal.cuh", "mr_common.cuh", "mr_handle.cuh", "mr_schemes.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -246,6 +246,7 @@ mr_status validate(const mr_lbm_config* c) {
   for (int a = 0; a < 3; ++a)
     if ((c->bc[2 * a] == MR_BC_PERIODIC) != (c->bc[2 * a + 1] == MR_BC_PERIODIC)) return MR_EINVAL;
   if (c->cross_sign != 0 && c->cross_sign != 1 && c->cross_sign != -1) return MR_EINVAL;
+  if (c->exact_collision != 0 && (c->exact_collision != 1 || c->precision != MR_FP64)) return MR_EINVAL;
   return MR_OK;
 }
 
@@ -410,7 +411,8 @@ void run_stream(Exec& x, const Group& G, int dst, int do_stream, int do_collide)
 // One iteration of the loop of Algorithm 1 for every instance of a group.
 void run_step(Exec& x, const Group& G, int cur) {
   run_adapt(x, G, cur);
-  run_stream(x, G, 1 - cur, 1, 1);
+  run_stream(x, G, 1 - cur, 1, G.exact ? 0 : 1);
+  if (G.exact) x.launches += mr_launch_exact_collision(G, 1 - cur, G.exact, G.exact_nd, x.st);
   mr_launch_count_updates(G, 1 - cur, x.st);
   x.launches += 1;
 }
@@ -685,6 +687,13 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   if (!make_group(h->grp, {h}, h->dinst, dchunk, h->st, h->nsm) || !upload_desc(h)) {
     mr_lbm_destroy(h);
     return MR_ECUDA;
+  }
+  if (cfg->exact_collision) {
+    h->grp.exact_nd = (long long)dense;
+    if (!dalloc(h, &h->grp.exact, dense * g.Q)) {
+      mr_lbm_destroy(h);
+      return MR_ENOMEM;
+    }
   }
   bool cok = cudaMemsetAsync(h->cntbuf, 0, 2 * sizeof(MeshCounts), h->st) == cudaSuccess &&
              cudaMemsetAsync(h->flags, 0, dense, h->st) == cudaSuccess &&
@@ -1069,7 +1078,7 @@ mr_status mr_lbm_adjoint(mr_lbm_t h, const double* conserved0, int on_device, in
   if (h->sticky != MR_OK) return h->sticky;
   if (h->batch) return MR_ESTATE;
   const Geo& g = h->g;
-  if (g.form != MR_FORM_F64) return MR_EINVAL;
+  if (g.form != MR_FORM_F64 || h->grp.exact) return MR_EINVAL;  // the leaf collision only
   AdjArena ar;
   const size_t NJ = g.ncode[g.J], ncb = (size_t)g.ncons * NJ;
   // the initial field, kept on the device for the equilibrium's adjoint
@@ -1246,6 +1255,8 @@ mr_status mr_lbm_batch_create(const mr_lbm_config* cfgs, int n, void* cuda_strea
   if (!out) return MR_EINVAL;
   *out = nullptr;
   if (!cfgs || n <= 0) return MR_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (cfgs[i].exact_collision) return MR_EINVAL;  // single solvers only
   mr_lbm_batch* b = new (std::nothrow) mr_lbm_batch();
   if (!b) return MR_ENOMEM;
   b->st = (cudaStream_t)cuda_stream;

@@ -224,6 +224,10 @@ struct Group {
   long long proj_cells[MR_MAXL];  // summed cells of level J - k (projection phase k)
   long long pred_cells[MR_MAXL];  // summed cells of level J_min + k (prediction phase k)
   int nsm;
+  // the original adaptive collision (a group of one only): dense FP64
+  // reconstruction buffer [Q][exact_nd] indexed like the dense map, or null
+  double* exact = nullptr;
+  long long exact_nd = 0;
 };
 
 // Launch of a step kernel with programmatic dependent launch: the next
@@ -277,6 +281,9 @@ void mr_launch_remesh_copy(const Group& G, int cur, cudaStream_t st);
 void mr_launch_predict_level(const Group& G, int dst, int k, cudaStream_t st);  // level J_min + k
 void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st);
 void mr_launch_count_updates(const Group& G, int dst, cudaStream_t st);
+// Original adaptive collision of the post-transport leaves of mesh dst
+// (mr_exact.cu); returns the number of launches.
+int mr_launch_exact_collision(const Group& G, int dst, double* Fd, long long nd, cudaStream_t st);
 
 // Input / output kernels of one instance.
 void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, void* LF,
