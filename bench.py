@@ -61,6 +61,8 @@ def _args():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--max-level", type=int, default=10)
     p.add_argument("--e2e-steps", type=int, default=30)
+    p.add_argument("--exact-steps", type=int, default=200,
+                   help="steps timed with the original adaptive collision (FP64); 0 skips the leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--profile-groups", action="store_true",
@@ -320,22 +322,23 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def timed_run(form, clocks_too=False):
+    def timed_run(form, clocks_too=False, extra=None, steps=None):
         """W untimed steps, then K steps timed one by one with CUDA events
         (L2 flushed between them, outside the events)."""
-        s = Solver(dict(cfg, precision=form), stream=stream.cuda_stream)
+        steps = steps or args.steps
+        s = Solver(dict(cfg, precision=form, **(extra or {})), stream=stream.cuda_stream)
         s.init(u)
         s.step(args.warmup)
         s.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+              for _ in range(steps)]
         upd0, _ = s.counters()
         l0 = s.launch_count()
         s.profile_enable(1)  # events around the transport + collision kernel
         clk = ClockSampler(local) if clocks_too else None
         barrier()
         tw = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(steps):
             flush.fill_(k & 0xFF)
             ev[k][0].record(stream)
             s.step(1)
@@ -385,6 +388,22 @@ def run_ours(args):
             forms[fm]["transport_roofline"] = {
                 "bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s", "frac": ach / fp64_tflops,
                 "peak_kind": "FP64 measured with cuBLAS DGEMM in this run"}
+
+    # the original adaptive collision (Sec. 5.3) on the same workload, FP64
+    exact = None
+    if args.exact_steps > 0:
+        s3, r3 = timed_run("fp64", extra={"exact_collision": 1}, steps=args.exact_steps)
+        nJ = (cfg["roots"][0] << cfg["max_level"]) * (cfg["roots"][1] << cfg["max_level"])
+        ms3 = 1e3 * r3["total_s"] / args.exact_steps
+        exact = {"value": r3["updates"] / r3["total_s"], "unit": UNIT, "ms_per_step": ms3,
+                 "steps": args.exact_steps, "leaves_per_step_avg": r3["updates"] / args.exact_steps,
+                 "launches_per_step": r3["launches"] / args.exact_steps,
+                 "finest_cells_collided_per_step": nJ, "finest_cells_per_s": nJ / (ms3 / 1e3),
+                 "ms_per_step_over_leaf_collision_fp64": ms3 - forms["fp64"]["ms_per_step"],
+                 "dtype": "f64",
+                 "note": "collision on the dense reconstruction of the post-transport data at level J, "
+                         "then averaged onto the leaves (Eq. sourceoferror); timed like the other forms"}
+        s3.close()
 
     serving = run_serving(args, stream, flush, local) if args.serving_n > 0 else None
 
@@ -497,6 +516,8 @@ def run_ours(args):
         line["accuracy_of_forms"] = ("relative L1 distance of the level-J conserved moments to the FP64 oracle "
                                      "(tests/test_gpu_forms.py bounds): fp32 <= 1e-5, fp16 storage <= 1e-3, "
                                      "bf16 storage <= 2e-2")
+        if exact is not None:
+            line["exact_collision"] = exact
         if serving is not None:
             line["batched"] = serving
         print(json.dumps(line), flush=True)

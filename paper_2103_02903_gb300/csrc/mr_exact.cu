@@ -13,9 +13,12 @@
 //        prediction from its parent's 3^d stencil (the reconstruction
 //        operator of Sec. 4.4); on level J every cell is then collided in
 //        place;
-//   average: a leaf sums its collided finest cells, x fastest, and scales
-//        by 2^{-d(J-j)}; the obstacle penalisation follows as after the
-//        leaf collision.
+//   average (J-1 .. J_min): every cell outside the tree, and every leaf,
+//        takes the average of its children (collided on level J, averaged
+//        below): the leaf's average over its finest cells, 2^{-d(J-j)} times
+//        their sum, formed level by level so that no thread sums a large
+//        leaf alone; then each leaf takes its cell's value and the obstacle
+//        penalisation follows as after the leaf collision.
 // Single instances in the FP64 form; the cost is that of the dense level-J
 // grid, the explosion the paper warns about, which 2D grids up to J = 10 fit.
 #include "mr_schemes.cuh"
@@ -100,11 +103,36 @@ __global__ void __launch_bounds__(256) k_exact_down(const InstDev* __restrict__ 
   for (int p = 0; p < Q; ++p) Fd[(size_t)p * nd + gi] = f[p];
 }
 
+template <int D>
+__global__ void __launch_bounds__(256) k_exact_average(const InstDev* __restrict__ IB, int dst, int kl,
+                                                       double* __restrict__ Fd, long long nd) {
+  __shared__ InstDev si;
+  int have = -1;
+  mr_inst_use(si, have, IB, 0);
+  mr_grid_dep();
+  const Geo& g = si.g;
+  const MeshDev& B = si.mesh[dst];
+  const int l = g.Jmin + kl;
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncode[l]) return;
+  const uint32_t gi = g.base[l] + c;
+  const int32_t e = B.map[gi];
+  if (e != MR_MAP_NONE && (((uint32_t)e) >> 30) == MR_CLS_INT) return;  // not inside a leaf
+  const double scale = D == 1 ? 0.5 : 0.25;
+  const uint32_t cb = g.base[l + 1] + (c << D);
+  for (int p = 0; p < g.Q; ++p) {
+    double acc = 0.0;
+#pragma unroll
+    for (int ci = 0; ci < (1 << D); ++ci) acc += Fd[(size_t)p * nd + cb + ci];
+    Fd[(size_t)p * nd + gi] = acc * scale;
+  }
+}
+
 template <int SC>
-__global__ void __launch_bounds__(128) k_exact_average(const InstDev* __restrict__ IB, int dst,
-                                                       const double* __restrict__ Fd, long long nd) {
+__global__ void __launch_bounds__(128) k_exact_leaves(const InstDev* __restrict__ IB, int dst,
+                                                      const double* __restrict__ Fd, long long nd) {
   using Sc = Scheme<SC>;
-  constexpr int D = Sc::D, Q = Sc::Q;
+  constexpr int Q = Sc::Q;
   __shared__ InstDev si;
   int have = -1;
   mr_inst_use(si, have, IB, 0);
@@ -116,35 +144,24 @@ __global__ void __launch_bounds__(128) k_exact_average(const InstDev* __restrict
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int l = B.lvl[MR_CLS_LEAF][i];
     const uint32_t code = B.code[MR_CLS_LEAF][i];
-    int x, y;
-    mr_decode(g, l, code, x, y);
-    const int w = 1 << (g.J - l), wy = D == 2 ? w : 1;
-    double acc[Q];
+    const uint32_t gi = g.base[l] + code;
+    double f[Q];
 #pragma unroll
-    for (int p = 0; p < Q; ++p) acc[p] = 0.0;
-    for (int cy = 0; cy < wy; ++cy)
-      for (int cx = 0; cx < w; ++cx) {
-        const uint32_t k = g.base[g.J] + mr_encode(g, g.J, x * w + cx, D == 2 ? y * wy + cy : 0);
-#pragma unroll
-        for (int p = 0; p < Q; ++p) acc[p] += Fd[(size_t)p * nd + k];
-      }
-    const double sc = ldexp(1.0, -D * (g.J - l));
-#pragma unroll
-    for (int p = 0; p < Q; ++p) acc[p] *= sc;
+    for (int p = 0; p < Q; ++p) f[p] = Fd[(size_t)p * nd + gi];
     if constexpr (Sc::DIAG) {
       if (g.obstacle) {
         const double phi = obstacle_fraction(g, l, code);
         if (phi > 0.0) {
 #pragma unroll
-          for (int p = 0; p < Q; ++p) acc[p] = phi * g.feq0[p] + (1.0 - phi) * acc[p];
+          for (int p = 0; p < Q; ++p) f[p] = phi * g.feq0[p] + (1.0 - phi) * f[p];
         }
       }
     }
     bool finite = true;
 #pragma unroll
     for (int p = 0; p < Q; ++p) {
-      finite = finite && is_finite_bits(acc[p]);
-      LF[(size_t)p * g.cap[0] + i] = acc[p];
+      finite = finite && is_finite_bits(f[p]);
+      LF[(size_t)p * g.cap[0] + i] = f[p];
     }
     if (!finite) mr_set_err(B.cnt, MR_DERR_NONFINITE);
   }
@@ -159,7 +176,9 @@ void launch_exact_t(const Group& G, int dst, double* Fd, long long nd, cudaStrea
     mr_launch_pdl(k_exact_up<D>, (unsigned)((cells(k) + 255) / 256), 256, 0, st, G.dev, dst, k, Fd, nd);
   for (int k = 1; k <= span; ++k)
     mr_launch_pdl(k_exact_down<SC>, (unsigned)((cells(k) + 255) / 256), 256, 0, st, G.dev, dst, k, Fd, nd);
-  mr_launch_pdl(k_exact_average<SC>, (unsigned)(G.nsm * 8), 128, 0, st, G.dev, dst, (const double*)Fd, nd);
+  for (int k = span - 1; k >= 0; --k)
+    mr_launch_pdl(k_exact_average<D>, (unsigned)((cells(k) + 255) / 256), 256, 0, st, G.dev, dst, k, Fd, nd);
+  mr_launch_pdl(k_exact_leaves<SC>, (unsigned)(G.nsm * 8), 128, 0, st, G.dev, dst, (const double*)Fd, nd);
 }
 
 }  // namespace
@@ -173,5 +192,5 @@ int mr_launch_exact_collision(const Group& G, int dst, double* Fd, long long nd,
     case 4: launch_exact_t<4>(G, dst, Fd, nd, st); break;
     default: return 0;
   }
-  return 2 * G.span + 2;
+  return 3 * G.span + 2;
 }
