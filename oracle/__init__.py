@@ -37,7 +37,7 @@ class OrConfig(C.Structure):
 
 
 SCHEMES = {"d1q2_advection": 0, "d1q2_burgers": 1, "d1q3_shallow_water": 2,
-           "d2q4x4_euler": 3, "d2q9_ns": 4}
+           "d2q4x4_euler": 3, "d2q9_ns": 4, "d3q6_advection": 5}
 BCS = {"periodic": 0, "copy": 1, "bounce_back": 2, "anti_bounce_back": 3,
        "bounce_back_velocity": 4}
 

@@ -197,6 +197,25 @@ static int setup_scheme(or_state* S) {
       for (int i = 0; i < 3; ++i) { S->cons_lat[i] = 0; S->cons_mom[i] = i; }
       break;
     }
+    case OR_D3Q6_ADVECTION: {
+      /* Sec. 7.3: xi^h = lambda (+-e_x, +-e_y, +-e_z), M as printed,
+       * S = diag(0, s1, s1, s1, s2, s2) with s1 = s[0], s2 = s[1] */
+      S->d = 3; S->q = 6; S->m = 1;
+      for (int h = 0; h < 6; ++h) S->eta[h][h / 2] = (h & 1) ? -1 : 1;
+      int op[6] = {1, 0, 3, 2, 5, 4};
+      for (int h = 0; h < 6; ++h) S->opp[h] = op[h];
+      double L2 = L * L;
+      double row[6][6] = {{1, 1, 1, 1, 1, 1},     {L, -L, 0, 0, 0, 0},       {0, 0, L, -L, 0, 0},
+                          {0, 0, 0, 0, L, -L},     {L2, L2, -L2, -L2, 0, 0},  {L2, L2, 0, 0, -L2, -L2}};
+      for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) S->M[i][j] = row[i][j];
+      for (int r = 1; r <= 3; ++r) S->srel[0][r] = S->cfg.s[0];
+      S->srel[0][4] = S->cfg.s[1];
+      S->srel[0][5] = S->cfg.s[1];
+      S->ncons = 1;
+      S->cons_lat[0] = 0; S->cons_mom[0] = 0;
+      break;
+    }
     default:
       return -1;
   }
@@ -239,6 +258,13 @@ static void equilibrium(const or_state* S, const double* u, double meq[4][9]) {
       }
       break;
     }
+    case OR_D3Q6_ADVECTION:
+      /* Sec. 7.3: m^eq = (u, V_x u, V_y u, V_z u, 0, 0), V = phys[0..2] */
+      meq[0][0] = u[0];
+      meq[0][1] = ph[0] * u[0];
+      meq[0][2] = ph[1] * u[0];
+      meq[0][3] = ph[2] * u[0];
+      break;
     case OR_D2Q9_NS: {
       /* Sec. 7.2.2.  Reading: the printed |q|/rho terms are |q|^2/rho and the
        * c_s^4 term carries rho (Lallemand-Luo at lambda = 1). */

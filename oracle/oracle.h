@@ -25,7 +25,8 @@ enum {
   OR_D1Q2_BURGERS = 1,
   OR_D1Q3_SHALLOW_WATER = 2,
   OR_D2Q4x4_EULER = 3,
-  OR_D2Q9_NS = 4
+  OR_D2Q9_NS = 4,
+  OR_D3Q6_ADVECTION = 5
 };
 
 enum { OR_BC_PERIODIC = 0, OR_BC_COPY = 1, OR_BC_BOUNCE_BACK = 2,

@@ -26,13 +26,14 @@ SCHEMES = {
     "d1q3_shallow_water": 2,
     "d2q4x4_euler": 3,
     "d2q9_ns": 4,
+    "d3q6_advection": 5,
 }
 DIM = {"d1q2_advection": 1, "d1q2_burgers": 1, "d1q3_shallow_water": 1,
-       "d2q4x4_euler": 2, "d2q9_ns": 2}
+       "d2q4x4_euler": 2, "d2q9_ns": 2, "d3q6_advection": 3}
 NCONS = {"d1q2_advection": 1, "d1q2_burgers": 1, "d1q3_shallow_water": 2,
-         "d2q4x4_euler": 4, "d2q9_ns": 3}
+         "d2q4x4_euler": 4, "d2q9_ns": 3, "d3q6_advection": 1}
 NPOP = {"d1q2_advection": 2, "d1q2_burgers": 2, "d1q3_shallow_water": 3,
-        "d2q4x4_euler": 16, "d2q9_ns": 9}
+        "d2q4x4_euler": 16, "d2q9_ns": 9, "d3q6_advection": 6}
 BC = {"periodic": 0, "copy": 1, "bounce_back": 2, "anti_bounce_back": 3,
       "bounce_back_velocity": 4}
 
@@ -63,8 +64,11 @@ def cell_centres(cfg: Dict):
         axes.append(cfg["xmin"][a] + (np.arange(n) + 0.5) * h)
     if d == 1:
         return (axes[0],)
-    X, Y = np.meshgrid(axes[0], axes[1], indexing="xy")
-    return (X.ravel(), Y.ravel())
+    if d == 2:
+        X, Y = np.meshgrid(axes[0], axes[1], indexing="xy")
+        return (X.ravel(), Y.ravel())
+    Z, Y, X = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")  # x fastest, then y, then z
+    return (X.ravel(), Y.ravel(), Z.ravel())
 
 
 def steps_to(cfg: Dict, T: float) -> int:
@@ -225,6 +229,32 @@ def vortices_2d(seed: int = 0, max_level: int = 8, min_level: int = 2, eps: floa
     return cfg, np.stack([rho, rho * ux, rho * uy]).astype(np.float64)
 
 
+# --------------------------------------------------------------------------
+# D3Q6 advection of a ball (Sec. 7.3)
+# --------------------------------------------------------------------------
+
+def advection_3d(seed: int = 0, max_level: int = 8, min_level: int = 2, eps: float = 1e-3, mu_bar: int = 2):
+    """Indicator of a ball of radius 0.15 on the periodic cube [-0.5, 0.5]^3,
+    advected with a constant velocity V: the test of Sec. 7.3 (lambda = 1,
+    s1 = 1.4, s2 = 1, mu_bar = 2, eps = 1e-3).  The paper gives neither the
+    domain nor V: the ball's centre is drawn within 0.05 of the origin and
+    each component of V in [-0.5, 0.5] (|V_a| <= lambda / 2) from the seed.
+    J_min = 2 (the paper's 1 is below the library's smallest level)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = rng.uniform(-0.05, 0.05, 3)
+    V = rng.uniform(-0.5, 0.5, 3)
+    s = [0.0] * 16
+    s[0], s[1] = 1.4, 1.0
+    phys = [0.0] * 8
+    phys[0:3] = list(V)
+    cfg = base_config("d3q6_advection", lambda_=1.0, xmin=[-0.5, -0.5, -0.5], xmax=[0.5, 0.5, 0.5],
+                      min_level=min_level, max_level=max_level, eps=eps, mu_bar=mu_bar,
+                      bc=["periodic"] * 6, s=s, phys=phys)
+    X, Y, Z = cell_centres(cfg)
+    u = (((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) <= 0.15 ** 2).astype(np.float64)
+    return cfg, u[None, :]
+
+
 def serving_batch(seed: int = 0, n: int = 256, levels=(6, 7, 8, 9, 10), eps=(1e-3, 1e-4),
                   precision: str = "fp16"):
     """Independent instances of a batched serving load: half D2Q9 periodic
@@ -253,4 +283,5 @@ WORKLOADS = {
     "euler_2d": euler_2d,
     "ns_obstacle_2d": ns_obstacle_2d,
     "vortices_2d": vortices_2d,
+    "advection_3d": advection_3d,
 }

@@ -203,6 +203,18 @@ def _ref_scheme(cfg):
         meq = (lambda u: [[u[0], V * u[0]]]) if sch == "d1q2_advection" else (lambda u: [[u[0], 0.5 * u[0] ** 2]])
         cons = [(0, 0)]
         m = 1
+    elif sch == "d3q6_advection":
+        # Sec. 7.3: velocities +-e_x, +-e_y, +-e_z, M and S as printed
+        eta = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+        L2 = lam * lam
+        M = np.array([[1, 1, 1, 1, 1, 1], [lam, -lam, 0, 0, 0, 0], [0, 0, lam, -lam, 0, 0],
+                      [0, 0, 0, 0, lam, -lam], [L2, L2, -L2, -L2, 0, 0], [L2, L2, 0, 0, -L2, -L2]], float)
+        s1, s2 = cfg["s"][0], cfg["s"][1]
+        S = [[0, s1, s1, s1, s2, s2]]
+        Vx, Vy, Vz = cfg["phys"][0:3]
+        meq = lambda u: [[u[0], Vx * u[0], Vy * u[0], Vz * u[0], 0.0 * u[0], 0.0 * u[0]]]
+        cons = [(0, 0)]
+        m = 1
     elif sch == "d1q3_shallow_water":
         eta = [(0,), (1,), (-1,)]
         M = np.array([[1, 1, 1], [0, lam, -lam], [0, lam ** 2, lam ** 2]], float)
@@ -334,7 +346,12 @@ def _leaves_dense(o):
     lev, ix, iy, iz, f = o.leaves()
     assert (lev == o.J).all()
     shape = o.level_shape(o.J)
-    idx = iy.astype(np.int64) * shape[0] + ix if o.d == 2 else ix.astype(np.int64)
+    if o.d == 3:
+        idx = (iz.astype(np.int64) * shape[1] + iy) * shape[0] + ix
+    elif o.d == 2:
+        idx = iy.astype(np.int64) * shape[0] + ix
+    else:
+        idx = ix.astype(np.int64)
     out = np.zeros((o.Q, int(np.prod(shape))))
     out[:, idx] = f
     return out
@@ -346,6 +363,7 @@ def _leaves_dense(o):
     ("shallow_water_1d", dict(max_level=7), 20),
     ("euler_2d", dict(max_level=5), 8),
     ("ns_obstacle_2d", dict(max_level=4), 8),
+    ("advection_3d", dict(max_level=4), 6),
 ])
 def test_epsilon_zero_is_reference_scheme(name, kw, steps):
     cfg, u = W.WORKLOADS[name](seed=3, **kw)
@@ -386,7 +404,8 @@ def test_relaxation_one_reaches_equilibrium_moment():
 
 @pytest.mark.parametrize("name,kw", [("advection_1d", dict(max_level=9)),
                                      ("euler_2d", dict(max_level=6)),
-                                     ("ns_obstacle_2d", dict(max_level=5))])
+                                     ("ns_obstacle_2d", dict(max_level=5)),
+                                     ("advection_3d", dict(max_level=5))])
 def test_conservation_periodic(name, kw):
     cfg, u = W.WORKLOADS[name](seed=4, **kw)
     cfg["bc"] = ["periodic"] * 6
