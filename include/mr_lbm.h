@@ -63,13 +63,18 @@ typedef enum {
   MR_D1Q2_BURGERS = 1,       /* m^eq = (u, u^2/2) */
   MR_D1Q3_SHALLOW_WATER = 2, /* m^eq = (h, q, q^2/h + g h^2/2), g = phys[0] */
   MR_D2Q4x4_EULER = 3,       /* vectorial D2Q4^4 of Sec. 7.1.2, gamma = phys[0] */
-  MR_D2Q9_NS = 4             /* D2Q9 of Sec. 7.2.2 (orthogonal moments, Lallemand-Luo):
+  MR_D2Q9_NS = 4,            /* D2Q9 of Sec. 7.2.2 (orthogonal moments, Lallemand-Luo):
                                 conserved (rho, q_x, q_y); s[0] relaxes the energy, energy
                                 square and heat-flux moments, s[1] the two stress moments;
                                 rho0 = phys[0], u0 = (phys[1], phys[2]) for
                                 MR_BC_BOUNCE_BACK_VELOCITY and the obstacle; obstacle disc
                                 centre (phys[3], phys[4]), radius phys[5].  Needs the
                                 tensor-product prediction (cross_sign +1). */
+  MR_D3Q6_ADVECTION = 5      /* D3Q6 of Sec. 7.3: eta = +-e_x, +-e_y, +-e_z, the printed M,
+                                m^eq = (u, V_x u, V_y u, V_z u, 0, 0), V = phys[0..2];
+                                s[0] = s1 (first moments), s[1] = s2 (the two second
+                                moments); d = 3, keys are 3-way Morton codes with a root
+                                prefix, max_level <= 10 */
 } mr_scheme;
 
 typedef enum {

@@ -20,13 +20,13 @@ LIB_PATH = os.path.join(HERE, "libmrlbm.so")
 MR_STATUS = {0: "MR_OK", 1: "MR_EINVAL", 2: "MR_ENOMEM", 3: "MR_ECUDA", 4: "MR_ECAPACITY",
              5: "MR_ENOCONV", 6: "MR_ENONFINITE", 7: "MR_ESTATE", 8: "MR_EINTERNAL"}
 SCHEMES = {"d1q2_advection": 0, "d1q2_burgers": 1, "d1q3_shallow_water": 2, "d2q4x4_euler": 3,
-           "d2q9_ns": 4}
+           "d2q9_ns": 4, "d3q6_advection": 5}
 BCS = {"periodic": 0, "copy": 1, "bounce_back": 2, "anti_bounce_back": 3, "bounce_back_velocity": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 FUNCTIONALS = {"ke_sum": 1, "ke_final": 2}
-NCONS = {0: 1, 1: 1, 2: 2, 3: 4, 4: 3}
-NPOP = {0: 2, 1: 2, 2: 3, 3: 16, 4: 9}
-DIM = {0: 1, 1: 1, 2: 1, 3: 2, 4: 2}
+NCONS = {0: 1, 1: 1, 2: 2, 3: 4, 4: 3, 5: 1}
+NPOP = {0: 2, 1: 2, 2: 3, 3: 16, 4: 9, 5: 6}
+DIM = {0: 1, 1: 1, 2: 1, 3: 2, 4: 2, 5: 3}
 
 
 class MrError(RuntimeError):
@@ -399,10 +399,39 @@ def encode_keys(cfg: Dict, level, ix, iy=None) -> np.ndarray:
     return (root << (np.uint64(2) * level)) | local
 
 
+def encode_keys3(cfg: Dict, level, ix, iy, iz) -> np.ndarray:
+    """Keys of a d = 3 scheme: (root << 3l) | 3-way interleave of (x, y, z)
+    at the cell's level, root = x >> l + roots_x (y >> l + roots_y (z >> l))."""
+    level = np.asarray(level, np.uint64)
+    ix, iy, iz = (np.asarray(v, np.uint64) for v in (ix, iy, iz))
+    mask = (np.uint64(1) << level) - np.uint64(1)
+    root = (ix >> level) + np.uint64(cfg["roots"][0]) * ((iy >> level) + np.uint64(cfg["roots"][1]) * (iz >> level))
+    local = _spread(ix & mask, 3) | (_spread(iy & mask, 3) << np.uint64(1)) | (_spread(iz & mask, 3) << np.uint64(2))
+    return (root << (np.uint64(3) * level)) | local
+
+
+def decode_keys3(cfg: Dict, level, keys):
+    """(x, y, z) of the keys of a d = 3 scheme."""
+    keys = np.asarray(keys, np.uint64)
+    level = np.asarray(level, np.uint64)
+    root = keys >> (np.uint64(3) * level)
+    local = keys & ((np.uint64(1) << (np.uint64(3) * level)) - np.uint64(1))
+    rxy = np.uint64(cfg["roots"][0] * cfg["roots"][1])
+    rz, rr = root // rxy, root % rxy
+    rx, ry = rr % np.uint64(cfg["roots"][0]), rr // np.uint64(cfg["roots"][0])
+    x = (rx << level) | _compact(local, 3)
+    y = (ry << level) | _compact(local >> np.uint64(1), 3)
+    z = (rz << level) | _compact(local >> np.uint64(2), 3)
+    return x.astype(np.int64), y.astype(np.int64), z.astype(np.int64)
+
+
 def decode_keys(cfg: Dict, level, keys):
+    """(x, y) of the keys of a d <= 2 scheme (y = 0 in 1D); (x, y, z) for d = 3."""
     d = DIM[SCHEMES[cfg["scheme"]]]
     keys = np.asarray(keys, np.uint64)
     level = np.asarray(level, np.uint64)
+    if d == 3:
+        return decode_keys3(cfg, level, keys)
     if d == 1:
         return keys.astype(np.int64), np.zeros(keys.shape, np.int64)
     root = keys >> (np.uint64(2) * level)

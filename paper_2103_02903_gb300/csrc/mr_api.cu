@@ -83,6 +83,14 @@ bool scheme_setup(Geo& g, const mr_lbm_config* c) {
       }
       break;
     }
+    case MR_D3Q6_ADVECTION:
+      g.d = 3; g.q = 6; g.m = 1; g.ncons = 1;
+      for (int h = 0; h < 6; ++h) {
+        g.eta[h][h / 2] = (h & 1) ? -1 : 1;
+        g.opp[h] = h ^ 1;
+        g.consw[0][h] = 1;
+      }
+      break;
     default:
       return false;
   }
@@ -201,6 +209,12 @@ void host_equilibrium(const Geo& g, const double* u, double* f) {
       }
       break;
     }
+    case MR_D3Q6_ADVECTION: {
+      // m^eq = (u, V u, 0, 0): a = b = c = u / 3 (see Scheme<5>)
+      const double a = u[0] / 3.0;
+      for (int h = 0; h < 6; ++h) f[h] = 0.5 * (a + ((h & 1) ? -1.0 : 1.0) * g.phys[h / 2] * u[0] / L);
+      break;
+    }
     case MR_D2Q9_NS: {
       // orthogonal integer rows R_r (the rows of M over their power of
       // lambda): f = sum_r R_r mu_r / |R_r|^2, j = q / lambda
@@ -229,7 +243,8 @@ void host_equilibrium(const Geo& g, const double* u, double* f) {
 
 mr_status validate(const mr_lbm_config* c) {
   if (!c) return MR_EINVAL;
-  if (c->scheme < 0 || c->scheme > MR_D2Q9_NS) return MR_EINVAL;
+  if (c->scheme < 0 || c->scheme > MR_D3Q6_ADVECTION) return MR_EINVAL;
+  if (c->scheme == MR_D3Q6_ADVECTION && c->max_level > 10) return MR_EINVAL;  // 30-bit 3-way codes
   if (c->scheme == MR_D2Q9_NS && c->cross_sign == -1) return MR_EINVAL;  // needs the tensor product
   if (c->obstacle != 0 && (c->obstacle != 1 || c->scheme != MR_D2Q9_NS)) return MR_EINVAL;
   for (int f = 0; f < 6; ++f)
@@ -246,7 +261,9 @@ mr_status validate(const mr_lbm_config* c) {
   for (int a = 0; a < 3; ++a)
     if ((c->bc[2 * a] == MR_BC_PERIODIC) != (c->bc[2 * a + 1] == MR_BC_PERIODIC)) return MR_EINVAL;
   if (c->cross_sign != 0 && c->cross_sign != 1 && c->cross_sign != -1) return MR_EINVAL;
-  if (c->exact_collision != 0 && (c->exact_collision != 1 || c->precision != MR_FP64)) return MR_EINVAL;
+  if (c->exact_collision != 0 &&
+      (c->exact_collision != 1 || c->precision != MR_FP64 || c->scheme == MR_D3Q6_ADVECTION))
+    return MR_EINVAL;
   return MR_OK;
 }
 
@@ -594,7 +611,8 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   g.Jmin = cfg->min_level;
   g.J = cfg->max_level;
   for (int a = 0; a < 3; ++a) g.roots[a] = a < g.d ? std::max(1, cfg->roots[a]) : 1;
-  if (g.d == 2 && (g.roots[0] * g.roots[1] > 2)) {  // root prefix must fit the 32-bit key
+  if ((g.d == 2 && g.roots[0] * g.roots[1] > 2) ||
+      (g.d == 3 && g.roots[0] * g.roots[1] * g.roots[2] > 2)) {  // root prefix must fit the 32-bit key
     delete h;
     return MR_EINVAL;
   }
@@ -1078,7 +1096,7 @@ mr_status mr_lbm_adjoint(mr_lbm_t h, const double* conserved0, int on_device, in
   if (h->sticky != MR_OK) return h->sticky;
   if (h->batch) return MR_ESTATE;
   const Geo& g = h->g;
-  if (g.form != MR_FORM_F64 || h->grp.exact) return MR_EINVAL;  // the leaf collision only
+  if (g.form != MR_FORM_F64 || h->grp.exact || g.d == 3) return MR_EINVAL;  // 1D and 2D, the leaf collision
   AdjArena ar;
   const size_t NJ = g.ncode[g.J], ncb = (size_t)g.ncons * NJ;
   // the initial field, kept on the device for the equilibrium's adjoint
@@ -1094,7 +1112,7 @@ mr_status mr_lbm_adjoint(mr_lbm_t h, const double* conserved0, int on_device, in
   mr_status s = mr_lbm_init(h, cons, 1);
   if (s != MR_OK) return s;
   const int K = checkpoint_every, nseg = (nsteps + K - 1) / K;
-  const double vol_J = g.d == 1 ? g.dxJ : g.dxJ * g.dxJ;
+  const double vol_J = g.d == 1 ? g.dxJ : g.d == 2 ? g.dxJ * g.dxJ : g.dxJ * g.dxJ * g.dxJ;
   const int grid = grid_for(h, 4);
   std::vector<Checkpoint> cps(nseg + 1);
   // forward pass: the functional and a checkpoint every K steps

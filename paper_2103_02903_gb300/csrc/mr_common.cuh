@@ -347,11 +347,11 @@ __device__ __forceinline__ double mr_predict_canonical(const double* v, int ci, 
 // children share are formed once.  out[ci], ci = x bit | y bit << 1.
 template <int D>
 __device__ __forceinline__ void mr_predict_children_canonical(const double* v, int cross_sign, double* out) {
-  if (D == 1) {
+  if constexpr (D == 1) {
     const double q = __dmul_rn(MR_C1, __dsub_rn(v[2], v[0]));
     out[0] = __dadd_rn(v[1], q);
     out[1] = __dsub_rn(v[1], q);
-  } else {
+  } else if constexpr (D == 2) {
     const double qx = __dmul_rn(MR_C1, __dsub_rn(v[5], v[3]));
     const double qy = __dmul_rn(MR_C1, __dsub_rn(v[7], v[1]));
     const double q2 = __dmul_rn(MR_C1 * MR_C1, __dadd_rn(__dsub_rn(__dsub_rn(v[8], v[6]), v[2]), v[0]));
@@ -367,6 +367,42 @@ __device__ __forceinline__ void mr_predict_children_canonical(const double* v, i
       out[1] = __dadd_rn(t1, q2);
       out[2] = __dadd_rn(t2, q2);
       out[3] = __dsub_rn(t3, q2);
+    }
+  } else {
+    // d = 3: the tensor product of the one-dimensional operator, terms added
+    // in the order x, y, z, xy, xz, yz, xyz (pairs carrying cross_sign)
+#define MR_V3(a, b, c) v[(((c) + 1) * 3 + ((b) + 1)) * 3 + ((a) + 1)]
+    const double qx = __dmul_rn(MR_C1, __dsub_rn(MR_V3(1, 0, 0), MR_V3(-1, 0, 0)));
+    const double qy = __dmul_rn(MR_C1, __dsub_rn(MR_V3(0, 1, 0), MR_V3(0, -1, 0)));
+    const double qz = __dmul_rn(MR_C1, __dsub_rn(MR_V3(0, 0, 1), MR_V3(0, 0, -1)));
+    const double qxy = __dmul_rn(MR_C1 * MR_C1, __dadd_rn(__dsub_rn(__dsub_rn(MR_V3(1, 1, 0), MR_V3(-1, 1, 0)),
+                                                                     MR_V3(1, -1, 0)), MR_V3(-1, -1, 0)));
+    const double qxz = __dmul_rn(MR_C1 * MR_C1, __dadd_rn(__dsub_rn(__dsub_rn(MR_V3(1, 0, 1), MR_V3(-1, 0, 1)),
+                                                                     MR_V3(1, 0, -1)), MR_V3(-1, 0, -1)));
+    const double qyz = __dmul_rn(MR_C1 * MR_C1, __dadd_rn(__dsub_rn(__dsub_rn(MR_V3(0, 1, 1), MR_V3(0, -1, 1)),
+                                                                     MR_V3(0, 1, -1)), MR_V3(0, -1, -1)));
+    double w = __dsub_rn(MR_V3(1, 1, 1), MR_V3(-1, 1, 1));
+    w = __dsub_rn(w, MR_V3(1, -1, 1));
+    w = __dsub_rn(w, MR_V3(1, 1, -1));
+    w = __dadd_rn(w, MR_V3(-1, -1, 1));
+    w = __dadd_rn(w, MR_V3(-1, 1, -1));
+    w = __dadd_rn(w, MR_V3(1, -1, -1));
+    w = __dsub_rn(w, MR_V3(-1, -1, -1));
+    const double q3 = __dmul_rn(MR_C1 * MR_C1 * MR_C1, w);
+    const double t0 = MR_V3(0, 0, 0);
+#undef MR_V3
+#pragma unroll
+    for (int ci = 0; ci < 8; ++ci) {
+      const int sx = (ci & 1) ? -1 : 1, sy = (ci & 2) ? -1 : 1, sz = (ci & 4) ? -1 : 1;
+      // t + s q with s = +-1 is t + q or t - q, bit for bit
+      auto add = [](double t, int s, double q) { return s > 0 ? __dadd_rn(t, q) : __dsub_rn(t, q); };
+      double t = add(t0, sx, qx);
+      t = add(t, sy, qy);
+      t = add(t, sz, qz);
+      t = add(t, cross_sign * sx * sy, qxy);
+      t = add(t, cross_sign * sx * sz, qxz);
+      t = add(t, cross_sign * sy * sz, qyz);
+      out[ci] = add(t, sx * sy * sz, q3);
     }
   }
 }
@@ -402,4 +438,28 @@ __device__ __forceinline__ bool mr_stencil_entries(const Geo& g, const MeshDev& 
       ok = ok && (e != MR_MAP_NONE);
     }
   return ok;
+}
+
+// Coordinate-array forms (any D): entry e (x fastest) of the 3^D stencil of
+// the cell c on level l, and all of them.
+template <int D>
+__device__ __forceinline__ int32_t mr_stencil_entry_d(const Geo& g, const MeshDev& M, int l, const int* c, int e) {
+  int s[3] = {c[0] + (e % 3) - 1, D >= 2 ? c[1] + (e / 3) % 3 - 1 : 0, D == 3 ? c[2] + e / 9 - 1 : 0};
+  mr_nbr_stencil_d<D>(g, l, s);
+  return M.map[g.base[l] + mr_encode_d<D>(g, l, s)];
+}
+template <int D>
+__device__ __forceinline__ bool mr_stencil_entries_d(const Geo& g, const MeshDev& M, int l, const int* c,
+                                                     int32_t* ent) {
+  if constexpr (D <= 2) {
+    return mr_stencil_entries<D>(g, M, l, c[0], D == 2 ? c[1] : 0, ent);
+  } else {
+    bool ok = true;
+#pragma unroll 1
+    for (int e = 0; e < 27; ++e) {
+      ent[e] = mr_stencil_entry_d<3>(g, M, l, c, e);
+      ok = ok && (ent[e] != MR_MAP_NONE);
+    }
+    return ok;
+  }
 }

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_project(const InstDev* __restrict__ IB,
     const MeshCounts* c = I.mesh[cur].cnt;
     return (c->off[MR_CLS_INT][L + 1] - c->off[MR_CLS_INT][L] + 31) / 32;
   });
-  const double scale = D == 1 ? 0.5 : 0.25;
+  const double scale = D == 1 ? 0.5 : D == 2 ? 0.25 : 0.125;  // 2^-d
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int b = mr_group_find(pre, n, t);
     mr_inst_use(si, have, IB, b);
@@ -91,6 +91,7 @@ __device__ __forceinline__ long long half_units30(__half h) {
 template <int D>
 __device__ __forceinline__ bool half_details(const ValPtr<__half>* sv, const ValPtr<__half>* cv, int p,
                                              double cross_sign, long long& imax) {
+  if constexpr (D == 3) return false;  // d = 3 keeps the FP64 path
   constexpr int NS = D == 2 ? 9 : 3;
   __half hv[NS], hc[1 << D];
   unsigned int nonfinite = 0;
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
   __shared__ unsigned long long red[PY][32];
   // the cell's 3^D stencil entries and 2^D child entries, looked up once per
   // cell (spread over the population rows) and shared through the block
-  constexpr int NS = D == 2 ? 9 : 3, NE = NS + (1 << D);
+  constexpr int NS = Pow3<D>::value, NE = NS + (1 << D);
   __shared__ int32_t sent[NE][32];
   int have = -1;
   mr_inst_prefetch(si, have, IB, n);
@@ -161,10 +162,10 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
     if (i < nI) {
       const int L = A.lvl[MR_CLS_INT][i];
       const uint32_t code = A.code[MR_CLS_INT][i];
-      int x, y;
-      mr_decode(g, L, code, x, y);
+      int c[3] = {0, 0, 0};
+      mr_decode_d<D>(g, L, code, c);
       for (int e = threadIdx.y; e < NE; e += PY)
-        sent[e][threadIdx.x] = e < NS ? mr_stencil_entry<D>(g, A, L, x, y, e)
+        sent[e][threadIdx.x] = e < NS ? mr_stencil_entry_d<D>(g, A, L, c, e)
                                       : A.map[g.base[L + 1] + ((code << D) | (uint32_t)(e - NS))];
     }
     __syncthreads();
@@ -255,6 +256,7 @@ void launch_details_t(const Group& G, int cur, cudaStream_t st) {
     case 103: MR_DISPATCH_F(FN, 1, 3, __VA_ARGS__); break;        \
     case 209: MR_DISPATCH_F(FN, 2, 9, __VA_ARGS__); break;        \
     case 216: MR_DISPATCH_F(FN, 2, 16, __VA_ARGS__); break;       \
+    case 306: MR_DISPATCH_F(FN, 3, 6, __VA_ARGS__); break;        \
     default: break;                                               \
   }
 

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_exact_up(const InstDev* __restrict__ IB
   if (cls == MR_CLS_LEAF) {
     for (int p = 0; p < g.Q; ++p) Fd[(size_t)p * nd + gi] = LF[(size_t)p * g.cap[0] + idx];
   } else if (cls == MR_CLS_INT) {
-    const double scale = D == 1 ? 0.5 : 0.25;
+    const double scale = D == 1 ? 0.5 : D == 2 ? 0.25 : 0.125;  // 2^-d
     const uint32_t cb = g.base[l + 1] + (c << D);
     for (int p = 0; p < g.Q; ++p) {
       double acc = 0.0;
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_exact_average(const InstDev* __restrict
   const uint32_t gi = g.base[l] + c;
   const int32_t e = B.map[gi];
   if (e != MR_MAP_NONE && (((uint32_t)e) >> 30) == MR_CLS_INT) return;  // not inside a leaf
-  const double scale = D == 1 ? 0.5 : 0.25;
+  const double scale = D == 1 ? 0.5 : D == 2 ? 0.25 : 0.125;  // 2^-d
   const uint32_t cb = g.base[l + 1] + (c << D);
   for (int p = 0; p < g.Q; ++p) {
     double acc = 0.0;

@@ -123,6 +123,24 @@ __host__ __device__ inline uint32_t mr_compact2(uint32_t x) {
   return x;
 }
 
+// three-way interleave of 10-bit integers (d = 3)
+__host__ __device__ inline uint32_t mr_spread3(uint32_t x) {
+  x &= 0x000003FFu;
+  x = (x | (x << 16)) & 0x030000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+__host__ __device__ inline uint32_t mr_compact3(uint32_t x) {
+  x &= 0x09249249u;
+  x = (x | (x >> 2)) & 0x030C30C3u;
+  x = (x | (x >> 4)) & 0x0300F00Fu;
+  x = (x | (x >> 8)) & 0x030000FFu;
+  x = (x | (x >> 16)) & 0x000003FFu;
+  return x;
+}
+
 __host__ __device__ inline uint32_t mr_encode(const Geo& g, int l, int x, int y) {
   if (g.d == 1) return (uint32_t)x;
   uint32_t mask = (1u << l) - 1u;
@@ -142,6 +160,27 @@ __host__ __device__ inline void mr_decode(const Geo& g, int l, uint32_t code, in
   int rx = (int)(root % (uint32_t)g.roots[0]), ry = (int)(root / (uint32_t)g.roots[0]);
   x = (rx << l) | (int)mr_compact2(local);
   y = (ry << l) | (int)mr_compact2(local >> 1);
+}
+
+// d = 3: (root << 3l) | spread3(x) | spread3(y) << 1 | spread3(z) << 2, with
+// root = x >> l + roots_x (y >> l + roots_y (z >> l))
+__host__ __device__ inline uint32_t mr_encode3(const Geo& g, int l, int x, int y, int z) {
+  uint32_t mask = (1u << l) - 1u;
+  uint32_t root = (uint32_t)(x >> l) +
+                  (uint32_t)g.roots[0] * ((uint32_t)(y >> l) + (uint32_t)g.roots[1] * (uint32_t)(z >> l));
+  uint32_t local = mr_spread3((uint32_t)x & mask) | (mr_spread3((uint32_t)y & mask) << 1) |
+                   (mr_spread3((uint32_t)z & mask) << 2);
+  return (root << (3 * l)) | local;
+}
+__host__ __device__ inline void mr_decode3(const Geo& g, int l, uint32_t code, int& x, int& y, int& z) {
+  uint32_t root = code >> (3 * l);
+  uint32_t local = code & ((l > 0) ? ((1u << (3 * l)) - 1u) : 0u);
+  const uint32_t rxy = (uint32_t)g.roots[0] * (uint32_t)g.roots[1];
+  int rz = (int)(root / rxy), rr = (int)(root % rxy);
+  int rx = rr % g.roots[0], ry = rr / g.roots[0];
+  x = (rx << l) | (int)mr_compact3(local);
+  y = (ry << l) | (int)mr_compact3(local >> 1);
+  z = (rz << l) | (int)mr_compact3(local >> 2);
 }
 
 // periodic wrap of a cell index a few cells outside [0, n): every caller
@@ -179,6 +218,50 @@ __host__ __device__ inline void mr_nbr_stencil(const Geo& g, int l, int& x, int&
     y = 0;
   }
 }
+
+// Dimension-generic forms of the above on a coordinate array c[D]: for D <= 2
+// they call the two-coordinate functions (c[1] = 0 when D = 1).
+template <int D>
+__host__ __device__ inline uint32_t mr_encode_d(const Geo& g, int l, const int* c) {
+  if constexpr (D == 3)
+    return mr_encode3(g, l, c[0], c[1], c[2]);
+  else
+    return mr_encode(g, l, c[0], D == 2 ? c[1] : 0);
+}
+template <int D>
+__host__ __device__ inline void mr_decode_d(const Geo& g, int l, uint32_t code, int* c) {
+  if constexpr (D == 3) {
+    mr_decode3(g, l, code, c[0], c[1], c[2]);
+  } else {
+    int x, y;
+    mr_decode(g, l, code, x, y);
+    c[0] = x;
+    if (D == 2) c[1] = y;
+  }
+}
+template <int D>
+__host__ __device__ inline bool mr_nbr_mesh_d(const Geo& g, int l, int* c) {
+  for (int a = 0; a < D; ++a) {
+    const int n = g.n[l][a];
+    if (c[a] < 0 || c[a] >= n) {
+      if (!g.periodic[a]) return false;
+      c[a] = mr_wrap(c[a], n);
+    }
+  }
+  return true;
+}
+template <int D>
+__host__ __device__ inline void mr_nbr_stencil_d(const Geo& g, int l, int* c) {
+  for (int a = 0; a < D; ++a) {
+    const int n = g.n[l][a];
+    if (c[a] < 0 || c[a] >= n) c[a] = g.periodic[a] ? mr_wrap(c[a], n) : (c[a] < 0 ? 0 : n - 1);
+  }
+}
+// 3^D stencil / 2^D children counts
+template <int D>
+struct Pow3 {
+  static constexpr int value = D == 1 ? 3 : D == 2 ? 9 : 27;
+};
 
 __host__ __device__ inline int mr_slot(int k, int N, int periodic) {
   if (periodic) return 2;

@@ -65,16 +65,17 @@ __global__ void __launch_bounds__(256) k_flags_H(const InstDev* __restrict__ IB,
     const uint32_t code = A.code[MR_CLS_INT][i];
     if (!(flags[g.base[L] + code] & MR_F_T)) continue;
     mr_atomic_or_byte(flags, g.base[L] + code, MR_F_H);
-    int x, y;
-    mr_decode(g, L, code, x, y);
+    int c0[3] = {0, 0, 0};
+    mr_decode_d<D>(g, L, code, c0);
     // neighbour rule (Eq. AdditionNeigh) on the children, which are the
     // cells of R(T_eps(Lambda)) on level L+1
     for (int ci = 0; ci < (1 << D); ++ci) {
-      const int cx = 2 * x + (ci & 1), cy = D == 2 ? 2 * y + ((ci >> 1) & 1) : 0;
       for (int h = 0; h < g.q; ++h) {
-        int nx = cx - g.eta[h][0], ny = D == 2 ? cy - g.eta[h][1] : 0;
-        if (!mr_nbr_mesh(g, L + 1, nx, ny)) continue;
-        const uint32_t gi = g.base[L] + mr_encode(g, L, nx >> 1, ny >> 1);
+        int nb[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) nb[a] = 2 * c0[a] + ((ci >> a) & 1) - g.eta[h][a];
+        if (!mr_nbr_mesh_d<D>(g, L + 1, nb)) continue;
+        for (int a = 0; a < D; ++a) nb[a] >>= 1;
+        const uint32_t gi = g.base[L] + mr_encode_d<D>(g, L, nb);
         if (!(flags[gi] & MR_F_H)) mr_atomic_or_byte(flags, gi, MR_F_H);
       }
     }
@@ -114,6 +115,18 @@ __device__ __forceinline__ uint32_t grade_need(const Geo& g, const uint8_t* flag
   }
   return m;
 }
+// d = 3: the 27 neighbours of (x, y, z) on level L, their parents on L - 1
+__device__ __forceinline__ uint32_t grade_need3(const Geo& g, const uint8_t* flags, int L, const int* c) {
+  uint32_t m = 0;
+  const uint8_t* fl = flags + g.base[L - 1];
+  for (int k = 0; k < 27; ++k) {
+    int nb[3] = {c[0] + k % 3 - 1, c[1] + (k / 3) % 3 - 1, c[2] + k / 9 - 1};
+    if (!mr_nbr_mesh_d<3>(g, L, nb)) continue;
+    for (int a = 0; a < 3; ++a) nb[a] >>= 1;
+    if (!(fl[mr_encode_d<3>(g, L - 1, nb)] & (MR_F_H | MR_F_G))) m |= 1u << k;
+  }
+  return m;
+}
 
 template <int D>
 __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, int n) {
@@ -139,12 +152,21 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
     const int l0 = mr_level_of(g, gi);
     const uint32_t c0 = gi - g.base[l0];
     if (c0 >= g.ncode[l0]) continue;
-    int sl[MR_MAXL], sx[MR_MAXL], sy[MR_MAXL];
+    int sl[MR_MAXL], sx[MR_MAXL], sy[MR_MAXL], sz[MR_MAXL];
     uint32_t sm[MR_MAXL];
     int sp = 1;
     sl[0] = l0;
-    mr_decode(g, l0, c0, sx[0], sy[0]);
-    sm[0] = grade_need<D>(g, flags, l0, sx[0], sy[0]);
+    {
+      int c[3] = {0, 0, 0};
+      mr_decode_d<D>(g, l0, c0, c);
+      sx[0] = c[0];
+      sy[0] = c[1];
+      sz[0] = c[2];
+      if constexpr (D == 3)
+        sm[0] = grade_need3(g, flags, l0, c);
+      else
+        sm[0] = grade_need<D>(g, flags, l0, sx[0], sy[0]);
+    }
     while (sp > 0) {
       const int t = sp - 1;
       if (sm[t] == 0u) {
@@ -154,16 +176,20 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
       const int k = __ffs(sm[t]) - 1;
       sm[t] &= sm[t] - 1u;
       const int L = sl[t];
-      int nx = sx[t] + (k % 3) - 1, ny = D == 2 ? sy[t] + (k / 3) - 1 : 0;
-      mr_nbr_mesh(g, L, nx, ny);  // inside: only such cells enter the mask
+      int nb[3] = {sx[t] + (k % 3) - 1, D >= 2 ? sy[t] + (k / 3) % 3 - 1 : 0, D == 3 ? sz[t] + k / 9 - 1 : 0};
+      mr_nbr_mesh_d<D>(g, L, nb);  // inside: only such cells enter the mask
       const int tl = L - 1;
-      const int px = nx >> 1, py = ny >> 1;
-      const uint32_t old = mr_atomic_or_byte(flags, g.base[tl] + mr_encode(g, tl, px, py), MR_F_G);
+      for (int a = 0; a < D; ++a) nb[a] >>= 1;
+      const uint32_t old = mr_atomic_or_byte(flags, g.base[tl] + mr_encode_d<D>(g, tl, nb), MR_F_G);
       if (!(old & (MR_F_H | MR_F_G)) && tl > g.Jmin && sp < MR_MAXL) {
         sl[sp] = tl;
-        sx[sp] = px;
-        sy[sp] = py;
-        sm[sp] = grade_need<D>(g, flags, tl, px, py);
+        sx[sp] = nb[0];
+        sy[sp] = nb[1];
+        sz[sp] = nb[2];
+        if constexpr (D == 3)
+          sm[sp] = grade_need3(g, flags, tl, nb);
+        else
+          sm[sp] = grade_need<D>(g, flags, tl, nb[0], nb[1]);
         ++sp;
       }
     }
@@ -239,6 +265,58 @@ __device__ __forceinline__ void ghost_window_cell(bool block, int w, int x, int 
   }
 }
 
+// d = 3: the 12 axis window cells of a leaf (4 per axis), each cell outside
+// the tree marked with the cascade over the 27-cell stencils of its parents
+__device__ __forceinline__ uint32_t ghost_need3(const Geo& g, const uint8_t* cls, int L, const int* c) {
+  uint32_t m = 0;
+  const uint8_t* cl = cls + g.base[L];
+  for (int k = 0; k < 27; ++k) {
+    int nb[3] = {c[0] + k % 3 - 1, c[1] + (k / 3) % 3 - 1, c[2] + k / 9 - 1};
+    if (!mr_nbr_mesh_d<3>(g, L, nb)) continue;
+    if (!(cl[mr_encode_d<3>(g, L, nb)] & (3u | MR_C_GHOST))) m |= 1u << k;
+  }
+  return m;
+}
+
+__device__ void mark_ghosts3(const Geo& g, uint8_t* cls, int l, uint32_t code) {
+  int x[3];
+  mr_decode_d<3>(g, l, code, x);
+  for (int w = 0; w < 12; ++w) {
+    const int axis = w >> 2, k = w & 3;
+    int nb[3] = {x[0], x[1], x[2]};
+    nb[axis] += k < 2 ? k - 2 : k - 1;
+    if (!mr_nbr_mesh_d<3>(g, l, nb)) continue;
+    const uint32_t gw = g.base[l] + mr_encode_d<3>(g, l, nb);
+    if (cls[gw] & (3u | MR_C_GHOST)) continue;
+    const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
+    if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
+    int sl[MR_MAXL], sc[MR_MAXL][3];
+    uint32_t sm[MR_MAXL];
+    sl[0] = l - 1;
+    for (int a = 0; a < 3; ++a) sc[0][a] = nb[a] >> 1;
+    sm[0] = ghost_need3(g, cls, l - 1, sc[0]);
+    int sp = 1;
+    while (sp > 0) {
+      const int t = sp - 1;
+      if (sm[t] == 0u) {
+        --sp;
+        continue;
+      }
+      const int kk = __ffs(sm[t]) - 1;
+      sm[t] &= sm[t] - 1u;
+      const int L = sl[t];
+      int ac[3] = {sc[t][0] + kk % 3 - 1, sc[t][1] + (kk / 3) % 3 - 1, sc[t][2] + kk / 9 - 1};
+      mr_nbr_mesh_d<3>(g, L, ac);
+      const uint32_t o2 = mr_atomic_or_byte(cls, g.base[L] + mr_encode_d<3>(g, L, ac), MR_C_GHOST);
+      if ((o2 & MR_C_GHOST) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
+      sl[sp] = L - 1;
+      for (int a = 0; a < 3; ++a) sc[sp][a] = ac[a] >> 1;
+      sm[sp] = ghost_need3(g, cls, L - 1, sc[sp]);
+      ++sp;
+    }
+  }
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__ IB,
                                                      const int* __restrict__ chunk_pre, int n) {
@@ -251,6 +329,10 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
   const bool block = D == 2 && g.diag;
   MR_DENSE_CHUNK_BEGIN(g, chunk, l, c, gi)
     if ((cls[gi] & 3u) != MR_C_LEAF) continue;
+    if constexpr (D == 3) {
+      mark_ghosts3(g, cls, l, c);
+      continue;
+    }
     int x, y;
     mr_decode(g, l, c, x, y);
     uint32_t need = 0;
@@ -506,16 +588,20 @@ __global__ void __launch_bounds__(256) k_leaves_check(Geo g, const uint8_t* __re
   do {                                                           \
     if (D_ == 1)                                                 \
       KER<1><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);            \
-    else                                                         \
+    else if (D_ == 2)                                            \
       KER<2><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);            \
+    else                                                         \
+      KER<3><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);            \
   } while (0)
 // step kernels (they call mr_grid_dep before reading what an earlier kernel writes)
 #define MR_DISPATCH_D_PDL(KER, GRID, BLOCK, SMEM, ST, ...)                 \
   do {                                                                     \
     if (D_ == 1)                                                           \
       mr_launch_pdl(KER<1>, GRID, BLOCK, SMEM, ST, __VA_ARGS__);           \
-    else                                                                   \
+    else if (D_ == 2)                                                      \
       mr_launch_pdl(KER<2>, GRID, BLOCK, SMEM, ST, __VA_ARGS__);           \
+    else                                                                   \
+      mr_launch_pdl(KER<3>, GRID, BLOCK, SMEM, ST, __VA_ARGS__);           \
   } while (0)
 
 void mr_launch_flags_T(const Group& G, int cur, cudaStream_t st) {

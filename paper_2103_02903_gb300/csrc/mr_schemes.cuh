@@ -255,6 +255,63 @@ struct Scheme<4> {
   }
 };
 
+// D3Q6 advection (Sec. 7.3): eta = +-e_x, +-e_y, +-e_z, the printed M,
+// S = diag(0, s1, s1, s1, s2, s2), m^eq = (u, V_x u, V_y u, V_z u, 0, 0).
+// With a = f0 + f1, b = f2 + f3, c = f4 + f5 the even rows are
+// m0 = a + b + c, m4 = l^2 (a - b), m5 = l^2 (a - c), so M^-1 is closed form.
+template <>
+struct Scheme<5> {
+  static constexpr int D = 3, Q = 6;
+  static constexpr int NR = 2;
+  static constexpr bool DIAG = false;
+  __device__ static int axis(int p) { return p >> 1; }
+  __device__ static int sign(int p) { return (p & 1) ? -1 : 1; }
+  __device__ static int opp(int p) { return p ^ 1; }
+  template <class C>
+  __device__ static void from_moments(const Geo& g, const C* m, C* f) {
+    const C il = MR_K(C, g, inv_lambda), il2 = il * il;
+    const C a = (m[0] + (m[4] + m[5]) * il2) / (C)3;
+    const C b = a - m[4] * il2, c = a - m[5] * il2;
+    f[0] = (C)0.5 * (a + m[1] * il);
+    f[1] = (C)0.5 * (a - m[1] * il);
+    f[2] = (C)0.5 * (b + m[2] * il);
+    f[3] = (C)0.5 * (b - m[2] * il);
+    f[4] = (C)0.5 * (c + m[3] * il);
+    f[5] = (C)0.5 * (c - m[3] * il);
+  }
+  template <class C>
+  __device__ static void collide(const Geo& g, C* f) {
+    const C L = MR_K(C, g, lambda), L2 = L * L;
+    const C s1 = mr_rate<C>(g, 0), s2 = mr_rate<C>(g, 1);
+    C m[6];
+    const C a = f[0] + f[1], b = f[2] + f[3], c = f[4] + f[5];
+    m[0] = a + b + c;
+    m[1] = L * (f[0] - f[1]);
+    m[2] = L * (f[2] - f[3]);
+    m[3] = L * (f[4] - f[5]);
+    m[4] = L2 * (a - b);
+    m[5] = L2 * (a - c);
+#pragma unroll
+    for (int r = 1; r <= 3; ++r) m[r] = ((C)1 - s1) * m[r] + s1 * (MR_K(C, g, phys[r - 1]) * m[0]);
+    m[4] = ((C)1 - s2) * m[4];
+    m[5] = ((C)1 - s2) * m[5];
+    from_moments<C>(g, m, f);
+  }
+  template <class T>
+  __device__ static void equilibrium(const Geo& g, const T* u, T* f) {
+    T m[6] = {u[0], (T)g.phys[0] * u[0], (T)g.phys[1] * u[0], (T)g.phys[2] * u[0], (T)0, (T)0};
+    const T il = (T)g.inv_lambda, il2 = il * il;
+    const T a = (m[0] + (m[4] + m[5]) * il2) / (T)3;
+    const T b = a - m[4] * il2, c = a - m[5] * il2;
+    f[0] = (T)0.5 * (a + m[1] * il);
+    f[1] = (T)0.5 * (a - m[1] * il);
+    f[2] = (T)0.5 * (b + m[2] * il);
+    f[3] = (T)0.5 * (b - m[2] * il);
+    f[4] = (T)0.5 * (c + m[3] * il);
+    f[5] = (T)0.5 * (c - m[3] * il);
+  }
+};
+
 // eta^p_a in {-1, 0, 1} of the schemes with axis velocities only
 template <class Sc>
 __device__ __forceinline__ int eta_of(int p, int a) {
@@ -280,8 +337,24 @@ template <int D, class C>
 __device__ __forceinline__ C predict_c(const C* v, int ci, C cross_sign) {
   const C sx = (ci & 1) ? (C)-1 : (C)1;
   const C c1 = (C)MR_C1;
-  if (D == 1) {
+  if constexpr (D == 1) {
     return v[1] + sx * (c1 * (v[2] - v[0]));
+  } else if constexpr (D == 3) {
+#define MR_V3(a, b, c) v[(((c) + 1) * 3 + ((b) + 1)) * 3 + ((a) + 1)]
+    const C sy = (ci & 2) ? (C)-1 : (C)1, sz = (ci & 4) ? (C)-1 : (C)1;
+    const C qx = c1 * (MR_V3(1, 0, 0) - MR_V3(-1, 0, 0));
+    const C qy = c1 * (MR_V3(0, 1, 0) - MR_V3(0, -1, 0));
+    const C qz = c1 * (MR_V3(0, 0, 1) - MR_V3(0, 0, -1));
+    const C qxy = (c1 * c1) * (((MR_V3(1, 1, 0) - MR_V3(-1, 1, 0)) - MR_V3(1, -1, 0)) + MR_V3(-1, -1, 0));
+    const C qxz = (c1 * c1) * (((MR_V3(1, 0, 1) - MR_V3(-1, 0, 1)) - MR_V3(1, 0, -1)) + MR_V3(-1, 0, -1));
+    const C qyz = (c1 * c1) * (((MR_V3(0, 1, 1) - MR_V3(0, -1, 1)) - MR_V3(0, 1, -1)) + MR_V3(0, -1, -1));
+    const C q3 = (c1 * c1 * c1) * (((((((MR_V3(1, 1, 1) - MR_V3(-1, 1, 1)) - MR_V3(1, -1, 1)) - MR_V3(1, 1, -1)) +
+                                       MR_V3(-1, -1, 1)) + MR_V3(-1, 1, -1)) + MR_V3(1, -1, -1)) -
+                                    MR_V3(-1, -1, -1));
+    const C t = MR_V3(0, 0, 0);
+#undef MR_V3
+    return t + sx * qx + sy * qy + sz * qz + (cross_sign * sx * sy) * qxy + (cross_sign * sx * sz) * qxz +
+           (cross_sign * sy * sz) * qyz + (sx * sy * sz) * q3;
   } else {
     const C sy = (ci & 2) ? (C)-1 : (C)1;
     const C qx = c1 * (v[5] - v[3]);

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
   });
   // the parent's 3^D stencil entries, looked up once per cell (spread over
   // the population rows) and shared through the block
-  constexpr int NS = D == 2 ? 9 : 3;
+  constexpr int NS = Pow3<D>::value;
   __shared__ int32_t sent[NS][32];
   for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {  // uniform over the block
     const int b = mr_group_find(pre, ngrp, tt);
@@ -128,9 +128,9 @@ __global__ void __launch_bounds__(256) k_predict_level(const InstDev* __restrict
     }
     __syncthreads();  // the previous tile's readers of sent are done
     if (active) {
-      int px, py;
-      mr_decode(g, level - 1, code >> D, px, py);
-      for (int e = threadIdx.y; e < NS; e += PY) sent[e][threadIdx.x] = mr_stencil_entry<D>(g, B, level - 1, px, py, e);
+      int pc[3] = {0, 0, 0};
+      mr_decode_d<D>(g, level - 1, code >> D, pc);
+      for (int e = threadIdx.y; e < NS; e += PY) sent[e][threadIdx.x] = mr_stencil_entry_d<D>(g, B, level - 1, pc, e);
     }
     __syncthreads();
     if (!active) continue;
@@ -199,7 +199,7 @@ __device__ __forceinline__ void crit_axis_terms(const Geo& g, const typename For
                                                 const ValPtr<typename FormT<F>::S>* cv, typename FormT<F>::C scale,
                                                 typename FormT<F>::C* tmp) {
   using C = typename FormT<F>::C;
-  constexpr int D = Sc::D, NS = D == 2 ? 9 : 3;
+  constexpr int D = Sc::D, NS = Pow3<D>::value;
   const C cs = MR_K(C, g, cross_sign);
   const int N1 = g.n[l + 1][a];
 #pragma unroll 1
@@ -227,7 +227,7 @@ __device__ __forceinline__ void crit_axis_terms(const Geo& g, const typename For
       const C det = ld_c<C>(cv[ci], p) - predict_c<D, C>(v, ci, cs);
       corr += wt[delta + 2] * det;
     }
-    corr *= (D == 2 ? (C)0.5 : (C)1);
+    corr *= (C)1 / (C)(1 << (D - 1));  // average over the 2^{d-1} children on the shared face
     tmp[p] = scale * (incoming ? corr : -corr);
   }
 }
@@ -245,15 +245,15 @@ template <class Sc, int F>
 __device__ __forceinline__ void stream_axis(const Geo& g, const MeshDev& B,
                                             const typename FormT<F>::S* __restrict__ LFin,
                                             const typename FormT<F>::C* __restrict__ W, int l, int a, int x, int y,
-                                            const ValPtr<typename FormT<F>::S>* vp, const bool* has,
+                                            int z, const ValPtr<typename FormT<F>::S>* vp, const bool* has,
                                             const int32_t* ent, const typename FormT<F>::C* fs,
                                             const typename FormT<F>::C* offv, typename FormT<F>::C* out,
                                             typename FormT<F>::C scale, typename FormT<F>::C* tmp,
                                             const int32_t (*win)[MR_WIN_TPB]) {
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
-  constexpr int D = Sc::D, Q = Sc::Q;
-  const int k = a == 0 ? x : y;
+  constexpr int D = Sc::D, Q = Sc::Q, NS = Pow3<D>::value;
+  const int k = a == 0 ? x : (a == 1 ? y : z);
   const int N = g.n[l][a];
   const int per = g.periodic[a];
   const int slot = mr_slot(k, N, per);
@@ -282,16 +282,17 @@ __device__ __forceinline__ void stream_axis(const Geo& g, const MeshDev& B,
     if (!((refined >> si) & 1u)) continue;
     const int side = si == 0 ? -1 : 1;
     const int ox = a == 0 ? side : 0, oy = a == 1 ? side : 0;
-    int nx = x + ox, ny = y + oy;
-    mr_nbr_mesh(g, l, nx, ny);
-    int32_t st[D == 2 ? 9 : 3];
+    int nb[3] = {x, y, z};
+    nb[a] += side;
+    mr_nbr_mesh_d<D>(g, l, nb);
+    int32_t st[NS];
     bool ok;
     if constexpr (D == 2)
-      ok = win ? win_stencil(g, l, x, y, ox, oy, win, st) : mr_stencil_entries<D>(g, B, l, nx, ny, st);
+      ok = win ? win_stencil(g, l, x, y, ox, oy, win, st) : mr_stencil_entries_d<D>(g, B, l, nb, st);
     else
-      ok = mr_stencil_entries<D>(g, B, l, nx, ny, st);
-    const uint32_t ncode = mr_encode(g, l, nx, ny);
-    ValPtr<S> sv[D == 2 ? 9 : 3], cv[1 << D];
+      ok = mr_stencil_entries_d<D>(g, B, l, nb, st);
+    const uint32_t ncode = mr_encode_d<D>(g, l, nb);
+    ValPtr<S> sv[NS], cv[1 << D];
 #pragma unroll
     for (int ci = 0; ci < (1 << D); ++ci) {
       const int32_t e = B.map[g.base[l + 1] + ((ncode << D) | (uint32_t)ci)];
@@ -303,7 +304,7 @@ __device__ __forceinline__ void stream_axis(const Geo& g, const MeshDev& B,
       continue;
     }
 #pragma unroll
-    for (int kk = 0; kk < (D == 2 ? 9 : 3); ++kk) sv[kk] = mr_resolve<S>(g, B, LFin, st[kk]);
+    for (int kk = 0; kk < NS; ++kk) sv[kk] = mr_resolve<S>(g, B, LFin, st[kk]);
     crit_axis_terms<Sc, F>(g, W, l, a, k, side, per, sv, cv, scale, tmp);
 #pragma unroll
     for (int p = 0; p < Q; ++p)
@@ -416,7 +417,7 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
       has[w] = win_valid(ent[w]);
       vp[w] = mr_resolve<S>(g, B, LFin, has[w] ? ent[w] : 0);
     }
-    stream_axis<Sc, F>(g, B, LFin, W, l, a, x, y, vp, has, ent, fs, offv, out, scale, tmp, win);
+    stream_axis<Sc, F>(g, B, LFin, W, l, a, x, y, 0, vp, has, ent, fs, offv, out, scale, tmp, win);
   }
 
   // ---- the four single finest cells of each diagonal velocity
@@ -553,8 +554,9 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
       fs[p] = out[p];
     }
     if (do_stream) {
-      int x, y;
-      mr_decode(g, l, code, x, y);
+      int xc[3] = {0, 0, 0};
+      mr_decode_d<D>(g, l, code, xc);
+      const int x = xc[0], y = xc[1], z = xc[2];
       const C scale = (C)__longlong_as_double((long long)(1023 + l - g.J) << 52);  // 2^{l-J}, exact
       if constexpr (Sc::DIAG) {
         __shared__ int32_t win[25][MR_WIN_TPB];
@@ -568,16 +570,17 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
             const int off = w < 2 ? w - 2 : w - 1;  // -2, -1, +1, +2 along a
-            int nx = x + (a == 0 ? off : 0), ny = y + (a == 1 ? off : 0);
-            has[w] = mr_nbr_mesh(g, l, nx, ny);
-            ent[w] = has[w] ? B.map[g.base[l] + mr_encode(g, l, nx, ny)] : MR_MAP_NONE;
+            int nb[3] = {x, y, z};
+            nb[a] += off;
+            has[w] = mr_nbr_mesh_d<D>(g, l, nb);
+            ent[w] = has[w] ? B.map[g.base[l] + mr_encode_d<D>(g, l, nb)] : MR_MAP_NONE;
             if (has[w] && ent[w] == MR_MAP_NONE) {
               mr_set_err(B.cnt, MR_DERR_INTERNAL);
               has[w] = false;
             }
             vp[w] = mr_resolve<S>(g, B, LFin, has[w] ? ent[w] : 0);
           }
-          stream_axis<Sc, F>(g, B, LFin, W, l, a, x, y, vp, has, ent, fs, offv, out, scale, tmp, nullptr);
+          stream_axis<Sc, F>(g, B, LFin, W, l, a, x, y, z, vp, has, ent, fs, offv, out, scale, tmp, nullptr);
         }
       }
     }
@@ -613,11 +616,11 @@ __global__ void __launch_bounds__(256) k_init_eq(Geo g, MeshDev B, const double*
   using S = typename FormT<F>::S;
   S* LF = (S*)LF_;
   const int n = B.cnt->total[MR_CLS_LEAF];
-  const long long NJ = (long long)g.n[g.J][0] * (Sc::D == 2 ? g.n[g.J][1] : 1);
+  const long long NJ = (long long)g.n[g.J][0] * g.n[g.J][1] * g.n[g.J][2];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int x, y;
-    mr_decode(g, g.J, B.code[MR_CLS_LEAF][i], x, y);
-    const long long r = (long long)y * g.n[g.J][0] + x;
+    int c[3] = {0, 0, 0};
+    mr_decode_d<Sc::D>(g, g.J, B.code[MR_CLS_LEAF][i], c);
+    const long long r = ((long long)c[2] * g.n[g.J][1] + c[1]) * g.n[g.J][0] + c[0];
     double u[4], f[Sc::Q];
     for (int k = 0; k < g.ncons; ++k) u[k] = cons[k * NJ + r];
     Sc::equilibrium(g, u, f);
@@ -670,15 +673,16 @@ template <int D, int F>
 __global__ void __launch_bounds__(256) k_project_dense(Geo g, MeshDev B, const void* __restrict__ LF, int level,
                                                        const double* __restrict__ prev, double* cur) {
   using S = typename FormT<F>::S;
-  const int nx = g.n[level][0], ny = D == 2 ? g.n[level][1] : 1;
-  const long long N = (long long)nx * ny;
-  const int pnx = level > g.Jmin ? g.n[level - 1][0] : 1;
-  const long long PN = level > g.Jmin ? (long long)pnx * (D == 2 ? g.n[level - 1][1] : 1) : 1;
+  constexpr int NS = Pow3<D>::value;
+  const int n0 = g.n[level][0], n1 = g.n[level][1];
+  const long long N = (long long)n0 * n1 * g.n[level][2];
+  const int p0 = level > g.Jmin ? g.n[level - 1][0] : 1, p1 = level > g.Jmin ? g.n[level - 1][1] : 1;
+  const long long PN = level > g.Jmin ? (long long)p0 * p1 * g.n[level - 1][2] : 1;
   const double cs = (double)g.cross_sign;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
        r += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(r % nx), y = (int)(r / nx);
-    const int32_t e = B.map[g.base[level] + mr_encode(g, level, x, y)];
+    const int c[3] = {(int)(r % n0), (int)((r / n0) % n1), (int)(r / ((long long)n0 * n1))};
+    const int32_t e = B.map[g.base[level] + mr_encode_d<D>(g, level, c)];
     if (e != MR_MAP_NONE && (((uint32_t)e) >> 30) <= MR_CLS_INT) {
       const ValPtr<S> v = mr_resolve<S>(g, B, LF, e);
       for (int k = 0; k < g.ncons; ++k) {
@@ -688,17 +692,20 @@ __global__ void __launch_bounds__(256) k_project_dense(Geo g, MeshDev B, const v
         cur[k * N + r] = acc;
       }
     } else if (level > g.Jmin) {
-      const int px = x >> 1, py = y >> 1;
-      const int ci = (x & 1) | (D == 2 ? ((y & 1) << 1) : 0);
+      int ci = 0;
+      for (int a = 0; a < D; ++a) ci |= (c[a] & 1) << a;
       for (int k = 0; k < g.ncons; ++k) {
-        double v[9];
-        for (int b = 0; b < (D == 2 ? 3 : 1); ++b)
-          for (int a2 = 0; a2 < 3; ++a2) {
-            int sx = px + a2 - 1, sy = D == 2 ? py + b - 1 : 0;
-            mr_nbr_stencil(g, level - 1, sx, sy);
-            v[b * 3 + a2] = prev[k * PN + (long long)sy * pnx + sx];
-          }
-        cur[k * N + r] = mr_predict_fast<D>(v, ci, cs);
+        double v[NS];
+        for (int q = 0; q < NS; ++q) {
+          int s[3] = {(c[0] >> 1) + q % 3 - 1, D >= 2 ? (c[1] >> 1) + (q / 3) % 3 - 1 : 0,
+                      D == 3 ? (c[2] >> 1) + q / 9 - 1 : 0};
+          mr_nbr_stencil_d<D>(g, level - 1, s);
+          v[q] = prev[k * PN + ((long long)s[2] * p1 + s[1]) * p0 + s[0]];
+        }
+        if constexpr (D == 3)
+          cur[k * N + r] = predict_c<3, double>(v, ci, cs);
+        else
+          cur[k * N + r] = mr_predict_fast<D>(v, ci, cs);
       }
     } else {
       mr_set_err(B.cnt, MR_DERR_INTERNAL);
@@ -774,6 +781,7 @@ void mr_launch_remesh_copy(const Group& G, int cur, cudaStream_t st) {
     case 3: MR_FORMS2(launch_remesh_t, 3, G, cur, st); break;
     case 9: MR_FORMS2(launch_remesh_t, 9, G, cur, st); break;
     case 16: MR_FORMS2(launch_remesh_t, 16, G, cur, st); break;
+    case 6: MR_FORMS2(launch_remesh_t, 6, G, cur, st); break;
   }
 }
 
@@ -783,6 +791,7 @@ void mr_launch_predict_level(const Group& G, int dst, int kl, cudaStream_t st) {
     case 103: MR_FORMS3(launch_predict_t, 1, 3, G, dst, kl, st); break;
     case 209: MR_FORMS3(launch_predict_t, 2, 9, G, dst, kl, st); break;
     case 216: MR_FORMS3(launch_predict_t, 2, 16, G, dst, kl, st); break;
+    case 306: MR_FORMS3(launch_predict_t, 3, 6, G, dst, kl, st); break;
   }
 }
 
@@ -793,6 +802,7 @@ void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_col
     case 2: MR_FORMS2(launch_stream_t, 2, G, dst, do_stream, do_collide, st); break;
     case 3: MR_FORMS2(launch_stream_t, 3, G, dst, do_stream, do_collide, st); break;
     case 4: MR_FORMS2(launch_stream_t, 4, G, dst, do_stream, do_collide, st); break;
+    case 5: MR_FORMS2(launch_stream_t, 5, G, dst, do_stream, do_collide, st); break;
   }
 }
 
@@ -804,6 +814,7 @@ void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, void*
     case 2: MR_FORMS2(launch_init_t, 2, g, B, cons, LF, st, grid); break;
     case 3: MR_FORMS2(launch_init_t, 3, g, B, cons, LF, st, grid); break;
     case 4: MR_FORMS2(launch_init_t, 4, g, B, cons, LF, st, grid); break;
+    case 5: MR_FORMS2(launch_init_t, 5, g, B, cons, LF, st, grid); break;
   }
 }
 
@@ -839,8 +850,10 @@ void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int
   const Geo& G = g;
   if (g.d == 1) {
     MR_FORMS2(launch_dense_t, 1, g, B, LF, level, prev, cur, st, grid);
-  } else {
+  } else if (g.d == 2) {
     MR_FORMS2(launch_dense_t, 2, g, B, LF, level, prev, cur, st, grid);
+  } else {
+    MR_FORMS2(launch_dense_t, 3, g, B, LF, level, prev, cur, st, grid);
   }
 }
 
