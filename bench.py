@@ -61,6 +61,8 @@ def _args():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--max-level", type=int, default=10)
     p.add_argument("--e2e-steps", type=int, default=30)
+    p.add_argument("--d3-steps", type=int, default=100,
+                   help="steps timed on the 3D ball advection (D3Q6, 256^3 finest cells); 0 skips the leg")
     p.add_argument("--exact-steps", type=int, default=200,
                    help="steps timed with the original adaptive collision (FP64); 0 skips the leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -405,6 +407,35 @@ def run_ours(args):
                          "then averaged onto the leaves (Eq. sourceoferror); timed like the other forms"}
         s3.close()
 
+    # the 3D test of Sec. 7.3: D3Q6 advection of a ball, J = 8 (256^3), eps = 1e-3, mu_bar = 2
+    d3 = None
+    if args.d3_steps > 0:
+        from paper_2103_02903_gb300 import workloads
+        from paper_2103_02903_gb300.binding import Solver as _S3
+        cfg3, u3 = workloads.advection_3d(seed=args.seed, max_level=8)
+        d3 = {"workload": "d3q6_ball_advection_J8", "finest_cells": 256 ** 3, "eps": cfg3["eps"],
+              "mu_bar": cfg3["mu_bar"], "steps": args.d3_steps, "unit": UNIT}
+        for fm in ("fp16", "fp64"):
+            s3 = _S3(dict(cfg3, precision=fm), stream=stream.cuda_stream)
+            s3.init(u3)
+            s3.step(args.warmup)
+            s3.synchronize()
+            e3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.d3_steps)]
+            c0, _ = s3.counters()
+            for k in range(args.d3_steps):
+                flush.fill_(k & 0xFF)
+                e3[k][0].record(stream)
+                s3.step(1)
+                e3[k][1].record(stream)
+            torch.cuda.synchronize()
+            c1, _ = s3.counters()
+            ms3 = sum(a.elapsed_time(b) for a, b in e3) / args.d3_steps
+            _, mesh_or3, _ = s3.stats()
+            d3[fm] = {"value": (c1 - c0) / (ms3 * args.d3_steps / 1e3), "ms_per_step": ms3,
+                      "leaves_per_step_avg": (c1 - c0) / args.d3_steps, "occupancy_final": mesh_or3}
+            s3.close()
+
     serving = run_serving(args, stream, flush, local) if args.serving_n > 0 else None
 
     # whole-job aggregate: updates summed over ranks, time = max over ranks
@@ -518,6 +549,8 @@ def run_ours(args):
                                      "bf16 storage <= 2e-2")
         if exact is not None:
             line["exact_collision"] = exact
+        if d3 is not None:
+            line["d3q6_3d"] = d3
         if serving is not None:
             line["batched"] = serving
         print(json.dumps(line), flush=True)
