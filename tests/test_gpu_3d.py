@@ -131,3 +131,50 @@ def test_refusals():
     with pytest.raises(MrError):
         s.adjoint(u, 2, 1)
     s.close()
+
+
+def test_batch_of_3d_instances_equals_each_alone():
+    """3D instances (several finest levels, both forms) in one batch: every
+    instance ends bit for bit where it ends stepped alone."""
+    from paper_2103_02903_gb300.binding import Batch
+    cases = []
+    for i, (J, form) in enumerate([(4, "fp64"), (5, "fp64"), (5, "fp16"), (4, "fp16")]):
+        cfg, u = W.advection_3d(seed=10 + i, max_level=J)
+        cfg["precision"] = form
+        cases.append((cfg, u))
+    b = Batch([c for c, _ in cases])
+    for s, (c, u) in zip(b.instances, cases):
+        s.init(u)
+    b.step(5)
+    b.synchronize()
+    for i, (s, (c, u)) in enumerate(zip(b.instances, cases)):
+        alone = _solver(c)
+        alone.init(u)
+        alone.step(5)
+        k1, l1, f1 = s.get_leaves()
+        k2, l2, f2 = alone.get_leaves()
+        assert np.array_equal(l1, l2) and np.array_equal(k1, k2), "instance %d: leaf sets differ" % i
+        assert np.array_equal(f1, f2), "instance %d: populations differ" % i
+        alone.close()
+    b.close()
+
+
+def test_capacity_and_input_errors():
+    from paper_2103_02903_gb300.binding import MrError, encode_keys3
+    cfg, u = W.advection_3d(seed=7, max_level=5)
+    s = _solver(dict(cfg, leaf_capacity=200))
+    with pytest.raises(MrError) as ei:  # the initial full mesh needs 32^3 leaves
+        s.init(u)
+        s.synchronize()
+    assert ei.value.status == 4  # MR_ECAPACITY, reported at the next synchronising call
+    s.close()
+    s = _solver(cfg)
+    s.init(u)
+    keys, lev, f = s.get_leaves()
+    bad = keys.copy()
+    bad[0] = bad[1]  # two leaves on one cell: not a partition
+    with pytest.raises(MrError):
+        s.set_leaves(bad, lev, f)
+    x = np.array([0, 1]), np.array([0, 0]), np.array([0, 0])
+    assert list(encode_keys3(cfg, np.array([5, 5]), *x)) == [0, 1]
+    s.close()
