@@ -215,6 +215,43 @@ struct MortonBox {
   __device__ __forceinline__ uint32_t code(int a, int b) const { return ((rx[a] + ry[b]) << sh) | px[a] | py[b]; }
 };
 
+// d = 3 form of MortonBox: the code of (X, Y, Z) is the sum of an X part, a
+// Y part and a Z part (root X >> l + roots_x (Y >> l + roots_y (Z >> l))
+// shifted by 3l, or-ed with the three 3-way interleaves), so a box needs
+// 3 (2R+1) interleaves.  Same wrap / outside / `half` rules as MortonBox.
+template <int R>
+struct MortonBox3 {
+  static constexpr int W = 2 * R + 1;
+  uint32_t p[3][W], r[3][W];
+  bool in[3][W];
+  int sh;
+  __device__ __forceinline__ void init(const Geo& g, int l, const int* c, bool half = false) {
+    const int lc = half ? l - 1 : l;
+    const uint32_t mask = (1u << lc) - 1u;
+    const uint32_t rs[3] = {1u, (uint32_t)g.roots[0], (uint32_t)g.roots[0] * (uint32_t)g.roots[1]};
+    sh = 3 * lc;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int o = 0; o < W; ++o) {
+        int X = c[a] + o - R;
+        const int n = g.n[l][a];
+        in[a][o] = X >= 0 && X < n;
+        if (!in[a][o] && g.periodic[a]) {
+          X = mr_wrap(X, n);
+          in[a][o] = true;
+        }
+        if (half) X >>= 1;
+        p[a][o] = mr_spread3((uint32_t)X & mask) << a;
+        r[a][o] = rs[a] * ((uint32_t)X >> lc);
+      }
+  }
+  __device__ __forceinline__ bool inside(int i, int j, int k) const { return in[0][i] && in[1][j] && in[2][k]; }
+  __device__ __forceinline__ uint32_t code(int i, int j, int k) const {
+    return ((r[0][i] + r[1][j] + r[2][k]) << sh) | p[0][i] | p[1][j] | p[2][k];
+  }
+};
+
 // Entry e (x fastest) of the 3^D prediction stencil of cell (x, y) on level
 // l, with the stencil's boundary rule (periodic wrap, else the nearest cell).
 template <int D>

@@ -119,11 +119,12 @@ __device__ __forceinline__ uint32_t grade_need(const Geo& g, const uint8_t* flag
 __device__ __forceinline__ uint32_t grade_need3(const Geo& g, const uint8_t* flags, int L, const int* c) {
   uint32_t m = 0;
   const uint8_t* fl = flags + g.base[L - 1];
+  MortonBox3<1> bx;
+  bx.init(g, L, c, true);
+#pragma unroll
   for (int k = 0; k < 27; ++k) {
-    int nb[3] = {c[0] + k % 3 - 1, c[1] + (k / 3) % 3 - 1, c[2] + k / 9 - 1};
-    if (!mr_nbr_mesh_d<3>(g, L, nb)) continue;
-    for (int a = 0; a < 3; ++a) nb[a] >>= 1;
-    if (!(fl[mr_encode_d<3>(g, L - 1, nb)] & (MR_F_H | MR_F_G))) m |= 1u << k;
+    const int i = k % 3, j = (k / 3) % 3, kk = k / 9;
+    if (bx.inside(i, j, kk) && !(fl[bx.code(i, j, kk)] & (MR_F_H | MR_F_G))) m |= 1u << k;
   }
   return m;
 }
@@ -270,10 +271,12 @@ __device__ __forceinline__ void ghost_window_cell(bool block, int w, int x, int 
 __device__ __forceinline__ uint32_t ghost_need3(const Geo& g, const uint8_t* cls, int L, const int* c) {
   uint32_t m = 0;
   const uint8_t* cl = cls + g.base[L];
+  MortonBox3<1> bx;
+  bx.init(g, L, c);
+#pragma unroll
   for (int k = 0; k < 27; ++k) {
-    int nb[3] = {c[0] + k % 3 - 1, c[1] + (k / 3) % 3 - 1, c[2] + k / 9 - 1};
-    if (!mr_nbr_mesh_d<3>(g, L, nb)) continue;
-    if (!(cl[mr_encode_d<3>(g, L, nb)] & (3u | MR_C_GHOST))) m |= 1u << k;
+    const int i = k % 3, j = (k / 3) % 3, kk = k / 9;
+    if (bx.inside(i, j, kk) && !(cl[bx.code(i, j, kk)] & (3u | MR_C_GHOST))) m |= 1u << k;
   }
   return m;
 }
@@ -281,13 +284,27 @@ __device__ __forceinline__ uint32_t ghost_need3(const Geo& g, const uint8_t* cls
 __device__ void mark_ghosts3(const Geo& g, uint8_t* cls, int l, uint32_t code) {
   int x[3];
   mr_decode_d<3>(g, l, code, x);
-  for (int w = 0; w < 12; ++w) {
+  uint32_t need = 0;
+  {
+    // the window's classes first, as independent loads
+    MortonBox3<2> bx;
+    bx.init(g, l, x);
+    const uint8_t* cl = cls + g.base[l];
+#pragma unroll
+    for (int w = 0; w < 12; ++w) {
+      const int axis = w >> 2, k = w & 3, o = k < 2 ? k : k + 1;  // offsets -2, -1, +1, +2
+      const int i = axis == 0 ? o : 2, j = axis == 1 ? o : 2, kk = axis == 2 ? o : 2;
+      if (bx.inside(i, j, kk) && !(cl[bx.code(i, j, kk)] & (3u | MR_C_GHOST))) need |= 1u << w;
+    }
+  }
+  while (need) {
+    const int w = __ffs(need) - 1;
+    need &= need - 1u;
     const int axis = w >> 2, k = w & 3;
     int nb[3] = {x[0], x[1], x[2]};
     nb[axis] += k < 2 ? k - 2 : k - 1;
-    if (!mr_nbr_mesh_d<3>(g, l, nb)) continue;
+    mr_nbr_mesh_d<3>(g, l, nb);  // inside: only such cells enter the mask
     const uint32_t gw = g.base[l] + mr_encode_d<3>(g, l, nb);
-    if (cls[gw] & (3u | MR_C_GHOST)) continue;
     const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
     if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
     int sl[MR_MAXL], sc[MR_MAXL][3];
