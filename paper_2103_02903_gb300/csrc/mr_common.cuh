@@ -252,15 +252,6 @@ struct MortonBox3 {
   }
 };
 
-// Entry e (x fastest) of the 3^D prediction stencil of cell (x, y) on level
-// l, with the stencil's boundary rule (periodic wrap, else the nearest cell).
-template <int D>
-__device__ __forceinline__ int32_t mr_stencil_entry(const Geo& g, const MeshDev& M, int l, int x, int y, int e) {
-  int sx = x + (e % 3) - 1, sy = D == 2 ? y + (e / 3) - 1 : 0;
-  mr_nbr_stencil(g, l, sx, sy);
-  return M.map[g.base[l] + mr_encode(g, l, sx, sy)];
-}
-
 // ------------------------------------------------------------------ groups
 // A step kernel runs one phase for every instance of a group.  The phase's
 // work in instance b is count(b) passes of the block ("tiles"); the tiles of
@@ -356,29 +347,8 @@ __device__ __forceinline__ int mr_group_chunk(const int* __restrict__ chunk_pre,
   return lo;
 }
 
-// Canonical s = 1 prediction of child ci from a 3^D stencil (x fastest),
-// evaluated in the order written in Sec. 4.1 with no fused multiply-add:
-// the same bits as the CPU oracle on the same inputs.
-template <int D>
-__device__ __forceinline__ double mr_predict_canonical(const double* v, int ci, int cross_sign) {
-  const double sx = (ci & 1) ? -1.0 : 1.0;
-  if (D == 1) {
-    double qx = __dmul_rn(MR_C1, __dsub_rn(v[2], v[0]));
-    return __dadd_rn(v[1], __dmul_rn(sx, qx));
-  } else {
-    const double sy = (ci & 2) ? -1.0 : 1.0;
-    double qx = __dmul_rn(MR_C1, __dsub_rn(v[5], v[3]));
-    double qy = __dmul_rn(MR_C1, __dsub_rn(v[7], v[1]));
-    double q2 = __dmul_rn(MR_C1 * MR_C1, __dadd_rn(__dsub_rn(__dsub_rn(v[8], v[6]), v[2]), v[0]));
-    double t = v[4];
-    t = __dadd_rn(t, __dmul_rn(sx, qx));
-    t = __dadd_rn(t, __dmul_rn(sy, qy));
-    t = __dadd_rn(t, __dmul_rn((double)cross_sign * sx * sy, q2));
-    return t;
-  }
-}
-
-// All 2^D children of one stencil with the rounding of mr_predict_canonical:
+// All 2^D children of one stencil, each operation rounded as written (FP64,
+// no contraction; the oracle's order):
 // the products with the signs +-1 are exact, so they become the signs of the
 // additions (x + (-y) and x - y round alike), and the partial sums that two
 // children share are formed once.  out[ci], ci = x bit | y bit << 1.
