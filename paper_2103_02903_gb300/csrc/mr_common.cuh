@@ -333,6 +333,18 @@ __device__ __forceinline__ void mr_inst_prefetch(InstDev& si, int& have, const I
 
 // Dense kernels: instance and chunk of this block, from the group's chunk
 // prefix (one block per dense chunk of every instance).
+__device__ __forceinline__ int mr_group_chunk_of(const int* __restrict__ chunk_pre, int n, int t, int& chunk) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(chunk_pre + mid) <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  chunk = t - __ldg(chunk_pre + lo);
+  return lo;
+}
 __device__ __forceinline__ int mr_group_chunk(const int* __restrict__ chunk_pre, int n, int& chunk) {
   int lo = 0, hi = n - 1;
   const int t = (int)blockIdx.x;

@@ -431,22 +431,35 @@ __device__ __forceinline__ int cls_of(uint8_t c) {
   return -1;
 }
 
+// Grid-stride over the chunks of all instances (a few resident blocks per
+// SM instead of one short block per chunk); the next chunk's class bytes are
+// loaded before the current chunk's barriers.
 __global__ void __launch_bounds__(1024) k_count(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
-                                                int n) {
+                                                int n, int nchunks) {
   mr_grid_dep();
-  int chunk;
-  const int b = mr_group_chunk(chunk_pre, n, chunk);
-  const uint8_t* __restrict__ cls = IB[b].cls;
-  int* bc = IB[b].bcounts;
-  const uint32_t gi = (uint32_t)chunk * 1024u + threadIdx.x;
-  const int k = cls_of(cls[gi]);
-  const int nl = __syncthreads_count(k == MR_CLS_LEAF);
-  const int ni = __syncthreads_count(k == MR_CLS_INT);
-  const int ng = __syncthreads_count(k == MR_CLS_GHOST);
-  if (threadIdx.x == 0) {
-    bc[chunk * 3 + 0] = nl;
-    bc[chunk * 3 + 1] = ni;
-    bc[chunk * 3 + 2] = ng;
+  int chunk = 0, b = 0;
+  uint8_t v = 0;
+  if ((int)blockIdx.x < nchunks) {
+    b = mr_group_chunk_of(chunk_pre, n, blockIdx.x, chunk);
+    v = IB[b].cls[(uint32_t)chunk * 1024u + threadIdx.x];
+  }
+  for (int t = blockIdx.x; t < nchunks; t += gridDim.x) {
+    const int k = cls_of(v);
+    int* bc = IB[b].bcounts;
+    const int cur = chunk;
+    const int tn = t + gridDim.x;
+    if (tn < nchunks) {  // prefetch the next chunk
+      b = mr_group_chunk_of(chunk_pre, n, tn, chunk);
+      v = IB[b].cls[(uint32_t)chunk * 1024u + threadIdx.x];
+    }
+    const int nl = __syncthreads_count(k == MR_CLS_LEAF);
+    const int ni = __syncthreads_count(k == MR_CLS_INT);
+    const int ng = __syncthreads_count(k == MR_CLS_GHOST);
+    if (threadIdx.x == 0) {
+      bc[cur * 3 + 0] = nl;
+      bc[cur * 3 + 1] = ni;
+      bc[cur * 3 + 2] = ng;
+    }
   }
 }
 
@@ -517,51 +530,63 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict_
 }
 
 __global__ void __launch_bounds__(1024) k_scatter(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
-                                                  int n, int dst) {
+                                                  int n, int dst, int nchunks) {
   __shared__ int wcount[32][3];
   __shared__ int woff[32][3];
   __shared__ InstDev si;
-  int chunk, have = -1;
-  mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, n);
+  __syncthreads();  // publishes the prefetched descriptor (mr_inst_use below skips a held one)
   mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
-  const Geo& g = si.g;
-  uint8_t* cls = si.cls;
-  uint8_t* flags = si.flags;
-  const int* __restrict__ bc = si.bcounts;
-  const MeshDev& B = si.mesh[dst];
-  const uint32_t gi = (uint32_t)chunk * 1024u + threadIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int k = cls_of(cls[gi]);
   const uint32_t lt = (1u << lane) - 1u;
-  int pre = 0;
+  for (int t = blockIdx.x; t < nchunks; t += gridDim.x) {  // grid-stride over the chunks
+    int chunk;
+    mr_inst_use(si, have, IB, mr_group_chunk_of(chunk_pre, n, t, chunk));
+    const Geo& g = si.g;
+    uint8_t* cls = si.cls;
+    uint8_t* flags = si.flags;
+    const int* __restrict__ bc = si.bcounts;
+    const MeshDev& B = si.mesh[dst];
+    const uint32_t gi = (uint32_t)chunk * 1024u + threadIdx.x;
+    const int k = cls_of(cls[gi]);
+    int pre = 0;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const uint32_t bal = __ballot_sync(0xffffffffu, k == c);
-    if (k == c) pre = __popc(bal & lt);
-    if (lane == 0) wcount[wid][c] = __popc(bal);
-  }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    int s = 0;
-    for (int w = 0; w < 32; ++w) {
-      woff[w][threadIdx.x] = s;
-      s += wcount[w][threadIdx.x];
+    for (int c = 0; c < 3; ++c) {
+      const uint32_t bal = __ballot_sync(0xffffffffu, k == c);
+      if (k == c) pre = __popc(bal & lt);
+      if (lane == 0) wcount[wid][c] = __popc(bal);
     }
-  }
-  __syncthreads();
-  int32_t entry = MR_MAP_NONE;
-  if (k >= 0) {
-    const int pos = bc[chunk * 3 + k] + woff[wid][k] + pre;
-    if (pos < g.cap[k]) {
-      const int l = mr_level_of(g, gi);
-      B.code[k][pos] = gi - g.base[l];
-      B.lvl[k][pos] = (uint8_t)l;
-      entry = (int32_t)(((uint32_t)k << 30) | (uint32_t)pos);
+    __syncthreads();
+    if (wid == 0) {  // exclusive scan of the 32 warp counts, one class per pass
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int v = wcount[lane][c];
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        woff[lane][c] = x - v;
+      }
     }
+    __syncthreads();
+    int32_t entry = MR_MAP_NONE;
+    if (k >= 0) {
+      const int pos = bc[chunk * 3 + k] + woff[wid][k] + pre;
+      if (pos < g.cap[k]) {
+        const int l = mr_level_of(g, gi);
+        B.code[k][pos] = gi - g.base[l];
+        B.lvl[k][pos] = (uint8_t)l;
+        entry = (int32_t)(((uint32_t)k << 30) | (uint32_t)pos);
+      }
+    }
+    B.map[gi] = entry;
+    cls[gi] = 0;
+    flags[gi] = 0;
+    __syncthreads();  // wcount / woff are reused by the next chunk
   }
-  B.map[gi] = entry;
-  cls[gi] = 0;
-  flags[gi] = 0;
 }
 
 // ---------------------------------------------------------------- input leaves
@@ -648,9 +673,10 @@ void mr_launch_mark_ghosts(const Group& G, cudaStream_t st) {
   MR_DISPATCH_D_PDL(k_mark_ghosts, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
 }
 void mr_launch_compact(const Group& G, int dst, cudaStream_t st) {
-  mr_launch_pdl(k_count, G.chunks, 1024, 0, st, G.dev, G.chunk_pre, G.n);
+  const int grid = std::min(G.chunks, 2 * G.nsm);  // two resident 1024-thread blocks per SM
+  mr_launch_pdl(k_count, grid, 1024, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
   mr_launch_pdl(k_scan_blocks, G.n, 1024, 0, st, G.dev, dst);
-  mr_launch_pdl(k_scatter, G.chunks, 1024, 0, st, G.dev, G.chunk_pre, G.n, dst);
+  mr_launch_pdl(k_scatter, grid, 1024, 0, st, G.dev, G.chunk_pre, G.n, dst, G.chunks);
 }
 void mr_launch_leaves_in(const Geo& g, long long n, const unsigned long long* keys,
                          const signed char* levels, int32_t* inidx, uint8_t* cls, MeshCounts* cnt,
