@@ -420,7 +420,7 @@ void run_adapt(Exec& x, const Group& G, int cur) {
 
 void run_stream(Exec& x, const Group& G, int dst, int do_stream, int do_collide) {
   prof_begin(x, PG_STREAM);
-  mr_launch_stream_collide(G, dst, do_stream, do_collide, x.st);
+  mr_launch_stream_collide(G, dst, do_stream, do_collide, x.st, 1);  // counts the step
   prof_end(x, PG_STREAM);
   x.launches += 1;
 }
@@ -430,8 +430,6 @@ void run_step(Exec& x, const Group& G, int cur) {
   run_adapt(x, G, cur);
   run_stream(x, G, 1 - cur, 1, G.exact ? 0 : 1);
   if (G.exact) x.launches += mr_launch_exact_collision(G, 1 - cur, G.exact, G.exact_nd, x.st);
-  mr_launch_count_updates(G, 1 - cur, x.st);
-  x.launches += 1;
 }
 
 void drop_graphs(Exec& x) {

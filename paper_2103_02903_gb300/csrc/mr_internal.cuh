@@ -362,8 +362,9 @@ void mr_launch_mark_ghosts(const Group& G, cudaStream_t st);
 void mr_launch_compact(const Group& G, int dst, cudaStream_t st);  // count + scan + scatter into mesh dst
 void mr_launch_remesh_copy(const Group& G, int cur, cudaStream_t st);
 void mr_launch_predict_level(const Group& G, int dst, int k, cudaStream_t st);  // level J_min + k
-void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st);
-void mr_launch_count_updates(const Group& G, int dst, cudaStream_t st);
+// count = 1: also add the step to the instances' counters (once per step)
+void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st,
+                              int count = 0);
 // Original adaptive collision of the post-transport leaves of mesh dst
 // (mr_exact.cu); returns the number of launches.
 int mr_launch_exact_collision(const Group& G, int dst, double* Fd, long long nd, cudaStream_t st);

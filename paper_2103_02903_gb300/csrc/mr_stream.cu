@@ -511,7 +511,7 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
 // ------------------------------------------------------------------ transport + collision
 template <int SC, int F>
 __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __restrict__ IB, int ngrp, int dst,
-                                                        int do_stream, int do_collide) {
+                                                        int do_stream, int do_collide, int count) {
   using Sc = Scheme<SC>;
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
@@ -540,6 +540,11 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
     S* __restrict__ LFout = (S*)si.fstate;
     const C* __restrict__ W = mr_wtab<C>(si);
     const int i = (tt - pre[b]) * MR_WIN_TPB + threadIdx.x;
+    if (count && tt == pre[b] && threadIdx.x == 0) {
+      // the step's counters (leaf updates, steps), once per instance
+      B.cnt->leaf_updates += B.cnt->total[MR_CLS_LEAF];
+      B.cnt->steps += 1;
+    }
     if (i >= B.cnt->total[MR_CLS_LEAF]) continue;
     const int l = B.lvl[MR_CLS_LEAF][i];
     const uint32_t code = B.code[MR_CLS_LEAF][i];
@@ -713,15 +718,6 @@ __global__ void __launch_bounds__(256) k_project_dense(Geo g, MeshDev B, const v
   }
 }
 
-__global__ void k_count_updates(const InstDev* __restrict__ IB, int ngrp, int dst) {
-  mr_grid_dep();
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= ngrp) return;
-  MeshCounts* cnt = IB[b].mesh[dst].cnt;
-  cnt->leaf_updates += cnt->total[MR_CLS_LEAF];
-  cnt->steps += 1;
-}
-
 template <int Q, int F>
 void launch_remesh_t(const Group& G, int cur, cudaStream_t st) {
   mr_launch_pdl(k_remesh_copy<Q, F>, mr_tile_grid(G, G.capL + G.capI, 32, 8), dim3(32, PopRows<Q>::value),
@@ -734,9 +730,9 @@ void launch_predict_t(const Group& G, int dst, int kl, cudaStream_t st) {
                 mr_pre_bytes(G), st, G.dev, G.n, dst, kl);
 }
 template <int SC, int F>
-void launch_stream_t(const Group& G, int dst, int ds, int dc, cudaStream_t st) {
+void launch_stream_t(const Group& G, int dst, int ds, int dc, int count, cudaStream_t st) {
   mr_launch_pdl(k_stream_collide<SC, F>, mr_tile_grid(G, G.capL, MR_WIN_TPB, 8), MR_WIN_TPB, mr_pre_bytes(G), st, G.dev,
-                G.n, dst, ds, dc);
+                G.n, dst, ds, dc, count);
 }
 template <int SC, int F>
 void launch_init_t(const Geo& g, const MeshDev& B, const double* cons, void* LF, cudaStream_t st, int grid) {
@@ -795,14 +791,15 @@ void mr_launch_predict_level(const Group& G, int dst, int kl, cudaStream_t st) {
   }
 }
 
-void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st) {
+void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st,
+                              int count) {
   switch (G.scheme) {
-    case 0: MR_FORMS2(launch_stream_t, 0, G, dst, do_stream, do_collide, st); break;
-    case 1: MR_FORMS2(launch_stream_t, 1, G, dst, do_stream, do_collide, st); break;
-    case 2: MR_FORMS2(launch_stream_t, 2, G, dst, do_stream, do_collide, st); break;
-    case 3: MR_FORMS2(launch_stream_t, 3, G, dst, do_stream, do_collide, st); break;
-    case 4: MR_FORMS2(launch_stream_t, 4, G, dst, do_stream, do_collide, st); break;
-    case 5: MR_FORMS2(launch_stream_t, 5, G, dst, do_stream, do_collide, st); break;
+    case 0: MR_FORMS2(launch_stream_t, 0, G, dst, do_stream, do_collide, count, st); break;
+    case 1: MR_FORMS2(launch_stream_t, 1, G, dst, do_stream, do_collide, count, st); break;
+    case 2: MR_FORMS2(launch_stream_t, 2, G, dst, do_stream, do_collide, count, st); break;
+    case 3: MR_FORMS2(launch_stream_t, 3, G, dst, do_stream, do_collide, count, st); break;
+    case 4: MR_FORMS2(launch_stream_t, 4, G, dst, do_stream, do_collide, count, st); break;
+    case 5: MR_FORMS2(launch_stream_t, 5, G, dst, do_stream, do_collide, count, st); break;
   }
 }
 
@@ -857,6 +854,3 @@ void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int
   }
 }
 
-void mr_launch_count_updates(const Group& G, int dst, cudaStream_t st) {
-  mr_launch_pdl(k_count_updates, (G.n + 127) / 128, 128, 0, st, G.dev, G.n, dst);
-}
