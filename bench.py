@@ -457,15 +457,8 @@ def run_ours(args):
     serving = run_serving(args, stream, flush, local) if args.serving_n > 0 else None
 
     # whole-job aggregate: updates summed over ranks, time = max over ranks
-    if dist is not None:
-        t = torch.tensor([float(leaf_updates), total_s], dtype=torch.float64, device="cuda")
-        s = t.clone()
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        m = t.clone()
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        leaf_updates_all, total_s_max = s[0].item(), m[1].item()
-    else:
-        leaf_updates_all, total_s_max = float(leaf_updates), total_s
+    from paper_2103_02903_gb300.replicas import aggregate
+    leaf_updates_all, total_s_max = aggregate(leaf_updates, total_s, device="cuda")
     value = leaf_updates_all / total_s_max
     per_step_leaves = leaf_updates / args.steps
 
@@ -526,7 +519,8 @@ def run_ours(args):
             e2e_leaves += nn
         barrier()
         t_e2e = time.perf_counter() - t0
-        e2e = {"value": e2e_leaves / t_e2e * world, "unit": UNIT,
+        e2e_all, t_e2e_max = aggregate(e2e_leaves, t_e2e, device="cuda")
+        e2e = {"value": e2e_all / t_e2e_max, "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
                "steps": args.e2e_steps,
                "call": "mr_lbm_set_leaves(host) + mr_lbm_step(1) + mr_lbm_get_leaves(host), pinned buffers"}
