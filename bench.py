@@ -70,6 +70,8 @@ def _args():
                    help="steps timed with the original adaptive collision (FP64); 0 skips the leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--cpu-all-cores", type=int, default=1,
+                   help="also time the oracle sample on every host core at once (1) or not (0)")
     p.add_argument("--profile-groups", action="store_true",
                    help="also time every kernel group once (extra steps, not part of value)")
     p.add_argument("--form", default="fp16", choices=["fp64", "fp32", "fp16", "bf16"],
@@ -175,6 +177,22 @@ def _oracle_sample(cfg, u, seconds, max_steps=None):
         leaves += o.num_leaves()
         steps += 1
     return leaves, steps, t
+
+
+def _oracle_replica(job):
+    cfg, u, seconds = job
+    return _oracle_sample(cfg, u, seconds)
+
+
+def _oracle_sample_all_cores(cfg, u, seconds, nproc):
+    """The same sample on every host core: one process per core (spawned, so
+    none inherits the GPU context), each stepping its own copy of the workload
+    from its initial condition.  Returns the summed leaf updates, the time of
+    the slowest process and the steps of each."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(nproc) as pool:
+        res = pool.map(_oracle_replica, [(cfg, u, seconds)] * nproc)
+    return sum(r[0] for r in res), max(r[2] for r in res), [r[1] for r in res]
 
 
 def run_reference(args):
@@ -526,12 +544,20 @@ def run_ours(args):
                "call": "mr_lbm_set_leaves(host) + mr_lbm_step(1) + mr_lbm_get_leaves(host), pinned buffers"}
 
     per_level, mesh_or, mem_or = solver.stats()
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         lv, st, t = _oracle_sample(cfg, u, args.cpu_seconds)
         cpu = {"value": lv / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "oracle (single thread) steps 1..%d of the same workload from its initial "
                          "condition, %.1f s" % (st, t)}
+        if args.cpu_all_cores:
+            nproc = os.cpu_count() or 1
+            lv_all, t_all, st_all = _oracle_sample_all_cores(cfg, u, args.cpu_seconds, nproc)
+            cpu_all = {"value": lv_all / t_all, "unit": UNIT, "cores": nproc, "kind": "oracle",
+                       "sample": "%d oracle processes at once, one per host core (nproc %d), each stepping "
+                                 "its own copy of the same workload from its initial condition for %.0f s "
+                                 "(%d..%d steps); leaf updates summed over the processes / time of the "
+                                 "slowest" % (nproc, nproc, args.cpu_seconds, min(st_all), max(st_all))}
 
     if rank == 0:
         line = {
@@ -547,7 +573,8 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "leaves_per_step_avg": per_step_leaves, "mesh_or_final": mesh_or, "mem_or_final": mem_or,
             "wall_s_timed_region": t_wall,
-            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
             "clocks": clocks,
         }
         if groups is not None:
