@@ -463,9 +463,13 @@ __global__ void __launch_bounds__(1024) k_count(const InstDev* __restrict__ IB, 
   }
 }
 
+// Exclusive scan of the chunk counts of one instance (one block per
+// instance), the three classes together: each thread takes MR_SCAN_VPT
+// consecutive chunks, so that a pass covers 1024 * MR_SCAN_VPT chunks.
+#define MR_SCAN_VPT 8
 __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict__ IB, int dst) {
-  __shared__ int warp_sums[32];
-  __shared__ int carry;
+  __shared__ int warp_sums[32][3];
+  __shared__ int carry[3];
   __shared__ InstDev si;
   int have = -1;
   mr_inst_use(si, have, IB, blockIdx.x);
@@ -475,47 +479,65 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict_
   const int nblocks = (int)(g.base[g.J + 1] / MR_DENSE_ALIGN);
   MeshCounts* cnt = si.mesh[dst].cnt;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c = 0; c < 3; ++c) {
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < nblocks; b0 += 1024) {
-      const int b = b0 + threadIdx.x;
-      const int v = b < nblocks ? bc[b * 3 + c] : 0;
-      int x = v;
+  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nblocks; b0 += 1024 * MR_SCAN_VPT) {
+    const int first = b0 + threadIdx.x * MR_SCAN_VPT;
+    int v[MR_SCAN_VPT][3], x[3], tot[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < MR_SCAN_VPT; ++j)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        v[j][c] = first + j < nblocks ? bc[(first + j) * 3 + c] : 0;
+        tot[c] += v[j][c];
+      }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x[c] = tot[c];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        const int y = __shfl_up_sync(0xffffffffu, x[c], o);
+        if (lane >= o) x[c] += y;
       }
-      if (lane == 31) warp_sums[wid] = x;
-      __syncthreads();
-      if (wid == 0) {
-        int s = warp_sums[lane];
+      if (lane == 31) warp_sums[wid][c] = x[c];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        int t = warp_sums[lane][c];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          int y = __shfl_up_sync(0xffffffffu, s, o);
-          if (lane >= o) s += y;
+          const int y = __shfl_up_sync(0xffffffffu, t, o);
+          if (lane >= o) t += y;
         }
-        warp_sums[lane] = s;
+        warp_sums[lane][c] = t;
       }
-      __syncthreads();
-      const int excl = carry + (wid > 0 ? warp_sums[wid - 1] : 0) + x - v;
-      if (b < nblocks) bc[b * 3 + c] = excl;
-      __syncthreads();
-      if (threadIdx.x == 1023) carry = excl + v;
-      __syncthreads();
     }
-    if (threadIdx.x == 0) {
-      // counts are clamped to the capacity so that no later kernel can run
-      // past an array; the overflow itself is reported through err
-      cnt->total[c] = carry < g.cap[c] ? carry : g.cap[c];
-      if (carry > g.cap[c]) atomicOr(&cnt->err, MR_DERR_CAPACITY);
-    }
+    __syncthreads();
+    int run[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) run[c] = carry[c] + (wid > 0 ? warp_sums[wid - 1][c] : 0) + x[c] - tot[c];
+#pragma unroll
+    for (int j = 0; j < MR_SCAN_VPT; ++j)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (first + j < nblocks) bc[(first + j) * 3 + c] = run[c];
+        run[c] += v[j][c];
+      }
+    __syncthreads();  // every thread has read carry
+    if (threadIdx.x == 1023)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) carry[c] = run[c];
     __syncthreads();
   }
   // per-level offsets: every level starts on a block boundary
   if (threadIdx.x < 3) {
     const int c = threadIdx.x;
+    // counts are clamped to the capacity so that no later kernel can run
+    // past an array; the overflow itself is reported through err
+    cnt->total[c] = carry[c] < g.cap[c] ? carry[c] : g.cap[c];
+    if (carry[c] > g.cap[c]) atomicOr(&cnt->err, MR_DERR_CAPACITY);
     for (int l = 0; l <= MR_MAXL; ++l) {
       int v;
       if (l < g.Jmin)
