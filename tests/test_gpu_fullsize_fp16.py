@@ -90,6 +90,6 @@ def test_bench_configuration_full_size():
         gpu.step(n - gpu.counters()[1])
         keys, lev, f = gpu.get_leaves()
         assert np.isfinite(f).all()
-        x, y, _ = decode_keys(cfg, lev, keys)
+        x, y = decode_keys(cfg, lev, keys)[:2]
         check_mesh(cfg, lev, np.asarray(x, np.int64), np.asarray(y, np.int64))
     gpu.close()
