@@ -421,8 +421,9 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
 }
 
 // ---------------------------------------------------------------- compaction
-// Stream compaction of the dense classification, 1024 dense cells per block,
-// with ballot / popc prefixes inside each block and one scan over blocks.
+// Stream compaction of the dense classification: class counts per 1024-cell
+// chunk (k_count), one scan over the chunks of each instance (k_scan_blocks),
+// then every cell written at its position (k_scatter).
 __device__ __forceinline__ int cls_of(uint8_t c) {
   const uint32_t k = c & 3u;
   if (k == MR_C_LEAF) return MR_CLS_LEAF;
@@ -431,34 +432,47 @@ __device__ __forceinline__ int cls_of(uint8_t c) {
   return -1;
 }
 
-// Grid-stride over the chunks of all instances (a few resident blocks per
-// SM instead of one short block per chunk); the next chunk's class bytes are
-// loaded before the current chunk's barriers.
-__global__ void __launch_bounds__(1024) k_count(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
-                                                int n, int nchunks) {
+// One warp per 1024-cell chunk, grid-stride over the chunks of all
+// instances, no block barrier: lane L reads the class bytes of cells
+// 32L .. 32L+31 of the chunk (two 16-byte loads) and counts them four at a
+// time with per-byte compares; the three counts are summed over the warp.
+__device__ __forceinline__ void cls_count4(uint32_t w, int& nl, int& ni, int& ng) {
+  const uint32_t lo = w & 0x03030303u;
+  const uint32_t isL = __vcmpeq4(lo, 0x01010101u * MR_C_LEAF);  // 0xFF in every matching byte
+  const uint32_t isI = __vcmpeq4(lo, 0x01010101u * MR_C_INT);
+  const uint32_t isG = __vcmpne4(w & (0x01010101u * MR_C_GHOST), 0u) & ~isL & ~isI;
+  nl += __popc(isL) >> 3;
+  ni += __popc(isI) >> 3;
+  ng += __popc(isG) >> 3;
+}
+
+__global__ void __launch_bounds__(256) k_count(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
+                                               int n, int nchunks) {
   mr_grid_dep();
-  int chunk = 0, b = 0;
-  uint8_t v = 0;
-  if ((int)blockIdx.x < nchunks) {
-    b = mr_group_chunk_of(chunk_pre, n, blockIdx.x, chunk);
-    v = IB[b].cls[(uint32_t)chunk * 1024u + threadIdx.x];
-  }
-  for (int t = blockIdx.x; t < nchunks; t += gridDim.x) {
-    const int k = cls_of(v);
-    int* bc = IB[b].bcounts;
-    const int cur = chunk;
-    const int tn = t + gridDim.x;
-    if (tn < nchunks) {  // prefetch the next chunk
-      b = mr_group_chunk_of(chunk_pre, n, tn, chunk);
-      v = IB[b].cls[(uint32_t)chunk * 1024u + threadIdx.x];
-    }
-    const int nl = __syncthreads_count(k == MR_CLS_LEAF);
-    const int ni = __syncthreads_count(k == MR_CLS_INT);
-    const int ng = __syncthreads_count(k == MR_CLS_GHOST);
-    if (threadIdx.x == 0) {
-      bc[cur * 3 + 0] = nl;
-      bc[cur * 3 + 1] = ni;
-      bc[cur * 3 + 2] = ng;
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < nchunks; t += nw) {
+    int chunk;
+    const int b = mr_group_chunk_of(chunk_pre, n, t, chunk);
+    const uint4* src = (const uint4*)(IB[b].cls + (size_t)chunk * MR_DENSE_ALIGN) + 2 * lane;
+    const uint4 v0 = src[0], v1 = src[1];
+    int nl = 0, ni = 0, ng = 0;
+    cls_count4(v0.x, nl, ni, ng);
+    cls_count4(v0.y, nl, ni, ng);
+    cls_count4(v0.z, nl, ni, ng);
+    cls_count4(v0.w, nl, ni, ng);
+    cls_count4(v1.x, nl, ni, ng);
+    cls_count4(v1.y, nl, ni, ng);
+    cls_count4(v1.z, nl, ni, ng);
+    cls_count4(v1.w, nl, ni, ng);
+    nl = __reduce_add_sync(0xffffffffu, nl);
+    ni = __reduce_add_sync(0xffffffffu, ni);
+    ng = __reduce_add_sync(0xffffffffu, ng);
+    if (lane == 0) {
+      int* bc = IB[b].bcounts + 3 * chunk;
+      bc[0] = nl;
+      bc[1] = ni;
+      bc[2] = ng;
     }
   }
 }
@@ -551,63 +565,59 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(1024) k_scatter(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
-                                                  int n, int dst, int nchunks) {
-  __shared__ int wcount[32][3];
-  __shared__ int woff[32][3];
-  __shared__ InstDev si;
-  int have = -1;
-  mr_inst_prefetch(si, have, IB, n);
-  __syncthreads();  // publishes the prefetched descriptor (mr_inst_use below skips a held one)
-  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// One warp per chunk, as k_count, with no block barrier: the warp walks the
+// chunk's cells 32 at a time in index order (lane L takes cell 32 it + L),
+// the position of each cell in its class array being the chunk's offset
+// plus the ballot prefix, so that every write is coalesced and every cell
+// gets its place in (level, code) order.  The class bytes, read up front,
+// and the flag bytes are then cleared 16 bytes at a time.
+__global__ void __launch_bounds__(256) k_scatter(const InstDev* __restrict__ IB, const int* __restrict__ chunk_pre,
+                                                 int n, int dst, int nchunks) {
+  mr_grid_dep();
+  const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  for (int t = blockIdx.x; t < nchunks; t += gridDim.x) {  // grid-stride over the chunks
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < nchunks; t += nw) {
     int chunk;
-    mr_inst_use(si, have, IB, mr_group_chunk_of(chunk_pre, n, t, chunk));
-    const Geo& g = si.g;
-    uint8_t* cls = si.cls;
-    uint8_t* flags = si.flags;
-    const int* __restrict__ bc = si.bcounts;
-    const MeshDev& B = si.mesh[dst];
-    const uint32_t gi = (uint32_t)chunk * 1024u + threadIdx.x;
-    const int k = cls_of(cls[gi]);
-    int pre = 0;
+    const InstDev& I = IB[mr_group_chunk_of(chunk_pre, n, t, chunk)];
+    const Geo& g = I.g;
+    const MeshDev& B = I.mesh[dst];
+    const uint32_t c0 = (uint32_t)chunk * MR_DENSE_ALIGN;
+    const uint8_t* cl = I.cls + c0;
+    uint8_t v[32];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const uint32_t bal = __ballot_sync(0xffffffffu, k == c);
-      if (k == c) pre = __popc(bal & lt);
-      if (lane == 0) wcount[wid][c] = __popc(bal);
-    }
-    __syncthreads();
-    if (wid == 0) {  // exclusive scan of the 32 warp counts, one class per pass
+    for (int it = 0; it < 32; ++it) v[it] = cl[32 * it + lane];
+    int run0 = I.bcounts[3 * chunk + 0], run1 = I.bcounts[3 * chunk + 1], run2 = I.bcounts[3 * chunk + 2];
+    const int l = mr_level_of(g, c0);
+    const uint32_t cb = c0 - g.base[l];
+    int32_t* map = B.map + c0;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int v = wcount[lane][c];
-        int x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane >= o) x += y;
-        }
-        woff[lane][c] = x - v;
+    for (int it = 0; it < 32; ++it) {
+      const int k = cls_of(v[it]);
+      const uint32_t bl = __ballot_sync(0xffffffffu, k == (int)MR_CLS_LEAF);
+      const uint32_t bi = __ballot_sync(0xffffffffu, k == (int)MR_CLS_INT);
+      const uint32_t bg = __ballot_sync(0xffffffffu, k == (int)MR_CLS_GHOST);
+      const int at = k == (int)MR_CLS_LEAF ? run0 + __popc(bl & lt)
+                                           : (k == (int)MR_CLS_INT ? run1 + __popc(bi & lt) : run2 + __popc(bg & lt));
+      run0 += __popc(bl);
+      run1 += __popc(bi);
+      run2 += __popc(bg);
+      int32_t e = MR_MAP_NONE;
+      if (k >= 0 && at < g.cap[k]) {
+        B.code[k][at] = cb + 32u * (uint32_t)it + (uint32_t)lane;
+        B.lvl[k][at] = (uint8_t)l;
+        e = (int32_t)(((uint32_t)k << 30) | (uint32_t)at);
       }
+      map[32 * it + lane] = e;
     }
-    __syncthreads();
-    int32_t entry = MR_MAP_NONE;
-    if (k >= 0) {
-      const int pos = bc[chunk * 3 + k] + woff[wid][k] + pre;
-      if (pos < g.cap[k]) {
-        const int l = mr_level_of(g, gi);
-        B.code[k][pos] = gi - g.base[l];
-        B.lvl[k][pos] = (uint8_t)l;
-        entry = (int32_t)(((uint32_t)k << 30) | (uint32_t)pos);
-      }
-    }
-    B.map[gi] = entry;
-    cls[gi] = 0;
-    flags[gi] = 0;
-    __syncthreads();  // wcount / woff are reused by the next chunk
+    __syncwarp();  // every lane's class bytes are read before any are cleared
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    uint4* clp = (uint4*)(I.cls + c0) + 2 * lane;
+    uint4* flp = (uint4*)(I.flags + c0) + 2 * lane;
+    clp[0] = zero;
+    clp[1] = zero;
+    flp[0] = zero;
+    flp[1] = zero;
   }
 }
 
@@ -695,10 +705,11 @@ void mr_launch_mark_ghosts(const Group& G, cudaStream_t st) {
   MR_DISPATCH_D_PDL(k_mark_ghosts, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
 }
 void mr_launch_compact(const Group& G, int dst, cudaStream_t st) {
-  const int grid = std::min(G.chunks, 2 * G.nsm);  // two resident 1024-thread blocks per SM
-  mr_launch_pdl(k_count, grid, 1024, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
+  // one warp per chunk, 8 warps per block, at most 8 blocks per SM
+  const int grid = std::min((G.chunks + 7) / 8, 8 * G.nsm);
+  mr_launch_pdl(k_count, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
   mr_launch_pdl(k_scan_blocks, G.n, 1024, 0, st, G.dev, dst);
-  mr_launch_pdl(k_scatter, grid, 1024, 0, st, G.dev, G.chunk_pre, G.n, dst, G.chunks);
+  mr_launch_pdl(k_scatter, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, dst, G.chunks);
 }
 void mr_launch_leaves_in(const Geo& g, long long n, const unsigned long long* keys,
                          const signed char* levels, int32_t* inidx, uint8_t* cls, MeshCounts* cnt,
