@@ -338,14 +338,40 @@ template <int D>
 __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__ IB,
                                                      const int* __restrict__ chunk_pre, int n) {
   __shared__ InstDev si;
+  __shared__ uint16_t queue[MR_DENSE_ALIGN];  // the chunk's leaves (offsets in the chunk)
+  __shared__ int qn;
   int chunk, have = -1;
   mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
   mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
   const Geo& g = si.g;
   uint8_t* cls = si.cls;
   const bool block = D == 2 && g.diag;
-  MR_DENSE_CHUNK_BEGIN(g, chunk, l, c, gi)
-    if ((cls[gi] & 3u) != MR_C_LEAF) continue;
+  const uint32_t c0 = (uint32_t)chunk * MR_DENSE_ALIGN;
+  const int l = mr_level_of(g, c0);
+  const uint32_t cb = c0 - g.base[l];
+  if (threadIdx.x == 0) qn = 0;
+  __syncthreads();
+  // Leaves are a few per cent of the dense cells: gather them first, so that
+  // the marking below runs on full warps instead of one lane in 32.  The
+  // marks are a union (atomic ORs; only the thread that sets a ghost walks
+  // its parent stencil), so the result does not depend on the order.
+  {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < (int)(MR_DENSE_ALIGN / 256u); ++k) {
+      const uint32_t off = (uint32_t)k * 256u + threadIdx.x;
+      const bool leaf = cb + off < g.ncode[l] && (cls[c0 + off] & 3u) == MR_C_LEAF;
+      const uint32_t bal = __ballot_sync(0xffffffffu, leaf);
+      int at = 0;
+      if (lane == 0 && bal) at = atomicAdd(&qn, __popc(bal));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (leaf) queue[at + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)off;
+    }
+  }
+  __syncthreads();
+  const int nq = qn;
+  for (int qi = threadIdx.x; qi < nq; qi += blockDim.x) {
+    const uint32_t c = cb + queue[qi];
     if constexpr (D == 3) {
       mark_ghosts3(g, cls, l, c);
       continue;
@@ -417,7 +443,7 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
         ++sp;
       }
     }
-  MR_DENSE_CHUNK_END
+  }
 }
 
 // ---------------------------------------------------------------- compaction
