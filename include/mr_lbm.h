@@ -191,7 +191,12 @@ mr_status mr_lbm_get_leaves(mr_lbm_t h, long long* n_inout, unsigned long long* 
  * domain and form a graded tree (every state produced by mr_lbm_step does).
  * keys/levels as in mr_lbm_get_leaves, f SoA [Q][n].  Duplicate or
  * overlapping leaves, or leaves that do not cover the domain, give
- * MR_EINVAL at the next synchronising call. */
+ * MR_EINVAL at the next synchronising call.  With host buffers (on_device =
+ * 0) the call returns once it has read them (pinned buffers are copied
+ * asynchronously, the populations on a second stream of the handle, while
+ * the mesh is built); the build and the gather of the values may still be
+ * running on the handle's stream, and their device-side errors come back at
+ * the next synchronising call. */
 mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* keys,
                             const signed char* levels, const double* f, int on_device);
 

@@ -748,6 +748,12 @@ mr_status mr_lbm_init(mr_lbm_t h, const double* conserved, int on_device) {
 
 static void destroy_handle_impl(mr_lbm_t h) {
   cudaStreamSynchronize(h->st);
+  if (h->up_st) {
+    cudaStreamSynchronize(h->up_st);
+    cudaStreamDestroy(h->up_st);
+    cudaEventDestroy(h->ev_prior);
+    cudaEventDestroy(h->ev_up);
+  }
   drop_graphs(*h);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   for (void* p : h->allocs) cudaFree(p);
@@ -920,18 +926,36 @@ mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* k
   const unsigned long long* dk = keys;
   const signed char* dl = levels;
   const double* df = f;
+  bool up = false;  // populations in flight on up_st
   if (!on_device) {
     const size_t bk = n * sizeof(unsigned long long), bl = (n + 255) / 256 * 256, bf = (size_t)g.Q * n * sizeof(double);
     if (ensure_staging(h, bk + bl + bf) != MR_OK) return h->sticky;
+    if (!h->up_st && (!cuda_ok(h, cudaStreamCreateWithFlags(&h->up_st, cudaStreamNonBlocking)) ||
+                      !cuda_ok(h, cudaEventCreateWithFlags(&h->ev_prior, cudaEventDisableTiming)) ||
+                      !cuda_ok(h, cudaEventCreateWithFlags(&h->ev_up, cudaEventDisableTiming))))
+      return MR_ECUDA;
     char* sp = (char*)h->staging;
+    // the populations (most of the bytes) go up on the second stream, after
+    // the handle stream's earlier work (which may still read the staging
+    // buffer), while the keys are checked and the mesh is built
+    if (!cuda_ok(h, cudaEventRecord(h->ev_prior, h->st)) ||
+        !cuda_ok(h, cudaStreamWaitEvent(h->up_st, h->ev_prior, 0)) ||
+        !cuda_ok(h, cudaMemcpyAsync(sp + bk + bl, f, bf, cudaMemcpyHostToDevice, h->up_st)) ||
+        !cuda_ok(h, cudaEventRecord(h->ev_up, h->up_st)))
+      return MR_ECUDA;
+    up = true;
     if (!cuda_ok(h, cudaMemcpyAsync(sp, keys, bk, cudaMemcpyHostToDevice, h->st)) ||
-        !cuda_ok(h, cudaMemcpyAsync(sp + bk, levels, n, cudaMemcpyHostToDevice, h->st)) ||
-        !cuda_ok(h, cudaMemcpyAsync(sp + bk + bl, f, bf, cudaMemcpyHostToDevice, h->st)))
+        !cuda_ok(h, cudaMemcpyAsync(sp + bk, levels, n, cudaMemcpyHostToDevice, h->st)))
       return MR_ECUDA;
     dk = (const unsigned long long*)sp;
     dl = (const signed char*)(sp + bk);
     df = (const double*)(sp + bk + bl);
   }
+  // every return below leaves the handle's stream ordered after the upload
+  auto join = [&]() {
+    if (up) cudaStreamWaitEvent(h->st, h->ev_up, 0);
+    up = false;
+  };
   MeshDev& B = h->mesh[h->cur];
   if (!cuda_ok(h, cudaMemsetAsync(h->vol, 0, sizeof(unsigned long long), h->st))) return MR_ECUDA;
   mr_launch_leaves_in(g, n, dk, dl, h->inidx, h->cls, B.cnt, h->vol, h->st, grid_for(h));
@@ -941,18 +965,26 @@ mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* k
   if (!cuda_ok(h, cudaMemcpyAsync(&vol, h->vol, sizeof(vol), cudaMemcpyDeviceToHost, h->st))) return MR_ECUDA;
   MeshCounts hc[2];
   mr_status s = read_counts(h, hc);
-  if (s != MR_OK) return s;
+  if (s != MR_OK) {
+    join();
+    return s;
+  }
   unsigned long long full = g.ncode[g.J];
-  if (vol != full) return fail(h, MR_EINVAL);
+  if (vol != full) {
+    join();
+    return fail(h, MR_EINVAL);
+  }
   run_build(*h, h->grp, h->cur);
+  join();
   mr_launch_gather_input(g, B, h->inidx, n, df, h->fstate, h->st, grid_for(h));
   count_launch(h);
   // reset the input index map for the next call
   if (!cuda_ok(h, cudaMemsetAsync(h->inidx, 0xff, (size_t)g.base[g.J + 1] * sizeof(int32_t), h->st)))
     return MR_ECUDA;
   if (check_launch(h) != MR_OK) return h->sticky;
-  s = read_counts(h, hc);
-  if (s != MR_OK) return s;
+  // the caller's buffers are free once the upload is done; errors of the
+  // build and the gather come back at the next synchronising call
+  if (!on_device && !cuda_ok(h, cudaEventSynchronize(h->ev_up))) return MR_ECUDA;
   h->initialized = true;
   return MR_OK;
 }

@@ -55,6 +55,9 @@ struct mr_lbm : Exec {
   size_t dense_elems = 0;
   void* staging = nullptr;
   size_t staging_bytes = 0;
+  // upload of mr_lbm_set_leaves' populations beside the mesh build
+  cudaStream_t up_st = nullptr;
+  cudaEvent_t ev_prior = nullptr, ev_up = nullptr;
   bool initialized = false;
   mr_status sticky = MR_OK;
   std::vector<void*> allocs;
