@@ -105,7 +105,9 @@ typedef struct {
                             D2Q9: s[0] (energy, energy square, heat flux), s[1] (stress) */
   double phys[8];        /* scheme constants (see mr_scheme) */
   double xmin[3], xmax[3]; /* physical domain (used by the obstacle only) */
-  int roots[3];          /* cells per axis at level 0 (1 for the unit square) */
+  int roots[3];          /* cells per axis at level 0 (1 for the unit square); MR_EINVAL
+                            unless roots_x roots_y roots_z 2^(d max_level) <= 2^32 and
+                            the cells of levels min_level..max_level number under 2^30 */
   int min_level, max_level; /* J_min and J; 2 <= J_min <= J <= 15 */
   double eps;            /* threshold epsilon >= 0, eps_j = 2^{d(j-J)} eps (Sec. 4.4) */
   int mu_bar;            /* regularity guess of the refinement rule, >= 0 */

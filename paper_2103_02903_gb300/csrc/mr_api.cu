@@ -609,8 +609,9 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   g.Jmin = cfg->min_level;
   g.J = cfg->max_level;
   for (int a = 0; a < 3; ++a) g.roots[a] = a < g.d ? std::max(1, cfg->roots[a]) : 1;
-  if ((g.d == 2 && g.roots[0] * g.roots[1] > 2) ||
-      (g.d == 3 && g.roots[0] * g.roots[1] * g.roots[2] > 2)) {  // root prefix must fit the 32-bit key
+  // the root-prefixed codes of the finest level must fit the 32-bit code
+  // arrays (the dense index space below, under 2^30, bounds them further)
+  if (((uint64_t)g.roots[0] * g.roots[1] * g.roots[2] << (g.d * g.J)) > (1ull << 32)) {
     delete h;
     return MR_EINVAL;
   }
