@@ -511,6 +511,9 @@ def run_ours(args):
         roofline["traffic"] = CAPTURED_DRAM_BYTES_PER_LEAF[args.form] * per_step_leaves
         roofline["traffic_unit"] = "B per launch"
         roofline["traffic_kind"] = CAPTURED_DRAM_NOTE
+        # the same bytes over the live launch time, against the measured HBM peak
+        roofline["traffic_gbs"] = roofline["traffic"] / kern_avg_s / 1e9
+        roofline["traffic_frac_of_hbm"] = roofline["traffic_gbs"] / peaks["hbm_gbs"]
     roofline.update({"kernel_ms_avg": 1e3 * kern_avg_s, "kernel_share_of_step": kern_ms / 1e3 / total_s,
                      "alg_flops_per_leaf": ALG_FLOPS_PER_LEAF, "alg_bytes_per_leaf": bytes_per_leaf})
 
@@ -560,7 +563,10 @@ def run_ours(args):
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         lv, st, t = _oracle_sample(cfg, u, args.cpu_seconds)
+        from paper_2103_02903_gb300 import workloads as wl
+        dense_cells = st * int(np.prod(wl.finest_shape(cfg)))
         cpu = {"value": lv / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "dense_cell_updates_per_s": dense_cells / t,
                "sample": "oracle (single thread) steps 1..%d of the same workload from its initial "
                          "condition, %.1f s" % (st, t)}
         if args.cpu_all_cores:
