@@ -33,6 +33,7 @@ class OrConfig(C.Structure):
         ("cross_sign", C.c_int),
         ("obstacle", C.c_int),
         ("exact_collision", C.c_int),
+        ("pred_s", C.c_int),
     ]
 
 
@@ -69,6 +70,8 @@ def lib():
         L.or_group_norms.argtypes = [vp, C.c_int, dp]
         L.or_prediction_coefficient.restype = C.c_double
         L.or_predict_children.argtypes = [C.c_int, C.c_int, dp, dp]
+        L.or_predict_children_s.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
+        L.or_prediction_coefficients.argtypes = [C.c_int, dp]
         L.or_check_graded.argtypes = [vp]
         _lib = L
     return _lib
@@ -96,6 +99,7 @@ def make_config(cfg: dict) -> OrConfig:
     c.cross_sign = int(cfg.get("cross_sign", 1))
     c.obstacle = int(cfg.get("obstacle", 0))
     c.exact_collision = int(cfg.get("exact_collision", 0))
+    c.pred_s = int(cfg.get("pred_s", 1))
     return c
 
 
@@ -193,4 +197,21 @@ def prediction_coefficient():
 def predict_children(d, stencil, cross_sign=1):
     out = np.zeros(1 << d, np.float64)
     lib().or_predict_children(d, cross_sign, np.ascontiguousarray(stencil, np.float64).ravel(), out)
+    return out
+
+
+def prediction_coefficients(s):
+    out = np.zeros(s, np.float64)
+    if lib().or_prediction_coefficients(s, out) != 0:
+        raise ValueError("s must be 1, 2 or 3")
+    return out
+
+
+def predict_children_s(d, stencil, cross_sign=1, s=1):
+    """Children of a (2s+1)^d stencil (x fastest) under the prediction of half-width s."""
+    out = np.zeros(1 << d, np.float64)
+    st = np.ascontiguousarray(stencil, np.float64).ravel()
+    assert st.size == (2 * s + 1) ** d
+    if lib().or_predict_children_s(d, cross_sign, s, st, out) != 0:
+        raise ValueError("bad d or s")
     return out

@@ -22,7 +22,11 @@
  * step: epsilon = 0 reduces to Eq. StreamFinest; conservation; Eq.
  * PredictionWithMatrix; brute-force minimal grading; the exact collision:
  * linear equilibria, finest leaves, mass, closed-form D1Q2 composition in
- * tests/test_oracle_exact_collision.py).
+ * tests/test_oracle_exact_collision.py; the prediction of half-width s = 2,
+ * 3 and the grading it widens: Appendix 2 coefficients, exactness to degree
+ * 2s and not beyond, consistency, the 2^-(2s+1) decay of details,
+ * brute-force minimal grading with the radius-2 stencil, in
+ * tests/test_oracle_prediction_s.py).
  */
 #include "oracle.h"
 
@@ -43,6 +47,7 @@ struct or_state {
   double srel[4][9];
   int cons_lat[4], cons_mom[4];
   int Jmin, J;
+  int s_pred; /* prediction stencil half-width s */
   int n[MAXL][3];
   long long nc[MAXL];
   unsigned char* leaf[MAXL];
@@ -331,28 +336,59 @@ static void equilibrium_populations(const or_state* S, const double* u, double* 
 /* multiresolution operators (Sec. 4)                                        */
 /* ------------------------------------------------------------------------ */
 
-/* Table 1, s = 1 */
-static const double C1 = -0.125;
+/* Table 1: c_1 .. c_s of the centred prediction of stencil half-width s. */
+static const double CTAB[4][3] = {
+    {0.0, 0.0, 0.0},
+    {-1.0 / 8.0, 0.0, 0.0},
+    {-22.0 / 128.0, 3.0 / 128.0, 0.0},
+    {-201.0 / 1024.0, 11.0 / 256.0, -5.0 / 1024.0},
+};
+static const double C1 = -0.125; /* s = 1 */
 
 double or_prediction_coefficient(void) { return C1; }
 
-/* Prediction operator of Sec. 4.1 on a (3)^d stencil v (x fastest) for the
- * child delta.  Reading: the diagonal (pair) term enters with the sign of the
- * tensor product of the one-dimensional operator, cross_sign = +1 (the
+int or_prediction_coefficients(int s, double* out) {
+  if (s < 1 || s > 3) return -1;
+  for (int i = 0; i < s; ++i) out[i] = CTAB[s][i];
+  return 0;
+}
+
+/* Prediction operator of Sec. 4.1 on a (2s+1)^d stencil v (x fastest) for
+ * the child delta: the one-dimensional sums along each axis, the products
+ * c_a c_b over the diagonals of each pair of axes and, in 3D, c_a c_b c_t
+ * over the cube's diagonals (the tensor-product construction of Bihari and
+ * Harten that Sec. 4.1 states for general s).  Every sum starts from its
+ * (1, 1, 1) term, so that s = 1 evaluates exactly the expressions of the
+ * 3^d formulas.  Reading: the diagonal (pair) term enters with the sign of
+ * the tensor product of the one-dimensional operator, cross_sign = +1 (the
  * construction of Appendix 2 and the exactness on polynomials of degree 2s);
  * cross_sign = -1 reproduces the sign printed in the formula and Fig. 2. */
-static double predict_stencil(int d, int cross_sign, const double* v, int dx, int dy, int dz) {
+static double predict_stencil_s(int d, int cross_sign, int s, const double* v, int dx, int dy, int dz) {
+  const double* c = CTAB[s];
+  const int w = 2 * s + 1;
   double sx = dx ? -1.0 : 1.0, sy = dy ? -1.0 : 1.0, sz = dz ? -1.0 : 1.0;
   double cs = (double)cross_sign;
   if (d == 1) {
-    double qx = C1 * (v[2] - v[0]);
-    return v[1] + sx * qx;
+#define V1(a) v[(a) + s]
+    double qx = c[0] * (V1(1) - V1(-1));
+    for (int a = 2; a <= s; ++a) qx = qx + c[a - 1] * (V1(a) - V1(-a));
+    return V1(0) + sx * qx;
+#undef V1
   }
   if (d == 2) {
-#define V2(a, b) v[((b) + 1) * 3 + ((a) + 1)]
-    double qx = C1 * (V2(1, 0) - V2(-1, 0));
-    double qy = C1 * (V2(0, 1) - V2(0, -1));
-    double q2 = (C1 * C1) * (((V2(1, 1) - V2(-1, 1)) - V2(1, -1)) + V2(-1, -1));
+#define V2(a, b) v[((b) + s) * w + ((a) + s)]
+    double qx = c[0] * (V2(1, 0) - V2(-1, 0));
+    double qy = c[0] * (V2(0, 1) - V2(0, -1));
+    for (int a = 2; a <= s; ++a) {
+      qx = qx + c[a - 1] * (V2(a, 0) - V2(-a, 0));
+      qy = qy + c[a - 1] * (V2(0, a) - V2(0, -a));
+    }
+    double q2 = 0.0;
+    for (int b = 1; b <= s; ++b)
+      for (int a = 1; a <= s; ++a) {
+        double t = (c[a - 1] * c[b - 1]) * (((V2(a, b) - V2(-a, b)) - V2(a, -b)) + V2(-a, -b));
+        q2 = (a == 1 && b == 1) ? t : q2 + t;
+      }
     double t = V2(0, 0);
     t = t + sx * qx;
     t = t + sy * qy;
@@ -361,18 +397,38 @@ static double predict_stencil(int d, int cross_sign, const double* v, int dx, in
 #undef V2
   }
   {
-#define V3(a, b, c) v[(((c) + 1) * 3 + ((b) + 1)) * 3 + ((a) + 1)]
-    double qx = C1 * (V3(1, 0, 0) - V3(-1, 0, 0));
-    double qy = C1 * (V3(0, 1, 0) - V3(0, -1, 0));
-    double qz = C1 * (V3(0, 0, 1) - V3(0, 0, -1));
-    double qxy = (C1 * C1) * (((V3(1, 1, 0) - V3(-1, 1, 0)) - V3(1, -1, 0)) + V3(-1, -1, 0));
-    double qxz = (C1 * C1) * (((V3(1, 0, 1) - V3(-1, 0, 1)) - V3(1, 0, -1)) + V3(-1, 0, -1));
-    double qyz = (C1 * C1) * (((V3(0, 1, 1) - V3(0, -1, 1)) - V3(0, 1, -1)) + V3(0, -1, -1));
-    double q3 = (C1 * C1 * C1) *
-                (((((((V3(1, 1, 1) - V3(-1, 1, 1)) - V3(1, -1, 1)) - V3(1, 1, -1)) + V3(-1, -1, 1)) +
-                   V3(-1, 1, -1)) +
-                  V3(1, -1, -1)) -
-                 V3(-1, -1, -1));
+#define V3(a, b, e) v[(((e) + s) * w + ((b) + s)) * w + ((a) + s)]
+    double qx = c[0] * (V3(1, 0, 0) - V3(-1, 0, 0));
+    double qy = c[0] * (V3(0, 1, 0) - V3(0, -1, 0));
+    double qz = c[0] * (V3(0, 0, 1) - V3(0, 0, -1));
+    for (int a = 2; a <= s; ++a) {
+      qx = qx + c[a - 1] * (V3(a, 0, 0) - V3(-a, 0, 0));
+      qy = qy + c[a - 1] * (V3(0, a, 0) - V3(0, -a, 0));
+      qz = qz + c[a - 1] * (V3(0, 0, a) - V3(0, 0, -a));
+    }
+    double qxy = 0.0, qxz = 0.0, qyz = 0.0, q3 = 0.0;
+    for (int b = 1; b <= s; ++b)
+      for (int a = 1; a <= s; ++a) {
+        const double cc = c[a - 1] * c[b - 1];
+        const int first = a == 1 && b == 1;
+        double t;
+        t = cc * (((V3(a, b, 0) - V3(-a, b, 0)) - V3(a, -b, 0)) + V3(-a, -b, 0));
+        qxy = first ? t : qxy + t;
+        t = cc * (((V3(a, 0, b) - V3(-a, 0, b)) - V3(a, 0, -b)) + V3(-a, 0, -b));
+        qxz = first ? t : qxz + t;
+        t = cc * (((V3(0, a, b) - V3(0, -a, b)) - V3(0, a, -b)) + V3(0, -a, -b));
+        qyz = first ? t : qyz + t;
+      }
+    for (int e = 1; e <= s; ++e)
+      for (int b = 1; b <= s; ++b)
+        for (int a = 1; a <= s; ++a) {
+          double t = (c[a - 1] * c[b - 1] * c[e - 1]) *
+                     (((((((V3(a, b, e) - V3(-a, b, e)) - V3(a, -b, e)) - V3(a, b, -e)) + V3(-a, -b, e)) +
+                        V3(-a, b, -e)) +
+                       V3(a, -b, -e)) -
+                      V3(-a, -b, -e));
+          q3 = (a == 1 && b == 1 && e == 1) ? t : q3 + t;
+        }
     double t = V3(0, 0, 0);
     t = t + sx * qx;
     t = t + sy * qy;
@@ -389,25 +445,33 @@ static double predict_stencil(int d, int cross_sign, const double* v, int dx, in
 int or_predict_children(int d, int cross_sign, const double* stencil, double* out) {
   int nch = 1 << d;
   for (int ci = 0; ci < nch; ++ci)
-    out[ci] = predict_stencil(d, cross_sign, stencil, ci & 1, (ci >> 1) & 1, (ci >> 2) & 1);
+    out[ci] = predict_stencil_s(d, cross_sign, 1, stencil, ci & 1, (ci >> 1) & 1, (ci >> 2) & 1);
+  return 0;
+}
+
+int or_predict_children_s(int d, int cross_sign, int s, const double* stencil, double* out) {
+  if (s < 1 || s > 3 || d < 1 || d > 3) return -1;
+  int nch = 1 << d;
+  for (int ci = 0; ci < nch; ++ci)
+    out[ci] = predict_stencil_s(d, cross_sign, s, stencil, ci & 1, (ci >> 1) & 1, (ci >> 2) & 1);
   return 0;
 }
 
 /* Predicted value of population p on child cell (l, x, y, z) from level l-1. */
 static double predict(const or_state* S, double* const* F, int l, int x, int y, int z, int p) {
   int L = l - 1, px = x >> 1, py = y >> 1, pz = z >> 1;
-  double v[27];
-  int d = S->d;
-  int nz3 = d >= 3 ? 3 : 1, ny3 = d >= 2 ? 3 : 1;
-  for (int c = 0; c < nz3; ++c)
-    for (int b = 0; b < ny3; ++b)
-      for (int a = 0; a < 3; ++a) {
-        int sx = stencil_coord(S, L, 0, px + a - 1);
-        int sy = d >= 2 ? stencil_coord(S, L, 1, py + b - 1) : 0;
-        int sz = d >= 3 ? stencil_coord(S, L, 2, pz + c - 1) : 0;
-        v[(c * ny3 + b) * 3 + a] = F[L][cidx(S, L, sx, sy, sz) * S->Q + p];
+  double v[343]; /* (2s+1)^d <= 7^3 */
+  int d = S->d, s = S->s_pred, w = 2 * s + 1;
+  int nz = d >= 3 ? w : 1, ny = d >= 2 ? w : 1;
+  for (int c = 0; c < nz; ++c)
+    for (int b = 0; b < ny; ++b)
+      for (int a = 0; a < w; ++a) {
+        int sx = stencil_coord(S, L, 0, px + a - s);
+        int sy = d >= 2 ? stencil_coord(S, L, 1, py + b - s) : 0;
+        int sz = d >= 3 ? stencil_coord(S, L, 2, pz + c - s) : 0;
+        v[(c * ny + b) * w + a] = F[L][cidx(S, L, sx, sy, sz) * S->Q + p];
       }
-  return predict_stencil(d, S->cfg.cross_sign, v, x & 1, y & 1, z & 1);
+  return predict_stencil_s(d, S->cfg.cross_sign, s, v, x & 1, y & 1, z & 1);
 }
 
 /* Membership of R(Lambda): leaves and all their ancestors. */
@@ -506,6 +570,8 @@ or_state* or_create(const or_config* cfg) {
   S->Jmin = cfg->min_level;
   S->J = cfg->max_level;
   if (S->Jmin < 0 || S->J >= MAXL || S->Jmin > S->J) { free(S); return NULL; }
+  S->s_pred = cfg->pred_s == 0 ? 1 : cfg->pred_s;
+  if (S->s_pred < 1 || S->s_pred > 3) { free(S); return NULL; }
   for (int l = S->Jmin; l <= S->J; ++l) {
     long long tot = 1;
     for (int a = 0; a < 3; ++a) {
@@ -717,7 +783,8 @@ static int adapt_impl(or_state* S) {
     }
 
   /* G: minimal graded tree, iterated to a fixed point (Def. Grading): every
-   * cell above J_min has the (3)^d stencil around its parent in the tree. */
+   * cell above J_min has the (2s+1)^d stencil around its parent in the tree. */
+  const int sp = S->s_pred;
   int changed = 1;
   while (changed) {
     changed = 0;
@@ -727,9 +794,9 @@ static int adapt_impl(or_state* S) {
         int x, y, z;
         cell_coords(S, l, c, &x, &y, &z);
         int px = x >> 1, py = y >> 1, pz = z >> 1;
-        for (int oc = (d >= 3 ? -1 : 0); oc <= (d >= 3 ? 1 : 0); ++oc)
-          for (int ob = (d >= 2 ? -1 : 0); ob <= (d >= 2 ? 1 : 0); ++ob)
-            for (int oa = -1; oa <= 1; ++oa) {
+        for (int oc = (d >= 3 ? -sp : 0); oc <= (d >= 3 ? sp : 0); ++oc)
+          for (int ob = (d >= 2 ? -sp : 0); ob <= (d >= 2 ? sp : 0); ++ob)
+            for (int oa = -sp; oa <= sp; ++oa) {
               int nx = mesh_coord(S, l - 1, 0, px + oa);
               int ny = mesh_coord(S, l - 1, 1, py + ob);
               int nz = mesh_coord(S, l - 1, 2, pz + oc);
@@ -977,9 +1044,10 @@ int or_check_graded(const or_state* S) {
       int x, y, z;
       cell_coords(S, l, c, &x, &y, &z);
       int px = x >> 1, py = y >> 1, pz = z >> 1;
-      for (int oc = (S->d >= 3 ? -1 : 0); oc <= (S->d >= 3 ? 1 : 0); ++oc)
-        for (int ob = (S->d >= 2 ? -1 : 0); ob <= (S->d >= 2 ? 1 : 0); ++ob)
-          for (int oa = -1; oa <= 1; ++oa) {
+      const int sp = S->s_pred;
+      for (int oc = (S->d >= 3 ? -sp : 0); oc <= (S->d >= 3 ? sp : 0); ++oc)
+        for (int ob = (S->d >= 2 ? -sp : 0); ob <= (S->d >= 2 ? sp : 0); ++ob)
+          for (int oa = -sp; oa <= sp; ++oa) {
             int nx = mesh_coord(S, l - 1, 0, px + oa);
             int ny = mesh_coord(S, l - 1, 1, py + ob);
             int nz = mesh_coord(S, l - 1, 2, pz + oc);

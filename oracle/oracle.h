@@ -46,6 +46,7 @@ typedef struct {
   int cross_sign;      /* +1 tensor-product prediction, -1 diagonal term as printed */
   int obstacle;        /* 1: volume-fraction penalisation after collision (Sec. 7.2) */
   int exact_collision; /* 1: collide the reconstructed finest data, then average (Eq. sourceoferror) */
+  int pred_s;          /* prediction stencil half-width s = 1, 2, 3 (Table 1); 0 reads as 1 */
 } or_config;
 
 typedef struct or_state or_state;
@@ -87,6 +88,11 @@ double or_prediction_coefficient(void);
 /* Predict the 2^d children of a level-0 parent from a (3)^d stencil given
  * row-major (x fastest); out[ci] with ci = dx + 2 dy + 4 dz. */
 int or_predict_children(int d, int cross_sign, const double* stencil, double* out);
+/* Table 1 coefficients c_1 .. c_s of the prediction of half-width s (1..3). */
+int or_prediction_coefficients(int s, double* out);
+/* The prediction of half-width s on a (2s+1)^d stencil (x fastest): the 2^d
+ * children's values, child index (dz << 2) | (dy << 1) | dx. */
+int or_predict_children_s(int d, int cross_sign, int s, const double* stencil, double* out);
 /* Mesh invariants of the current state: 1 if the leaves form a graded tree. */
 int or_check_graded(const or_state* st);
 
