@@ -134,7 +134,7 @@ def make_config(cfg: Dict, leaf_capacity: int = 0) -> MrConfig:
     c.max_level = int(cfg["max_level"])
     c.eps = float(cfg["eps"])
     c.mu_bar = int(cfg["mu_bar"])
-    c.pred_s = 1
+    c.pred_s = int(cfg.get("pred_s", 1))
     for f in range(6):
         b = cfg["bc"][f]
         c.bc[f] = BCS[b] if isinstance(b, str) else int(b)

@@ -57,6 +57,51 @@ def test_create_rejects_bad_config(lib):
     assert binding.library().mr_lbm_create(ctypes.byref(c), None, ctypes.byref(h)) == 1
 
 
+def _bad(name):
+    """One invalid configuration per rule of mr_lbm_create's validation."""
+    from paper_2103_02903_gb300 import workloads as W
+    cases = {
+        "negative_eps": (W.advection_1d, dict(max_level=6), dict(eps=-1.0)),
+        "lambda_zero": (W.advection_1d, dict(max_level=6), dict(lambda_=0.0)),
+        "relaxation_above_2": (W.advection_1d, dict(max_level=6), dict(s=[2.5] + [0.0] * 15)),
+        "mu_bar_negative": (W.advection_1d, dict(max_level=6), dict(mu_bar=-1)),
+        "min_level_below_2": (W.advection_1d, dict(max_level=6), dict(min_level=1)),
+        "max_below_min": (W.advection_1d, dict(max_level=6), dict(min_level=5, max_level=4)),
+        "max_level_16": (W.advection_1d, dict(max_level=6), dict(max_level=16)),
+        "prediction_s2_on_gpu": (W.advection_1d, dict(max_level=6), dict(pred_s=2)),
+        "half_periodic_axis": (W.advection_1d, dict(max_level=6),
+                               dict(bc=["periodic", "copy"] + ["periodic"] * 4)),
+        "obstacle_not_d2q9": (W.euler_2d, dict(max_level=5), dict(obstacle=1)),
+        "moving_wall_not_d2q9": (W.euler_2d, dict(max_level=5), dict(bc=["bounce_back_velocity"] * 6)),
+        "printed_sign_d2q9": (W.ns_obstacle_2d, dict(max_level=5), dict(cross_sign=-1)),
+        "exact_collision_fp16": (W.euler_2d, dict(max_level=5), dict(exact_collision=1, precision="fp16")),
+        "exact_collision_3d": (W.advection_3d, dict(max_level=4), dict(exact_collision=1)),
+        "d3q6_level_11": (W.advection_3d, dict(max_level=4), dict(max_level=11)),
+        "d3q6_dense_space": (W.advection_3d, dict(max_level=4), dict(max_level=10)),
+        "d2_dense_space": (W.euler_2d, dict(max_level=5), dict(max_level=15)),
+        "roots_overflow_codes": (W.euler_2d, dict(max_level=5), dict(roots=[1024, 1024, 1], max_level=12)),
+    }
+    make, kw, change = cases[name]
+    cfg, _ = make(**kw)
+    cfg.update(change)
+    return cfg
+
+
+@pytest.mark.parametrize("name", [
+    "negative_eps", "lambda_zero", "relaxation_above_2", "mu_bar_negative", "min_level_below_2",
+    "max_below_min", "max_level_16", "prediction_s2_on_gpu", "half_periodic_axis", "obstacle_not_d2q9",
+    "moving_wall_not_d2q9", "printed_sign_d2q9", "exact_collision_fp16", "exact_collision_3d",
+    "d3q6_level_11", "d3q6_dense_space", "d2_dense_space", "roots_overflow_codes"])
+def test_create_rejects_each_invalid_config(lib, name):
+    """Every rule is checked on the host before any device call, so this
+    runs without a GPU: MR_EINVAL (1) and a NULL handle."""
+    from paper_2103_02903_gb300 import binding
+    c = binding.make_config(_bad(name))
+    h = ctypes.c_void_p(1)
+    assert binding.library().mr_lbm_create(ctypes.byref(c), None, ctypes.byref(h)) == 1
+    assert not h.value
+
+
 def _paper_matrix():
     rows = []
     with open(os.path.join(ROOT, "tests", "golden", "flattening_matrix_1d.txt")) as fh:
