@@ -239,6 +239,16 @@ const char* mr_lbm_strerror(mr_status s);
 mr_status mr_lbm_flattened_weights(int roots, int level, int max_level, int periodic, int k,
                                    double* out);
 
+/* Host-only: the same weights for the prediction of half-width s = 1, 2, 3
+ * (Table 1; Sec. 4.1) over the window delta = -half_width..half_width:
+ * out[0 .. 2w] for the velocity +1, out[2w+1 .. 4w+1] for -1 (w =
+ * half_width; 4w + 2 doubles), max_level - level <= 12.  MR_EINVAL if a cell
+ * outside the window carries a nonzero weight (the window is too narrow for
+ * this s and gap) or an argument is out of range.  s = 1 with half_width 2
+ * gives the weights of mr_lbm_flattened_weights. */
+mr_status mr_lbm_flattened_weights_s(int s, int half_width, int roots, int level, int max_level,
+                                     int periodic, int k, double* out);
+
 /* ------------------------------------------------------------------ adjoint
  * Gradients of a functional of the trajectory through the time steps with
  * the mesh of every step frozen (the adaptation decisions of the forward

@@ -89,6 +89,7 @@ def library():
         L.mr_lbm_strerror.argtypes = [i]
         L.mr_lbm_strerror.restype = C.c_char_p
         L.mr_lbm_flattened_weights.argtypes = [i, i, i, i, i, vp]
+        L.mr_lbm_flattened_weights_s.argtypes = [i, i, i, i, i, i, i, vp]
         L.mr_lbm_adjoint.argtypes = [vp, vp, i, i, i, i, C.POINTER(d), vp, vp]
         L.mr_lbm_adjoint.restype = i
         L.mr_lbm_batch_create.argtypes = [C.POINTER(MrConfig), i, vp, C.POINTER(vp)]
@@ -104,7 +105,7 @@ def library():
         for name in ("mr_lbm_create", "mr_lbm_destroy", "mr_lbm_init", "mr_lbm_step", "mr_lbm_adapt",
                      "mr_lbm_project", "mr_lbm_project_noalloc", "mr_lbm_get_leaves", "mr_lbm_set_leaves", "mr_lbm_stats",
                      "mr_lbm_counters", "mr_lbm_profile_enable", "mr_lbm_profile_read",
-                     "mr_lbm_synchronize", "mr_lbm_flattened_weights", "mr_lbm_batch_create",
+                     "mr_lbm_synchronize", "mr_lbm_flattened_weights", "mr_lbm_flattened_weights_s", "mr_lbm_batch_create",
                      "mr_lbm_batch_instance", "mr_lbm_batch_step", "mr_lbm_batch_synchronize",
                      "mr_lbm_batch_counters", "mr_lbm_batch_profile_enable", "mr_lbm_batch_profile_read",
                      "mr_lbm_batch_destroy"):
@@ -164,6 +165,15 @@ def flattened_weights(roots: int, level: int, max_level: int, periodic: bool, k:
     out = np.zeros(10, np.float64)
     _check(library().mr_lbm_flattened_weights(roots, level, max_level, int(periodic), k,
                                               out.ctypes.data), "mr_lbm_flattened_weights")
+    return out
+
+
+def flattened_weights_s(s: int, half_width: int, roots: int, level: int, max_level: int, periodic: bool,
+                        k: int) -> np.ndarray:
+    """Weights of f_{k-w..k+w} for the velocities +1 (first 2w+1) and -1 (last 2w+1)."""
+    out = np.zeros(4 * half_width + 2, np.float64)
+    _check(library().mr_lbm_flattened_weights_s(s, half_width, roots, level, max_level, int(periodic), k,
+                                                out.ctypes.data), "mr_lbm_flattened_weights_s")
     return out
 
 

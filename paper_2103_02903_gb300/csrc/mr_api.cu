@@ -592,6 +592,78 @@ mr_status mr_lbm_flattened_weights(int roots, int level, int max_level, int peri
   return MR_OK;
 }
 
+// Table 1: c_1 .. c_s of the prediction of half-width s.
+const double kPredCoef[4][3] = {
+    {0.0, 0.0, 0.0},
+    {-1.0 / 8.0, 0.0, 0.0},
+    {-22.0 / 128.0, 3.0 / 128.0, 0.0},
+    {-201.0 / 1024.0, 11.0 / 256.0, -5.0 / 1024.0},
+};
+
+// One-dimensional reconstruction with the prediction of half-width s applied
+// `gap` times to a level field of N cells, constant extension outside.
+void recon1d_s(std::vector<double>& cur, int N, int gap, int s) {
+  for (int it = 0; it < gap; ++it) {
+    std::vector<double> nxt(2 * (size_t)N);
+    auto at = [&](int i) { return cur[std::min(std::max(i, 0), N - 1)]; };
+    for (int k = 0; k < N; ++k) {
+      double q = 0.0;
+      for (int a = 1; a <= s; ++a) q += kPredCoef[s][a - 1] * (at(k + a) - at(k - a));
+      nxt[2 * k] = cur[k] + q;
+      nxt[2 * k + 1] = cur[k] - q;
+    }
+    cur.swap(nxt);
+    N *= 2;
+  }
+}
+
+mr_status mr_lbm_flattened_weights_s(int s, int half_width, int roots, int level, int max_level, int periodic,
+                                     int k, double* out) {
+  if (!out || s < 1 || s > 3 || half_width < 1 || half_width > 16 || roots < 1 || level < 0 ||
+      max_level < level || max_level - level > 12 || level > 20)
+    return MR_EINVAL;
+  const long long N = (long long)roots << level;
+  if (k < 0 || k >= N) return MR_EINVAL;
+  const int W = half_width, gap = max_level - level, n = 1 << gap;
+  // a window of the level around k: the true faces where k is within 2W + 2
+  // cells of a non-periodic one, else an interior patch whose own faces lie
+  // beyond every weight's reach (then periodic and interior cells agree)
+  const int M = 4 * W + 5;
+  int Nsim, ks;
+  if (periodic || (k >= 2 * W + 2 && k <= N - 3 - 2 * W)) {
+    Nsim = M;
+    ks = 2 * W + 2;
+  } else if (k < 2 * W + 2) {
+    Nsim = (int)std::min<long long>(N, M);
+    ks = k;
+  } else {
+    Nsim = (int)std::min<long long>(N, M);
+    ks = (int)(k - (N - Nsim));
+  }
+  const bool lo_face = !periodic && k == 0, hi_face = !periodic && k == N - 1;
+  for (int dl = -(W + 2); dl <= W + 2; ++dl) {
+    const int i = ks + dl;
+    double r0 = 0, r1 = 0, l0 = 0, l1 = 0;
+    if (i >= 0 && i < Nsim) {
+      std::vector<double> f(Nsim, 0.0);
+      f[i] = 1.0;
+      recon1d_s(f, Nsim, gap, s);
+      if (!lo_face) r0 = f[(size_t)n * ks - 1];
+      r1 = f[(size_t)n * (ks + 1) - 1];
+      l0 = f[(size_t)n * ks];
+      if (!hi_face) l1 = f[(size_t)n * (ks + 1)];
+    }
+    const double wp = r0 - r1, wm = l1 - l0;
+    if (dl < -W || dl > W) {
+      if (wp != 0.0 || wm != 0.0) return MR_EINVAL;  // the weights reach beyond the half-width
+      continue;
+    }
+    out[dl + W] = wp;
+    out[2 * W + 1 + dl + W] = wm;
+  }
+  return MR_OK;
+}
+
 mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* out) {
   if (!out) return MR_EINVAL;
   *out = nullptr;

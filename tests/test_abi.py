@@ -157,3 +157,72 @@ def test_flattened_weights_match_oracle_near_boundaries(lib, k, gap):
     l_kp1 = fine[m * (k + 1)] if k + 1 < n else 0.0
     assert abs(w[0:5] @ win - (r_km1 - r_k)) < 1e-13
     assert abs(w[5:10] @ win - (l_kp1 - l_k)) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# flattened weights of the prediction of half-width s (host only)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("gap", [1, 2, 4])
+def test_flattened_weights_s1_are_the_transport_tables(lib, periodic, gap):
+    from paper_2103_02903_gb300.binding import flattened_weights, flattened_weights_s
+    level = 5
+    for k in (0, 1, 2, 9, 29, 30, 31):
+        a = flattened_weights(1, level, level + gap, periodic, k)
+        b = flattened_weights_s(1, 2, 1, level, level + gap, periodic, k)
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+@pytest.mark.parametrize("gap", [1, 2, 3])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_flattened_weights_s_match_oracle(lib, s, gap, periodic):
+    """The window weights reproduce, for every cell, the difference of the
+    finest edge values that the oracle's reconstruction (with the same s)
+    gives from a random uniform level: faces with constant extension, or the
+    periodic wrap."""
+    from oracle import Oracle
+    from paper_2103_02903_gb300 import workloads
+    from paper_2103_02903_gb300.binding import flattened_weights_s
+    level, w = 5, 2 * s
+    if periodic:
+        cfg, _ = workloads.advection_1d(max_level=level + gap, min_level=2)
+    else:
+        cfg, _ = workloads.burgers_1d(max_level=level + gap, min_level=2)
+    cfg["pred_s"] = s
+    n = 1 << level
+    rng = np.random.default_rng(7 * s + gap + 100 * periodic)
+    f = rng.standard_normal(n)
+    o = Oracle(cfg)
+    z = np.zeros(n, np.int32)
+    o.set_leaves(np.full(n, level, np.int32), np.arange(n, dtype=np.int32), z, z, np.stack([f, f]))
+    fine = o.reconstruct(cfg["max_level"])[0]
+    m = 1 << gap
+    for k in range(n):
+        wts = flattened_weights_s(s, w, 1, level, cfg["max_level"], periodic, k)
+        cells = [k + d for d in range(-w, w + 1)]
+        if periodic:
+            win = np.array([f[c % n] for c in cells])
+            r_km1, l_kp1 = fine[(m * k - 1) % (m * n)], fine[(m * (k + 1)) % (m * n)]
+        else:
+            win = np.array([f[c] if 0 <= c < n else 0.0 for c in cells])
+            r_km1 = fine[m * k - 1] if k > 0 else 0.0
+            l_kp1 = fine[m * (k + 1)] if k + 1 < n else 0.0
+        r_k, l_k = fine[m * (k + 1) - 1], fine[m * k]
+        assert abs(wts[: 2 * w + 1] @ win - (r_km1 - r_k)) < 1e-12
+        assert abs(wts[2 * w + 1:] @ win - (l_kp1 - l_k)) < 1e-12
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_flattened_weights_s_support_and_zero_sum(lib, s):
+    """The weights reach exactly 2s cells on either side once the gap is at
+    least s (a narrower window is refused), and for an interior cell they sum
+    to zero: a constant has no net flux."""
+    from paper_2103_02903_gb300.binding import MrError, flattened_weights_s
+    for gap in range(s, 9):
+        w = flattened_weights_s(s, 2 * s, 1, 6, 6 + gap, True, 10)
+        assert w[0] != 0.0 or w[4 * s] != 0.0 or w[4 * s + 1] != 0.0 or w[-1] != 0.0  # window ends
+        assert abs(w[: 4 * s + 1].sum()) < 1e-14 and abs(w[4 * s + 1:].sum()) < 1e-14
+        with pytest.raises(MrError):
+            flattened_weights_s(s, 2 * s - 1, 1, 6, 6 + gap, True, 10)
