@@ -16,6 +16,13 @@ storage (FP64 mesh decisions); the plain FP64 form is timed beside it
 and D2Q4^4 Riemann problems) stepped by shared launches against the same
 instances stepped one at a time in the plain form.
 
+Also on the line: the exact collision and the 3D ball (D3Q6) legs; the
+roofline of the transport + collision kernel (algorithmic bytes or flops over
+its live launch time, and the DRAM bytes of an ncu capture of it scaled to
+the timed launches); the CPU oracle on one core and on every host core (one
+process per core); and the end-to-end rate through the C-ABI with host
+buffers.
+
 Runs on N GPUs as N independent replicas (the single-instance step does not
 shard).  ``--impl reference`` times the CPU oracle on a bounded sample of
 the same workload on the host cores.
