@@ -110,7 +110,7 @@ typedef struct {
                             the cells of levels min_level..max_level number under 2^30 */
   int min_level, max_level; /* J_min and J; 2 <= J_min <= J <= 15 */
   double eps;            /* threshold epsilon >= 0, eps_j = 2^{d(j-J)} eps (Sec. 4.4) */
-  int mu_bar;            /* regularity guess of the refinement rule, >= 0 */
+  int mu_bar;            /* regularity guess of the refinement rule, 0 .. 2s+1 = 3 (Sec. 5.1) */
   int pred_s;            /* prediction stencil half-width; only 1 is supported */
   int bc[6];             /* mr_bc per face: -x, +x, -y, +y, -z, +z */
   int cross_sign;        /* +1: tensor-product prediction (default, also when 0);

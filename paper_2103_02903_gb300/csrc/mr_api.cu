@@ -252,6 +252,7 @@ mr_status validate(const mr_lbm_config* c) {
   if (c->obstacle && !(c->xmax[0] > c->xmin[0]) ) return MR_EINVAL;
   if (!(c->lambda > 0) || !(c->eps >= 0) || c->mu_bar < 0) return MR_EINVAL;
   if (c->pred_s != 0 && c->pred_s != 1) return MR_EINVAL;
+  if (c->mu_bar > 3) return MR_EINVAL;  // the regularity guess lies in [0, 2s + 1] (Sec. 5.1), s = 1
   if (c->precision < MR_FP64 || c->precision > MR_FP32_BF16STORE) return MR_EINVAL;
   if (c->min_level < 2 || c->max_level < c->min_level || c->max_level > 15) return MR_EINVAL;
   for (int i = 0; i < 16; ++i)

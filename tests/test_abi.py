@@ -65,6 +65,7 @@ def _bad(name):
         "lambda_zero": (W.advection_1d, dict(max_level=6), dict(lambda_=0.0)),
         "relaxation_above_2": (W.advection_1d, dict(max_level=6), dict(s=[2.5] + [0.0] * 15)),
         "mu_bar_negative": (W.advection_1d, dict(max_level=6), dict(mu_bar=-1)),
+        "mu_bar_above_order": (W.advection_1d, dict(max_level=6), dict(mu_bar=4)),
         "min_level_below_2": (W.advection_1d, dict(max_level=6), dict(min_level=1)),
         "max_below_min": (W.advection_1d, dict(max_level=6), dict(min_level=5, max_level=4)),
         "max_level_16": (W.advection_1d, dict(max_level=6), dict(max_level=16)),
@@ -88,7 +89,8 @@ def _bad(name):
 
 
 @pytest.mark.parametrize("name", [
-    "negative_eps", "lambda_zero", "relaxation_above_2", "mu_bar_negative", "min_level_below_2",
+    "negative_eps", "lambda_zero", "relaxation_above_2", "mu_bar_negative", "mu_bar_above_order",
+    "min_level_below_2",
     "max_below_min", "max_level_16", "prediction_s2_on_gpu", "half_periodic_axis", "obstacle_not_d2q9",
     "moving_wall_not_d2q9", "printed_sign_d2q9", "exact_collision_fp16", "exact_collision_3d",
     "d3q6_level_11", "d3q6_dense_space", "d2_dense_space", "roots_overflow_codes"])
