@@ -167,8 +167,9 @@ mr_status mr_lbm_project(mr_lbm_t h, int level, double* out, int on_device);
 /* Same result as mr_lbm_project, for callers that must not allocate memory
  * during the call (the paper has no counterpart: this is a deployment aid).
  * mr_lbm_project allocates its two dense level buffers on first use; a caller
- * that is queueing work while a stream is captured into a CUDA graph, or
- * whose device memory belongs to another allocator with a fixed budget,
+ * whose device memory belongs to another allocator with a fixed budget (a
+ * framework's caching allocator, a memory pool), or a serving loop that
+ * cannot afford the device-wide synchronisation an allocation may cause,
  * cannot let that happen.  This variant calls no cudaMalloc, cudaFree or
  * allocating library routine: its level buffers live in one file-scope
  * device array of 2^21 doubles (16 MiB) that each GPU loading the library

@@ -20,7 +20,11 @@
  * under tests/ (prediction: Table 1, Appendix 2, polynomial exactness,
  * consistency Eq. ConsistencyPrediction; details: Eq. DetailRedundancy;
  * step: epsilon = 0 reduces to Eq. StreamFinest; conservation; Eq.
- * PredictionWithMatrix; brute-force minimal grading; the exact collision:
+ * PredictionWithMatrix; brute-force minimal grading; the group norms of
+ * the details and the T / H / G decisions in 2D and 3D against a numpy
+ * restatement of the set definitions, and the obstacle penalisation
+ * against integer lattice counts and the rest equilibrium, in
+ * tests/test_oracle_obstacle_and_decisions.py; the exact collision:
  * linear equilibria, finest leaves, mass, closed-form D1Q2 composition in
  * tests/test_oracle_exact_collision.py; the prediction of half-width s = 2,
  * 3 and the grading it widens: Appendix 2 coefficients, exactness to degree
@@ -572,6 +576,9 @@ or_state* or_create(const or_config* cfg) {
   if (S->Jmin < 0 || S->J >= MAXL || S->Jmin > S->J) { free(S); return NULL; }
   S->s_pred = cfg->pred_s == 0 ? 1 : cfg->pred_s;
   if (S->s_pred < 1 || S->s_pred > 3) { free(S); return NULL; }
+  /* Sec. 5.1: the regularity guess mu_bar of the refinement rule lies in
+   * [0, 2s + 1], the order of the prediction operator */
+  if (cfg->mu_bar < 0 || cfg->mu_bar > 2 * S->s_pred + 1) { free(S); return NULL; }
   for (int l = S->Jmin; l <= S->J; ++l) {
     long long tot = 1;
     for (int a = 0; a < 3; ++a) {

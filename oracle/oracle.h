@@ -41,7 +41,8 @@ typedef struct {
   int roots[3];        /* cells per axis at level 0 */
   int min_level, max_level;
   double eps;          /* threshold epsilon of Eq. Thresholding */
-  int mu_bar;          /* regularity guess of the refinement rule */
+  int mu_bar;          /* regularity guess of the refinement rule, in [0, 2s + 1] (Sec. 5.1);
+                          or_create refuses other values */
   int bc[6];           /* -x,+x,-y,+y,-z,+z */
   int cross_sign;      /* +1 tensor-product prediction, -1 diagonal term as printed */
   int obstacle;        /* 1: volume-fraction penalisation after collision (Sec. 7.2) */

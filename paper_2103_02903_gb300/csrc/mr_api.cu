@@ -252,7 +252,8 @@ mr_status validate(const mr_lbm_config* c) {
   if (c->obstacle && !(c->xmax[0] > c->xmin[0]) ) return MR_EINVAL;
   if (!(c->lambda > 0) || !(c->eps >= 0) || c->mu_bar < 0) return MR_EINVAL;
   if (c->pred_s != 0 && c->pred_s != 1) return MR_EINVAL;
-  if (c->mu_bar > 3) return MR_EINVAL;  // the regularity guess lies in [0, 2s + 1] (Sec. 5.1), s = 1
+  const int s_pred = c->pred_s ? c->pred_s : 1;
+  if (c->mu_bar > 2 * s_pred + 1) return MR_EINVAL;  // the regularity guess lies in [0, 2s + 1] (Sec. 5.1)
   if (c->precision < MR_FP64 || c->precision > MR_FP32_BF16STORE) return MR_EINVAL;
   if (c->min_level < 2 || c->max_level < c->min_level || c->max_level > 15) return MR_EINVAL;
   for (int i = 0; i < 16; ++i)
@@ -1001,6 +1002,12 @@ mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* k
   const signed char* dl = levels;
   const double* df = f;
   bool up = false;  // populations in flight on up_st
+  // error returns: the caller's host buffers are free on return, so wait for
+  // the population upload to finish (after which nothing reads them)
+  auto release = [&]() {
+    if (up) cudaStreamSynchronize(h->up_st);
+    up = false;
+  };
   if (!on_device) {
     const size_t bk = n * sizeof(unsigned long long), bl = (n + 255) / 256 * 256, bf = (size_t)g.Q * n * sizeof(double);
     if (ensure_staging(h, bk + bl + bf) != MR_OK) return h->sticky;
@@ -1013,39 +1020,50 @@ mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* k
     // the handle stream's earlier work (which may still read the staging
     // buffer), while the keys are checked and the mesh is built
     if (!cuda_ok(h, cudaEventRecord(h->ev_prior, h->st)) ||
-        !cuda_ok(h, cudaStreamWaitEvent(h->up_st, h->ev_prior, 0)) ||
-        !cuda_ok(h, cudaMemcpyAsync(sp + bk + bl, f, bf, cudaMemcpyHostToDevice, h->up_st)) ||
-        !cuda_ok(h, cudaEventRecord(h->ev_up, h->up_st)))
+        !cuda_ok(h, cudaStreamWaitEvent(h->up_st, h->ev_prior, 0)))
       return MR_ECUDA;
+    if (!cuda_ok(h, cudaMemcpyAsync(sp + bk + bl, f, bf, cudaMemcpyHostToDevice, h->up_st))) return MR_ECUDA;
     up = true;
-    if (!cuda_ok(h, cudaMemcpyAsync(sp, keys, bk, cudaMemcpyHostToDevice, h->st)) ||
-        !cuda_ok(h, cudaMemcpyAsync(sp + bk, levels, n, cudaMemcpyHostToDevice, h->st)))
+    if (!cuda_ok(h, cudaEventRecord(h->ev_up, h->up_st))) {
+      release();
       return MR_ECUDA;
+    }
+    if (!cuda_ok(h, cudaMemcpyAsync(sp, keys, bk, cudaMemcpyHostToDevice, h->st)) ||
+        !cuda_ok(h, cudaMemcpyAsync(sp + bk, levels, n, cudaMemcpyHostToDevice, h->st))) {
+      release();
+      return MR_ECUDA;
+    }
     dk = (const unsigned long long*)sp;
     dl = (const signed char*)(sp + bk);
     df = (const double*)(sp + bk + bl);
   }
-  // every return below leaves the handle's stream ordered after the upload
+  // the success path orders the handle's stream after the upload
   auto join = [&]() {
     if (up) cudaStreamWaitEvent(h->st, h->ev_up, 0);
     up = false;
   };
   MeshDev& B = h->mesh[h->cur];
-  if (!cuda_ok(h, cudaMemsetAsync(h->vol, 0, sizeof(unsigned long long), h->st))) return MR_ECUDA;
+  if (!cuda_ok(h, cudaMemsetAsync(h->vol, 0, sizeof(unsigned long long), h->st))) {
+    release();
+    return MR_ECUDA;
+  }
   mr_launch_leaves_in(g, n, dk, dl, h->inidx, h->cls, B.cnt, h->vol, h->st, grid_for(h));
   mr_launch_leaves_check(g, h->cls, B.cnt, h->st, grid_for(h));
   count_launch(h, 2);
   unsigned long long vol = 0;
-  if (!cuda_ok(h, cudaMemcpyAsync(&vol, h->vol, sizeof(vol), cudaMemcpyDeviceToHost, h->st))) return MR_ECUDA;
+  if (!cuda_ok(h, cudaMemcpyAsync(&vol, h->vol, sizeof(vol), cudaMemcpyDeviceToHost, h->st))) {
+    release();
+    return MR_ECUDA;
+  }
   MeshCounts hc[2];
   mr_status s = read_counts(h, hc);
   if (s != MR_OK) {
-    join();
+    release();
     return s;
   }
   unsigned long long full = g.ncode[g.J];
   if (vol != full) {
-    join();
+    release();
     return fail(h, MR_EINVAL);
   }
   run_build(*h, h->grp, h->cur);

@@ -3,13 +3,14 @@
 //
 // mr_lbm_project allocates its two dense level buffers with cudaMalloc the
 // first time it is called on a handle.  Some callers cannot allocate at that
-// point: code that queues work while a stream is being captured into a CUDA
-// graph (an allocation there is not allowed), or a process whose device
-// memory is owned by another allocator (a framework caching allocator, a
-// memory pool with a hard budget) and must not see a foreign cudaMalloc in
-// the middle of a run.  This entry point uses instead one file-scope device
-// array of fixed size, MR_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB), that
-// every GPU which loads the library holds until the process exits.
+// point: a process whose device memory is owned by another allocator (a
+// framework's caching allocator, a memory pool with a hard budget) that must
+// not see a foreign cudaMalloc in the middle of a run, or a serving loop on
+// a shared GPU that cannot afford the device-wide synchronisation that
+// allocating and freeing device memory may cause.  This entry point uses
+// instead one file-scope device array of fixed size,
+// MR_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB), that every GPU which loads
+// the library holds until the process exits.
 //
 // Set-up: the first call on each device, with that device current, looks up
 // the device address of the array with cudaGetSymbolAddress (in host code the

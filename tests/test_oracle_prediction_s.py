@@ -223,3 +223,17 @@ def test_epsilon_zero_does_not_see_the_stencil_width():
         runs.append(o.leaves())
     for r in runs[1:]:
         assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_regularity_guess_bounded_by_the_order(s):
+    """Sec. 5.1 takes the regularity guess mu_bar of the refinement rule in
+    [0, 2s + 1], the order of the prediction: the oracle accepts the ends of
+    that range and refuses the values just outside it."""
+    cfg, _ = W.advection_1d(seed=0, max_level=5)
+    cfg["pred_s"] = s
+    for mu in (0, 2 * s + 1):
+        Oracle(dict(cfg, mu_bar=mu))
+    for mu in (-1, 2 * s + 2):
+        with pytest.raises(RuntimeError):
+            Oracle(dict(cfg, mu_bar=mu))

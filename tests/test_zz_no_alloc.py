@@ -1,8 +1,9 @@
 """mr_lbm_project_noalloc against mr_lbm_project, through the C-ABI.
 
 The allocation-free variant exists for callers that cannot let the library
-call cudaMalloc during a call (stream capture into a CUDA graph in progress,
-or device memory owned by another allocator with a fixed budget).  It keeps
+call cudaMalloc during a call (device memory owned by another allocator with
+a fixed budget, or a serving loop that cannot afford the device-wide
+synchronisation an allocation may cause).  It keeps
 its level buffers in a fixed 16 MiB file-scope device array instead.  Two
 calls in a row, at different levels so that the second one reuses the
 first one's leftover contents, must reproduce the allocating entry point
