@@ -6,9 +6,14 @@ in FP32; the details that decide the mesh stay FP64.  The error reported is
 the relative L1 distance of each conserved moment, reconstructed on the
 finest level, to the FP64 oracle after the same number of steps (the
 additional-error measure of Sec. 7.1.3, with the oracle as reference).
-Bounds: FP32 <= 1e-5; FP16 storage <= 1e-3; BF16 storage <= 2e-2 (its 8-bit
-significand gives 2^-9 per stored value; the 35-step advection of a step
-function measured 1.4e-2).
+Bounds: FP32 <= 1e-5 and FP16 storage <= 1e-3, the accuracies the forms are
+required to reach.  BF16 storage does not reach the 1e-3 of 16-bit storage:
+its 8-bit significand gives 2^-9 per stored value, and the 35-step advection
+of a step function measured 1.4e-2.  Its bound here, 2e-2, only guards the
+measured level against regressions; BF16 is reported as failing 1e-3.
+
+The D1Q2 Burgers and D1Q3 dam-break cases also run at their full size
+(J = 12, 4096 finest cells) to the final time T = 0.4 (2458 steps).
 """
 import numpy as np
 import pytest
@@ -18,7 +23,8 @@ from paper_2103_02903_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-BOUND = {"fp32": 1e-5, "fp16": 1e-3, "bf16": 2e-2}
+BOUND = {"fp32": 1e-5, "fp16": 1e-3}
+BF16_REGRESSION_BOUND = 2e-2  # BF16 storage fails the 1e-3 of 16-bit storage (measured 1.4e-2)
 
 
 def _l1(a, b):
@@ -45,6 +51,25 @@ def test_form_error_vs_fp64_oracle(form, name, kw, steps):
     J = cfg["max_level"]
     err = _l1(gpu.project(J), ref.project(J))
     print("%s %s: L1 error %.3e, leaves gpu %d oracle %d" % (name, form, err, gpu.num_leaves(), ref.num_leaves()))
+    assert err <= BOUND.get(form, BF16_REGRESSION_BOUND)
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16"])
+@pytest.mark.parametrize("name", ["burgers_1d", "shallow_water_1d"])
+def test_form_error_full_size_to_final_time(form, name):
+    """D1Q2 Burgers / D1Q3 dam break at J = 12 to T = 0.4 (2458 steps)."""
+    from paper_2103_02903_gb300.binding import Solver
+    cfg, u = W.WORKLOADS[name](seed=0, max_level=12)
+    n = W.steps_to(cfg, 0.4)
+    assert n == 2458
+    ref = Oracle(cfg)
+    ref.init(u)
+    ref.step(n)
+    gpu = Solver(dict(cfg, precision=form))
+    gpu.init(u)
+    gpu.step(n)
+    err = _l1(gpu.project(12), ref.project(12))
+    print("%s %s J12 T=0.4: L1 error %.3e" % (name, form, err))
     assert err <= BOUND[form]
 
 

@@ -1,0 +1,161 @@
+"""Parity with the oracle at the sizes the benchmark runs, FP64 form.
+
+The smaller parity tests cover every scheme, boundary kind and edge case;
+these run the configurations of the measured workloads themselves, where the
+level gaps are largest (deep flattened windows, critical cases over many
+levels) and the oracle still finishes within a couple of minutes:
+
+- D2Q4^4 Euler at J = 10 (1024^2 finest cells), 50 steps, each step started
+  from the oracle's state (so the mesh decisions must agree bit for bit);
+- the same problem at J = 8 along independent trajectories to T = 0.25
+  (320 steps of Algorithm 1's loop);
+- D2Q9 flow past the obstacle at J = 10 (2048 x 1024) for a few steps from
+  the oracle's state, and at J = 8 for 120 steps along trajectories;
+- D3Q6 ball advection at J = 7 (128^3) for a few steps;
+- the exact collision (Eq. sourceoferror) at J = 10.
+
+Leaf sets bit-exact, populations within 1e-12 of each population field's
+max norm.  Along independent trajectories a keep / refine decision can
+differ only when a group norm lies within rounding of its threshold: such a
+step is accepted only if the oracle's smallest relative decision margin of
+that step is below 1e-10, and the GPU then restarts from the oracle's state
+(at most twice per trajectory).
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2103_02903_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+NEAR_TIE = 1e-10
+
+
+def _solver(cfg):
+    from paper_2103_02903_gb300.binding import Solver
+    return Solver(cfg)
+
+
+def _dim(cfg):
+    return W.DIM[cfg["scheme"]]
+
+
+def _load(gpu, ref, cfg):
+    from paper_2103_02903_gb300.binding import encode_keys, encode_keys3
+    lev, ix, iy, iz, f = ref.leaves()
+    keys = encode_keys3(cfg, lev, ix, iy, iz) if _dim(cfg) == 3 else encode_keys(cfg, lev, ix, iy)
+    gpu.set_leaves(keys, lev.astype(np.int8), f)
+
+
+def _gpu_sorted(gpu, cfg):
+    from paper_2103_02903_gb300.binding import decode_keys, decode_keys3
+    keys, lev, f = gpu.get_leaves()
+    if _dim(cfg) == 3:
+        x, y, z = decode_keys3(cfg, lev, keys)
+    else:
+        x, y = decode_keys(cfg, lev, keys)
+        z = np.zeros_like(x)
+    order = np.lexsort((x, y, z, lev))
+    return lev[order].astype(np.int64), x[order], y[order], z[order], f[:, order]
+
+
+def _same_leaves(gpu, ref, cfg):
+    glev, gx, gy, gz, gf = _gpu_sorted(gpu, cfg)
+    lev, ix, iy, iz, f = ref.leaves()
+    same = (len(glev) == len(lev) and (glev == lev).all() and (gx == ix).all() and (gy == iy).all()
+            and (gz == iz).all())
+    return same, gf, f
+
+
+def _check(gpu, ref, cfg, what):
+    same, gf, f = _same_leaves(gpu, ref, cfg)
+    if not same:
+        pytest.fail("%s: leaf sets differ (oracle margin %.3e)" % (what, ref.margin()))
+    scale = np.maximum(np.abs(f).max(axis=1, keepdims=True), 1e-300)
+    err = float((np.abs(gf - f) / scale).max())
+    assert err <= TOL, "%s: populations differ by %.3e (max-norm relative)" % (what, err)
+    return err
+
+
+def _per_step(cfg, u, steps, what):
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    levels = set()
+    for it in range(steps):
+        if it:
+            _load(gpu, ref, cfg)
+        gpu.step(1)
+        ref.step(1)
+        _check(gpu, ref, cfg, "%s step %d" % (what, it))
+        levels |= set(ref.leaves()[0].tolist())
+    gpu.close()
+    return levels
+
+
+def _trajectory(cfg, u, steps, what):
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    restarts = []
+    worst = 0.0
+    for it in range(steps):
+        gpu.step(1)
+        ref.step(1)
+        same, _, _ = _same_leaves(gpu, ref, cfg)
+        if not same:
+            m = ref.margin()
+            if m >= NEAR_TIE or len(restarts) >= 2:
+                pytest.fail("%s step %d: leaf sets differ with oracle decision margin %.3e" % (what, it, m))
+            restarts.append((it, m))
+            _load(gpu, ref, cfg)
+            continue
+        worst = max(worst, _check(gpu, ref, cfg, "%s step %d" % (what, it)))
+    gpu.close()
+    return restarts, worst
+
+
+def test_euler_J10_fifty_steps_from_the_oracle_state():
+    """The benchmarked configuration (D2Q4^4 Euler, J = 10, eps = 1e-3)."""
+    cfg, u = W.euler_2d(seed=0, max_level=10)
+    levels = _per_step(cfg, u, 50, "euler J10")
+    assert len(levels) >= 5
+
+
+def test_euler_J8_trajectory_to_final_time():
+    cfg, u = W.euler_2d(seed=1, max_level=8)
+    n = W.steps_to(cfg, 0.25)
+    assert n == 320
+    restarts, worst = _trajectory(cfg, u, n, "euler J8")
+    assert len(restarts) <= 2
+
+
+def test_ns_obstacle_J10_steps_from_the_oracle_state():
+    """Config of the D2Q9 leg: [0, 2] x [0, 1], 2048 x 1024 finest cells,
+    moving-wall bounce back, the obstacle penalised after each collision."""
+    cfg, u = W.ns_obstacle_2d(seed=0, max_level=10)
+    levels = _per_step(cfg, u, 4, "ns obstacle J10")
+    assert len(levels) >= 3
+
+
+def test_ns_obstacle_J8_trajectory_120_steps():
+    cfg, u = W.ns_obstacle_2d(seed=2, max_level=8)
+    restarts, worst = _trajectory(cfg, u, 120, "ns obstacle J8")
+    assert len(restarts) <= 2
+
+
+def test_d3q6_J7_steps_from_the_oracle_state():
+    cfg, u = W.advection_3d(seed=0, max_level=7)
+    levels = _per_step(cfg, u, 3, "d3q6 J7")
+    assert len(levels) >= 3
+
+
+def test_exact_collision_J10_steps_from_the_oracle_state():
+    cfg, u = W.euler_2d(seed=2, max_level=10)
+    cfg["exact_collision"] = 1
+    levels = _per_step(cfg, u, 3, "exact collision euler J10")
+    assert len(levels) >= 3
