@@ -23,7 +23,8 @@ FP16 and BF16 storage) is timed on the same window, and its relative L1
 distance to the FP64 run at the end of the window is reported against its
 bound.
 
-Also on the line: the exact collision and the 3D ball (D3Q6) legs; the
+Also on the line: the exact collision, the prediction of half-width s = 2
+and 3 ("prediction_s") and the 3D ball (D3Q6) legs; the
 other configurations ("configs": D1Q2 advection at J = 9 in microseconds
 per step, D1Q2 Burgers and D1Q3 dam break at J = 12 per form with their L1
 distance at T = 0.4, the D2Q9 obstacle flow at J = 10 and the time of its
@@ -122,6 +123,8 @@ def _args():
                    help="forward steps of the timed adjoint run (D2Q9 obstacle, J=10); 0 skips it")
     p.add_argument("--adjoint-every", type=int, default=100, help="checkpoint interval of the adjoint run")
     p.add_argument("--legs-only", action="store_true", help="run only the configuration legs")
+    p.add_argument("--wide-leg", type=int, default=1,
+                   help="also time the headline workload with the prediction of half-width s = 2 and 3 (1) or not")
     return p.parse_args()
 
 
@@ -578,6 +581,20 @@ def run_ours(args):
         s3.close()
         return out
 
+    def wide_leg():
+        """The same workload and window with the prediction of half-width s = 2
+        and 3 (Table 1): wider stencils, grading and transport windows."""
+        out = {"workload": WORKLOAD + " with pred_s = 2, 3", "unit": UNIT, "steps": args.steps}
+        for sw in (2, 3):
+            for fm in ("fp64", "fp16"):
+                s5, r5 = timed_run(fm, extra={"pred_s": sw})
+                out["s%d_%s" % (sw, fm)] = {"value": r5["updates"] / r5["total_s"],
+                                            "ms_per_step": 1e3 * r5["total_s"] / args.steps,
+                                            "leaves_per_step_avg": r5["updates"] / args.steps,
+                                            "launches_per_step": r5["launches"] / args.steps}
+                s5.close()
+        return out
+
     def d3_leg():
         """The 3D test of Sec. 7.3: D3Q6 advection of a ball, J = 8 (256^3), eps = 1e-3, mu_bar = 2."""
         from paper_2103_02903_gb300 import workloads
@@ -666,6 +683,7 @@ def run_ours(args):
     exact = exact_leg(forms["fp64"]["ms_per_step"]) if args.exact_steps > 0 else None
     legs = run_config_legs(args, stream, flush) if args.config_legs else None
     d3 = d3_leg() if args.d3_steps > 0 else None
+    wide = wide_leg() if args.wide_leg else None
 
     serving = run_serving(args, stream, flush, local) if args.serving_n > 0 else None
 
@@ -798,6 +816,8 @@ def run_ours(args):
             line["exact_collision"] = exact
         if d3 is not None:
             line["d3q6_3d"] = d3
+        if wide is not None:
+            line["prediction_s"] = wide
         if serving is not None:
             line["batched"] = serving
         if legs is not None:

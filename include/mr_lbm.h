@@ -110,8 +110,11 @@ typedef struct {
                             the cells of levels min_level..max_level number under 2^30 */
   int min_level, max_level; /* J_min and J; 2 <= J_min <= J <= 15 */
   double eps;            /* threshold epsilon >= 0, eps_j = 2^{d(j-J)} eps (Sec. 4.4) */
-  int mu_bar;            /* regularity guess of the refinement rule, 0 .. 2s+1 = 3 (Sec. 5.1) */
-  int pred_s;            /* prediction stencil half-width; only 1 is supported */
+  int mu_bar;            /* regularity guess of the refinement rule, 0 .. 2s + 1 (Sec. 5.1) */
+  int pred_s;            /* half-width s of the prediction operator, 1, 2 or 3 (Table 1; 0
+                            reads as 1): (2s+1)^d stencils, grading of radius s, transport
+                            windows of 2s cells.  s = 2, 3: not with D2Q9 (MR_D2Q9_NS) or
+                            the exact collision (MR_EINVAL); mr_lbm_adjoint needs s = 1 */
   int bc[6];             /* mr_bc per face: -x, +x, -y, +y, -z, +z */
   int cross_sign;        /* +1: tensor-product prediction (default, also when 0);
                             -1: diagonal term with the sign printed in Sec. 4.1 */

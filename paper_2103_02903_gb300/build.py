@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmrlbm.so")
 SOURCES = ["mr_api.cu", "mr_encode.cu", "mr_mesh.cu", "mr_stream.cu", "mr_noalloc.cu", "mr_adjoint.cu",
-           "mr_exact.cu"]
+           "mr_exact.cu", "mr_wide.cu"]
 HEADERS = ["mr_internal.cuh", "mr_common.cuh", "mr_handle.cuh", "mr_schemes.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -152,6 +152,87 @@ bool axis_weights(int N, int gap, bool periodic, int k, double* out) {
   return true;
 }
 
+// The same four tables for the prediction of half-width s = 2, 3, over the
+// window delta = -W..W (W = 2s) of the slot layout of mr_slot_w:
+// out[t * (2W + 1) + delta + W], t as in axis_weights.
+// Table 1: c_1 .. c_s of the prediction of half-width s.
+const double kPredCoef[4][3] = {
+    {0.0, 0.0, 0.0},
+    {-1.0 / 8.0, 0.0, 0.0},
+    {-22.0 / 128.0, 3.0 / 128.0, 0.0},
+    {-201.0 / 1024.0, 11.0 / 256.0, -5.0 / 1024.0},
+};
+
+// One-dimensional reconstruction with the prediction of half-width s applied
+// `gap` times to a level field of N cells, constant extension outside.
+void recon1d_s(std::vector<double>& cur, int N, int gap, int s) {
+  for (int it = 0; it < gap; ++it) {
+    std::vector<double> nxt(2 * (size_t)N);
+    auto at = [&](int i) { return cur[std::min(std::max(i, 0), N - 1)]; };
+    for (int k = 0; k < N; ++k) {
+      double q = 0.0;
+      for (int a = 1; a <= s; ++a) q += kPredCoef[s][a - 1] * (at(k + a) - at(k - a));
+      nxt[2 * k] = cur[k] + q;
+      nxt[2 * k + 1] = cur[k] - q;
+    }
+    cur.swap(nxt);
+    N *= 2;
+  }
+}
+
+void axis_weights_w(int N, int gap, bool periodic, int k, int s, int W, double* out) {
+  const int NW = 2 * W + 1;
+  int Nsim = N, ks = k;
+  if (periodic) {  // interior weights, computed away from any face of the patch
+    Nsim = 4 * W + 5;
+    ks = 2 * W + 2;
+  }
+  const size_t n = (size_t)1 << gap;
+  for (int dl = -W; dl <= W; ++dl) {
+    const int i = ks + dl;
+    double r0 = 0, r1 = 0, l0 = 0, l1 = 0;
+    if (i >= 0 && i < Nsim) {  // outside a non-periodic domain the kernel reads nothing: weight 0
+      std::vector<double> f(Nsim, 0.0);
+      f[i] = 1.0;
+      recon1d_s(f, Nsim, gap, s);
+      if (ks >= 1) r0 = f[n * ks - 1];
+      r1 = f[n * (ks + 1) - 1];
+      l0 = f[n * ks];
+      if (ks + 1 < Nsim) l1 = f[n * (ks + 1)];
+    }
+    out[0 * NW + dl + W] = r0 - r1;
+    out[1 * NW + dl + W] = l1 - l0;
+    out[2 * NW + dl + W] = r1;
+    out[3 * NW + dl + W] = l0;
+  }
+}
+
+void build_tables_w(const Geo& g, std::vector<double>& Ws) {
+  const int W = 2 * g.s_pred, NW = 2 * W + 1;
+  Ws.assign((size_t)MR_WWIDX(g.J + 1, 0, 0, 0, W), 0.0);
+  std::vector<double> w(4 * NW);
+  for (int l = g.Jmin; l <= g.J; ++l)
+    for (int a = 0; a < g.d; ++a) {
+      const int N = g.n[l][a];
+      const bool per = g.periodic[a] != 0;
+      std::vector<int> ks;
+      if (per) {
+        ks.push_back(0);
+      } else if (N <= NW) {
+        for (int k = 0; k < N; ++k) ks.push_back(k);
+      } else {
+        for (int k = 0; k <= W; ++k) ks.push_back(k);
+        for (int k = N - W; k < N; ++k) ks.push_back(k);
+      }
+      for (int k : ks) {
+        const int sl = mr_slot_w(k, N, per, W);
+        axis_weights_w(N, g.J - l, per, k, g.s_pred, W, w.data());
+        for (int t = 0; t < MR_NTAB; ++t)
+          for (int e = 0; e < NW; ++e) Ws[MR_WWIDX(l, a, sl, t, W) + e] = w[t * NW + e];
+      }
+    }
+}
+
 void build_tables(const Geo& g, std::vector<double>& W) {
   W.assign((size_t)(g.J + 1) * 3 * MR_NSLOT * MR_NTAB * 5, 0.0);
   for (int l = g.Jmin; l <= g.J; ++l)
@@ -251,8 +332,11 @@ mr_status validate(const mr_lbm_config* c) {
     if (c->bc[f] == MR_BC_BOUNCE_BACK_VELOCITY && c->scheme != MR_D2Q9_NS) return MR_EINVAL;
   if (c->obstacle && !(c->xmax[0] > c->xmin[0]) ) return MR_EINVAL;
   if (!(c->lambda > 0) || !(c->eps >= 0) || c->mu_bar < 0) return MR_EINVAL;
-  if (c->pred_s != 0 && c->pred_s != 1) return MR_EINVAL;
+  if (c->pred_s < 0 || c->pred_s > 3) return MR_EINVAL;
   const int s_pred = c->pred_s ? c->pred_s : 1;
+  // s = 2, 3: lattices with axis velocities and the leaf collision (the
+  // diagonal-velocity transport and the exact collision are built for s = 1)
+  if (s_pred > 1 && (c->scheme == MR_D2Q9_NS || c->exact_collision)) return MR_EINVAL;
   if (c->mu_bar > 2 * s_pred + 1) return MR_EINVAL;  // the regularity guess lies in [0, 2s + 1] (Sec. 5.1)
   if (c->precision < MR_FP64 || c->precision > MR_FP32_BF16STORE) return MR_EINVAL;
   if (c->min_level < 2 || c->max_level < c->min_level || c->max_level > 15) return MR_EINVAL;
@@ -303,6 +387,8 @@ void fill_desc(const mr_lbm* h, InstDev& d) {
   d.bcounts = h->bcounts;
   d.W = h->W;
   d.Wf = h->Wf;
+  d.Ws = h->Ws;
+  d.Wsf = h->Wsf;
   auto& k = d.g.f32;  // FP32 copies for the FP32 arithmetic of the forms
   k.lambda = (float)d.g.lambda;
   k.inv_lambda = (float)d.g.inv_lambda;
@@ -337,6 +423,7 @@ bool make_group(Group& G, const std::vector<const mr_lbm*>& members, const InstD
   G.Q = g0.Q;
   G.scheme = g0.scheme;
   G.form = g0.form;
+  G.s = g0.s_pred;
   std::vector<int> pre(G.n + 1, 0);
   for (int b = 0; b < G.n; ++b) {
     const Geo& g = members[b]->g;
@@ -594,31 +681,6 @@ mr_status mr_lbm_flattened_weights(int roots, int level, int max_level, int peri
   return MR_OK;
 }
 
-// Table 1: c_1 .. c_s of the prediction of half-width s.
-const double kPredCoef[4][3] = {
-    {0.0, 0.0, 0.0},
-    {-1.0 / 8.0, 0.0, 0.0},
-    {-22.0 / 128.0, 3.0 / 128.0, 0.0},
-    {-201.0 / 1024.0, 11.0 / 256.0, -5.0 / 1024.0},
-};
-
-// One-dimensional reconstruction with the prediction of half-width s applied
-// `gap` times to a level field of N cells, constant extension outside.
-void recon1d_s(std::vector<double>& cur, int N, int gap, int s) {
-  for (int it = 0; it < gap; ++it) {
-    std::vector<double> nxt(2 * (size_t)N);
-    auto at = [&](int i) { return cur[std::min(std::max(i, 0), N - 1)]; };
-    for (int k = 0; k < N; ++k) {
-      double q = 0.0;
-      for (int a = 1; a <= s; ++a) q += kPredCoef[s][a - 1] * (at(k + a) - at(k - a));
-      nxt[2 * k] = cur[k] + q;
-      nxt[2 * k + 1] = cur[k] - q;
-    }
-    cur.swap(nxt);
-    N *= 2;
-  }
-}
-
 mr_status mr_lbm_flattened_weights_s(int s, int half_width, int roots, int level, int max_level, int periodic,
                                      int k, double* out) {
   if (!out || s < 1 || s > 3 || half_width < 1 || half_width > 16 || roots < 1 || level < 0 ||
@@ -711,6 +773,7 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   g.eps = cfg->eps;
   g.mu_bar = cfg->mu_bar;
   g.cross_sign = cfg->cross_sign == -1 ? -1 : 1;
+  g.s_pred = cfg->pred_s ? cfg->pred_s : 1;
   g.form = cfg->precision;  // MR_FP64 .. MR_FP32_BF16STORE map onto MR_FORM_F64 .. MR_FORM_F32_BF16
   for (int p = 0; p < MR_MAXQ; ++p) g.off[p] = g.feq0[p] = g.bcv[p] = 0.0;
   g.diag = g.scheme == MR_D2Q9_NS;
@@ -769,6 +832,12 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   build_tables(g, W);
   ok = ok && dalloc(h, &h->W, W.size()) && dalloc(h, &h->Wf, W.size());
   std::vector<float> Wf(W.begin(), W.end());
+  std::vector<double> Ws;
+  if (g.s_pred > 1) {
+    build_tables_w(g, Ws);
+    ok = ok && dalloc(h, &h->Ws, Ws.size()) && dalloc(h, &h->Wsf, Ws.size());
+  }
+  std::vector<float> Wsf(Ws.begin(), Ws.end());
   int* dchunk = nullptr;
   ok = ok && dalloc(h, &h->dinst, 1) && dalloc(h, &dchunk, 2);
   if (!ok) {
@@ -796,6 +865,10 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
                  cudaSuccess &&
              cudaMemcpyAsync(h->W, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, h->st) ==
                  cudaSuccess &&
+             (Ws.empty() || (cudaMemcpyAsync(h->Ws, Ws.data(), Ws.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                             h->st) == cudaSuccess &&
+                             cudaMemcpyAsync(h->Wsf, Wsf.data(), Wsf.size() * sizeof(float),
+                                             cudaMemcpyHostToDevice, h->st) == cudaSuccess)) &&
              cudaStreamSynchronize(h->st) == cudaSuccess;
   if (!cok) {
     mr_lbm_destroy(h);
@@ -1218,7 +1291,7 @@ mr_status mr_lbm_adjoint(mr_lbm_t h, const double* conserved0, int on_device, in
   if (h->sticky != MR_OK) return h->sticky;
   if (h->batch) return MR_ESTATE;
   const Geo& g = h->g;
-  if (g.form != MR_FORM_F64 || h->grp.exact || g.d == 3) return MR_EINVAL;  // 1D and 2D, the leaf collision
+  if (g.form != MR_FORM_F64 || h->grp.exact || g.d == 3 || g.s_pred > 1) return MR_EINVAL;  // 1D and 2D, the leaf collision
   AdjArena ar;
   const size_t NJ = g.ncode[g.J], ncb = (size_t)g.ncons * NJ;
   // the initial field, kept on the device for the equilibrium's adjoint
@@ -1412,7 +1485,7 @@ mr_status mr_lbm_batch_create(const mr_lbm_config* cfgs, int n, void* cuda_strea
   // parts: instances of one scheme and storage form, at most MR_MAXB each
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
-  auto key = [&](int i) { return b->inst[i]->g.scheme * 16 + b->inst[i]->g.form; };
+  auto key = [&](int i) { return (b->inst[i]->g.s_pred * 16 + b->inst[i]->g.scheme) * 16 + b->inst[i]->g.form; };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
   if (cudaMalloc(&b->descs, sizeof(InstDev) * n) != cudaSuccess) {
     free_batch(b);

@@ -264,4 +264,7 @@ void mr_launch_project(const Group& G, int cur, int k, cudaStream_t st) {
   MR_DISPATCH_DQF(launch_project_t, G, cur, k, st);
 }
 
-void mr_launch_details(const Group& G, int cur, cudaStream_t st) { MR_DISPATCH_DQF(launch_details_t, G, cur, st); }
+void mr_launch_details(const Group& G, int cur, cudaStream_t st) {
+  if (G.s > 1) return mr_launch_details_w(G, cur, st);
+  MR_DISPATCH_DQF(launch_details_t, G, cur, st);
+}

@@ -51,6 +51,8 @@ struct mr_lbm : Exec {
   unsigned long long* vol = nullptr;
   double* W = nullptr;
   float* Wf = nullptr;
+  double* Ws = nullptr;  // s = 2, 3: flattened weights of half-width 2s
+  float* Wsf = nullptr;
   double* dense[2] = {nullptr, nullptr};
   size_t dense_elems = 0;
   void* staging = nullptr;

@@ -60,6 +60,7 @@ struct Geo {
   double consw[4][MR_MAXQ];    // conserved moments as linear forms of the populations
   int form;                    // storage / compute form, see MR_FORM_*
   double off[MR_MAXQ];         // stored value = population - off[p] (0 unless 16-bit storage)
+  int s_pred;                  // half-width s of the prediction operator (Table 1): 1, 2 or 3
   int diag;                    // lattice with diagonal velocities: 5^d stream window
   int obstacle;                // penalisation of Sec. 7.2.2 after the collision
   double obs[3];               // obstacle disc: centre x, y and radius
@@ -270,6 +271,20 @@ __host__ __device__ inline int mr_slot(int k, int N, int periodic) {
   return 2;
 }
 
+// Flattened weights of the prediction of half-width s = 2, 3: the window is
+// W = 2s cells on either side, so a table has 2W + 1 entries, and 2W + 1
+// slots tell apart the cells within W of a non-periodic face (a level of
+// at most 2W + 1 cells gets one slot per cell).
+// Layout: [level][axis][slot 0..2W][table 0..3][2W + 1], tables as above.
+#define MR_WWIDX(l, a, sl, t, W) (((((l) * 3 + (a)) * (2 * (W) + 1) + (sl)) * MR_NTAB + (t)) * (2 * (W) + 1))
+__host__ __device__ inline int mr_slot_w(int k, int N, int periodic, int W) {
+  if (periodic) return W;
+  if (N <= 2 * W + 1) return k;
+  if (k < W) return k;
+  if (k >= N - W) return W + 1 + (k - (N - W));
+  return W;
+}
+
 // ------------------------------------------------------------------------
 // instances and groups
 // ------------------------------------------------------------------------
@@ -290,6 +305,8 @@ struct __align__(16) InstDev {
   int* bcounts;       // per dense chunk: leaf / internal / ghost counts, then offsets
   const double* W;    // flattened weights, MR_WIDX layout
   const float* Wf;    // the same in FP32
+  const double* Ws;   // s = 2, 3: flattened weights of half-width 2s, MR_WWIDX layout (else null)
+  const float* Wsf;   // the same in FP32
 };
 
 // Instances of one scheme and storage form, stepped by shared launches: every
@@ -300,6 +317,7 @@ struct Group {
   const int* chunk_pre;  // device array [n + 1]: first dense chunk of each instance
   int n;
   int d, Q, scheme, form;
+  int s;                 // half-width of the prediction (all instances alike)
   int chunks;            // dense chunks of all instances
   int span;              // maximum of J - J_min
   bool grade;            // some instance has J > J_min + 1
@@ -385,6 +403,18 @@ void mr_launch_leaves_out(const Geo& g, const MeshDev& B, const void* LF, long l
 void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int level,
                              const double* prev, double* cur, cudaStream_t st, int grid);
 size_t mr_form_bytes(int form);  // bytes per stored population value
+
+// The same phases for the prediction of half-width s = 2, 3 (mr_wide.cu):
+// (2s+1)^d stencils, grading and ghost cascades of radius s, transport
+// windows of 2s cells on either side.  The launchers above call these when
+// the group's s is above 1.
+void mr_launch_details_w(const Group& G, int cur, cudaStream_t st);
+void mr_launch_grade_w(const Group& G, cudaStream_t st);
+void mr_launch_mark_ghosts_w(const Group& G, cudaStream_t st);
+void mr_launch_predict_level_w(const Group& G, int dst, int k, cudaStream_t st);
+void mr_launch_stream_collide_w(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st, int count);
+void mr_launch_project_dense_w(const Geo& g, const MeshDev& B, const void* LF, int level, const double* prev,
+                               double* cur, cudaStream_t st, int grid);
 
 // Adjoint kernels (mr_adjoint.cu), FP64, one instance; A = mesh of step n,
 // B = mesh of step n + 1, adjoint arrays in the layout of the value arrays.

@@ -713,6 +713,7 @@ void mr_launch_flags_H(const Group& G, int cur, cudaStream_t st) {
   MR_DISPATCH_D_PDL(k_flags_H, mr_tile_grid(G, G.capI, 256, 4), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
 }
 void mr_launch_grade(const Group& G, cudaStream_t st) {
+  if (G.s > 1) return mr_launch_grade_w(G, st);
   const int D_ = G.d;
   if (G.grade)
     MR_DISPATCH_D_PDL(k_grade, mr_tile_grid(G, (long long)G.chunks * MR_DENSE_ALIGN, 256, 4), 256, mr_pre_bytes(G), st,
@@ -727,6 +728,7 @@ void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int) {
   k_full_mesh<<<(int)(g.base[g.J + 1] / MR_DENSE_ALIGN), 256, 0, st>>>(g, cls);
 }
 void mr_launch_mark_ghosts(const Group& G, cudaStream_t st) {
+  if (G.s > 1) return mr_launch_mark_ghosts_w(G, st);
   const int D_ = G.d;
   MR_DISPATCH_D_PDL(k_mark_ghosts, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
 }

@@ -782,6 +782,7 @@ void mr_launch_remesh_copy(const Group& G, int cur, cudaStream_t st) {
 }
 
 void mr_launch_predict_level(const Group& G, int dst, int kl, cudaStream_t st) {
+  if (G.s > 1) return mr_launch_predict_level_w(G, dst, kl, st);
   switch (G.d * 100 + G.Q) {
     case 102: MR_FORMS3(launch_predict_t, 1, 2, G, dst, kl, st); break;
     case 103: MR_FORMS3(launch_predict_t, 1, 3, G, dst, kl, st); break;
@@ -793,6 +794,7 @@ void mr_launch_predict_level(const Group& G, int dst, int kl, cudaStream_t st) {
 
 void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st,
                               int count) {
+  if (G.s > 1) return mr_launch_stream_collide_w(G, dst, do_stream, do_collide, st, count);
   switch (G.scheme) {
     case 0: MR_FORMS2(launch_stream_t, 0, G, dst, do_stream, do_collide, count, st); break;
     case 1: MR_FORMS2(launch_stream_t, 1, G, dst, do_stream, do_collide, count, st); break;
@@ -844,6 +846,7 @@ static void launch_dense_t(const Geo& g, const MeshDev& B, const void* LF, int l
 }
 void mr_launch_project_dense(const Geo& g, const MeshDev& B, const void* LF, int level, const double* prev,
                              double* cur, cudaStream_t st, int grid) {
+  if (g.s_pred > 1) return mr_launch_project_dense_w(g, B, LF, level, prev, cur, st, grid);
   const Geo& G = g;
   if (g.d == 1) {
     MR_FORMS2(launch_dense_t, 1, g, B, LF, level, prev, cur, st, grid);

@@ -1,0 +1,681 @@
+// The adaptive step with the prediction operator of half-width s = 2, 3
+// (Table 1; the tensor-product operators of Sec. 4.1 for d = 2, 3).
+//
+// What changes with s, phase by phase:
+// - details (Def. Details): each internal cell predicts its 2^d children
+//   from its (2s+1)^d stencil; the evaluation order is the one of the
+//   operator's written form (axis sums, then the pair and triple diagonal
+//   sums, each started from its (1, 1, 1) term), in FP64 without
+//   contraction, so the group norms carry the same bits as a plain
+//   evaluation of those formulas;
+// - grading (Def. Grading): the parent of every tree cell has its
+//   (2s+1)^d neighbourhood in the tree;
+// - ghosts: the transport window reaches W = 2s cells on either side of a
+//   leaf along each axis, and every ghost's parent has its (2s+1)^d stencil
+//   available (tree cells or ghosts, cascading towards J_min);
+// - transport (Eq. AdaptiveAdvectionPhase with Eq. PredictionWithMatrixNew):
+//   the row-collapsed sums are the flattened weights of half-width W
+//   applied to the leaf's row, and every refined cell of the window adds the
+//   details of its children through the level-(j+1) edge weights (the
+//   critical case of Sec. 6.1).  Grading with radius s keeps level j+2
+//   cells out of reach of the leaf's edge reconstruction: a level-(j+2)
+//   cell below a level-(j+1) cell c needs c's +-s neighbourhood in the tree,
+//   which excludes the leaf's own children, so such cells lie 2s or more
+//   level-(j+2) cells away from the leaf's faces, beyond the W = 2s window.
+// Lattices with diagonal velocities keep s = 1 (their corner terms are
+// built on the 5 x 5 block of that window).
+//
+// The tuned s = 1 kernels are untouched; these are plain one-thread-per-cell
+// kernels that look cells up through the dense index map.
+#include "mr_schemes.cuh"
+
+namespace {
+
+// Table 1: coefficient c_a (a = 1..s) of the centred prediction of
+// half-width s.
+template <int S>
+__device__ __forceinline__ double wide_coef(int a) {
+  if constexpr (S == 2) return a == 1 ? -22.0 / 128.0 : 3.0 / 128.0;
+  return a == 1 ? -201.0 / 1024.0 : (a == 2 ? 11.0 / 256.0 : -5.0 / 1024.0);
+}
+
+// Arithmetic of the prediction: rounded as written, never contracted
+// (EXACT, FP64: the decision path), or plain operators in C.
+template <class C, bool EXACT>
+struct WAr {
+  __device__ static C add(C a, C b) { return a + b; }
+  __device__ static C sub(C a, C b) { return a - b; }
+  __device__ static C mul(C a, C b) { return a * b; }
+};
+template <>
+struct WAr<double, true> {
+  __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+  __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+};
+
+template <int D, int S>
+struct WBox {
+  static constexpr int W1 = 2 * S + 1;
+  static constexpr int N = D == 1 ? W1 : D == 2 ? W1 * W1 : W1 * W1 * W1;
+  // box index of offset (a, b, c), x fastest
+  __device__ static constexpr int at(int a, int b, int c) {
+    return D == 1 ? a + S : D == 2 ? (b + S) * W1 + (a + S) : ((c + S) * W1 + (b + S)) * W1 + (a + S);
+  }
+};
+
+// Predicted value of child ci (x bit | y bit << 1 | z bit << 2) from the
+// (2s+1)^D stencil v (x fastest): the value of the centre, then the signed
+// axis sums sum_a c_a (v_a - v_-a), then the pair sums sum_{b, a} c_a c_b
+// times the signed corner combination (b outer, a inner), then in 3D the
+// triple sum; the pair terms carry cross_sign.  Every product of a sign
+// +-1 is exact, so t + s q is formed as t + q or t - q.
+template <int D, int S, class C, bool EXACT>
+__device__ __forceinline__ C wide_predict(const C* v, int ci, int cross_sign) {
+  using A = WAr<C, EXACT>;
+  using B = WBox<D, S>;
+  auto V = [&](int a, int b, int c) { return v[B::at(a, b, c)]; };
+  auto pm = [](C t, int s, C q) { return s > 0 ? A::add(t, q) : A::sub(t, q); };
+  const int sx = (ci & 1) ? -1 : 1, sy = (ci & 2) ? -1 : 1, sz = (ci & 4) ? -1 : 1;
+  C q[3];
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    auto Va = [&](int o) { return ax == 0 ? V(o, 0, 0) : ax == 1 ? V(0, o, 0) : V(0, 0, o); };
+    C acc = A::mul((C)wide_coef<S>(1), A::sub(Va(1), Va(-1)));
+#pragma unroll
+    for (int a = 2; a <= S; ++a) acc = A::add(acc, A::mul((C)wide_coef<S>(a), A::sub(Va(a), Va(-a))));
+    q[ax] = acc;
+  }
+  C t = V(0, 0, 0);
+  t = pm(t, sx, q[0]);
+  if constexpr (D == 1) return t;
+  t = pm(t, sy, q[1]);
+  if constexpr (D == 3) t = pm(t, sz, q[2]);
+  // pair sums: (x, y), then in 3D (x, z) and (y, z)
+  constexpr int NP = D == 2 ? 1 : 3;
+#pragma unroll
+  for (int pr = 0; pr < NP; ++pr) {
+    C acc = (C)0;
+#pragma unroll
+    for (int b = 1; b <= S; ++b)
+#pragma unroll
+      for (int a = 1; a <= S; ++a) {
+        auto P = [&](int u, int w) { return pr == 0 ? V(u, w, 0) : pr == 1 ? V(u, 0, w) : V(0, u, w); };
+        const C cc = (C)(wide_coef<S>(a) * wide_coef<S>(b));  // exact: short dyadic rationals
+        const C term = A::mul(cc, A::add(A::sub(A::sub(P(a, b), P(-a, b)), P(a, -b)), P(-a, -b)));
+        acc = (a == 1 && b == 1) ? term : A::add(acc, term);
+      }
+    const int s1 = pr == 0 ? sx : (pr == 1 ? sx : sy), s2 = pr == 0 ? sy : sz;
+    t = pm(t, cross_sign * s1 * s2, acc);
+  }
+  if constexpr (D == 3) {
+    C acc = (C)0;
+#pragma unroll
+    for (int e = 1; e <= S; ++e)
+#pragma unroll
+      for (int b = 1; b <= S; ++b)
+#pragma unroll
+        for (int a = 1; a <= S; ++a) {
+          const C ccc = (C)(wide_coef<S>(a) * wide_coef<S>(b) * wide_coef<S>(e));  // exact
+          C w = A::sub(V(a, b, e), V(-a, b, e));
+          w = A::sub(w, V(a, -b, e));
+          w = A::sub(w, V(a, b, -e));
+          w = A::add(w, V(-a, -b, e));
+          w = A::add(w, V(-a, b, -e));
+          w = A::add(w, V(a, -b, -e));
+          w = A::sub(w, V(-a, -b, -e));
+          const C term = A::mul(ccc, w);
+          acc = (a == 1 && b == 1 && e == 1) ? term : A::add(acc, term);
+        }
+    t = pm(t, sx * sy * sz, acc);
+  }
+  return t;
+}
+
+// Map entries of the (2s+1)^D stencil around cell c of level l (constant
+// extension outside a non-periodic domain, wrap on a periodic axis).
+template <int D, int S>
+__device__ __forceinline__ bool wide_stencil(const Geo& g, const MeshDev& M, int l, const int* c, int32_t* ent) {
+  using B = WBox<D, S>;
+  bool ok = true;
+  for (int k = 0; k < B::N; ++k) {
+    int s[3] = {c[0] + k % B::W1 - S, D >= 2 ? c[1] + (k / B::W1) % B::W1 - S : 0,
+                D == 3 ? c[2] + k / (B::W1 * B::W1) - S : 0};
+    mr_nbr_stencil_d<D>(g, l, s);
+    ent[k] = M.map[g.base[l] + mr_encode_d<D>(g, l, s)];
+    ok = ok && ent[k] != MR_MAP_NONE;
+  }
+  return ok;
+}
+
+// ------------------------------------------------------------------ details
+// Group norm of the details of every internal cell's children (Def. Details,
+// max over the 2^d children and all populations), FP64 on stored values.
+template <int D, int S, int F>
+__global__ void __launch_bounds__(128) k_details_w(const InstDev* __restrict__ IB, int n, int cur) {
+  using St = typename FormT<F>::S;
+  using B = WBox<D, S>;
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, n);
+  mr_grid_dep();
+  const int tiles = mr_group_prefix(pre, n, [&](int b) { return (IB[b].mesh[cur].cnt->total[MR_CLS_INT] + 127) / 128; });
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int b = mr_group_find(pre, n, t);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    const MeshDev& A = si.mesh[cur];
+    const int i = (t - pre[b]) * 128 + threadIdx.x;
+    if (i >= A.cnt->total[MR_CLS_INT]) continue;
+    const int L = A.lvl[MR_CLS_INT][i];
+    const uint32_t code = A.code[MR_CLS_INT][i];
+    int c[3] = {0, 0, 0};
+    mr_decode_d<D>(g, L, code, c);
+    int32_t ent[B::N], che[1 << D];
+    bool ok = wide_stencil<D, S>(g, A, L, c, ent);
+    for (int ci = 0; ci < (1 << D); ++ci) {
+      che[ci] = A.map[g.base[L + 1] + ((code << D) | (uint32_t)ci)];
+      ok = ok && che[ci] != MR_MAP_NONE && (((uint32_t)che[ci]) >> 30) <= MR_CLS_INT;
+    }
+    for (int k = 0; k < B::N && ok; ++k) ok = (((uint32_t)ent[k]) >> 30) <= MR_CLS_INT;
+    if (!ok) {
+      mr_set_err(A.cnt, MR_DERR_INTERNAL);
+      continue;
+    }
+    double gmax = 0.0;
+    for (int p = 0; p < g.Q; ++p) {
+      double v[B::N];
+      for (int k = 0; k < B::N; ++k) v[k] = mr_ld(mr_resolve<St>(g, A, si.fstate, ent[k]), p);
+#pragma unroll 1
+      for (int ci = 0; ci < (1 << D); ++ci) {
+        const double pr = wide_predict<D, S, double, true>(v, ci, g.cross_sign);
+        const double d = fabs(__dsub_rn(mr_ld(mr_resolve<St>(g, A, si.fstate, che[ci]), p), pr));
+        gmax = d > gmax ? d : gmax;
+      }
+    }
+    A.G[i] = gmax;
+  }
+}
+
+// ------------------------------------------------------------------ grading
+// Every cell refined after H_eps (or by the grading itself) needs the
+// (2s+1)^D cells around it in the tree: their parents are marked refined,
+// depth first towards J_min by the thread that marks them first.
+template <int D, int S>
+__global__ void __launch_bounds__(256) k_grade_w(const InstDev* __restrict__ IB, int n) {
+  using B = WBox<D, S>;
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, n);
+  mr_grid_dep();
+  const int tiles = mr_group_prefix(pre, n, [&](int b) {
+    const Geo& gb = IB[b].g;
+    return gb.J > gb.Jmin + 1 ? (int)((gb.base[gb.J] - gb.base[gb.Jmin + 1] + 255) / 256) : 0;
+  });
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int b = mr_group_find(pre, n, t);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    uint8_t* flags = si.flags;
+    const uint32_t gi = g.base[g.Jmin + 1] + (uint32_t)(t - pre[b]) * 256u + threadIdx.x;
+    if (gi >= g.base[g.J]) continue;
+    if (!(flags[gi] & MR_F_H)) continue;
+    const int l0 = mr_level_of(g, gi);
+    const uint32_t c0 = gi - g.base[l0];
+    if (c0 >= g.ncode[l0]) continue;
+    int sl[MR_MAXL], sc[MR_MAXL][3], sk[MR_MAXL];
+    int sp = 1;
+    sl[0] = l0;
+    sk[0] = 0;
+    sc[0][0] = sc[0][1] = sc[0][2] = 0;
+    mr_decode_d<D>(g, l0, c0, sc[0]);
+    while (sp > 0) {
+      const int f = sp - 1;
+      if (sk[f] == B::N) {
+        --sp;
+        continue;
+      }
+      const int k = sk[f]++;
+      const int L = sl[f];
+      int nb[3] = {sc[f][0] + k % B::W1 - S, D >= 2 ? sc[f][1] + (k / B::W1) % B::W1 - S : 0,
+                   D == 3 ? sc[f][2] + k / (B::W1 * B::W1) - S : 0};
+      if (!mr_nbr_mesh_d<D>(g, L, nb)) continue;
+      for (int a = 0; a < D; ++a) nb[a] >>= 1;
+      const int tl = L - 1;
+      const uint32_t pi = g.base[tl] + mr_encode_d<D>(g, tl, nb);
+      if (flags[pi] & (MR_F_H | MR_F_G)) continue;  // plain load first
+      const uint32_t old = mr_atomic_or_byte(flags, pi, MR_F_G);
+      if (!(old & (MR_F_H | MR_F_G)) && tl > g.Jmin && sp < MR_MAXL) {
+        sl[sp] = tl;
+        sk[sp] = 0;
+        for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? nb[a] : 0;
+        ++sp;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ ghosts
+// Cells the transport of a leaf reads that are not in the tree: the window
+// of W = 2s cells on either side along each axis.  Each one not yet marked
+// becomes a ghost, and its parent's (2s+1)^D stencil is marked the same way
+// (cells outside the tree become ghosts), towards J_min.
+template <int D, int S>
+__global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict__ IB,
+                                                       const int* __restrict__ chunk_pre, int n) {
+  using B = WBox<D, S>;
+  constexpr int W = 2 * S;
+  __shared__ InstDev si;
+  int chunk, have = -1;
+  mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
+  mr_grid_dep();
+  const Geo& g = si.g;
+  uint8_t* cls = si.cls;
+  const uint32_t c0 = (uint32_t)chunk * MR_DENSE_ALIGN;
+  const int l = mr_level_of(g, c0);
+  const uint32_t cb = c0 - g.base[l];
+  for (int k = 0; k < (int)(MR_DENSE_ALIGN / 256u); ++k) {
+    const uint32_t c = cb + (uint32_t)k * 256u + threadIdx.x;
+    if (c >= g.ncode[l] || (cls[c0 + (c - cb)] & 3u) != MR_C_LEAF) continue;
+    int x[3] = {0, 0, 0};
+    mr_decode_d<D>(g, l, c, x);
+    for (int w = 0; w < D * 2 * W; ++w) {
+      const int axis = w / (2 * W), o = w % (2 * W), off = o < W ? o - W : o - W + 1;  // -W..-1, 1..W
+      int nb[3] = {x[0], x[1], x[2]};
+      nb[axis] += off;
+      if (!mr_nbr_mesh_d<D>(g, l, nb)) continue;
+      const uint32_t gw = g.base[l] + mr_encode_d<D>(g, l, nb);
+      if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
+      const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
+      if ((old & (3u | MR_C_GHOST)) || l - 1 < g.Jmin) continue;
+      // cascade over the stencils of the ghosts' parents
+      int sl[MR_MAXL], sc[MR_MAXL][3], sk[MR_MAXL];
+      int sp = 1;
+      sl[0] = l - 1;
+      sk[0] = 0;
+      for (int a = 0; a < 3; ++a) sc[0][a] = a < D ? nb[a] >> 1 : 0;
+      while (sp > 0) {
+        const int f = sp - 1;
+        if (sk[f] == B::N) {
+          --sp;
+          continue;
+        }
+        const int kk = sk[f]++;
+        const int L = sl[f];
+        int ac[3] = {sc[f][0] + kk % B::W1 - S, D >= 2 ? sc[f][1] + (kk / B::W1) % B::W1 - S : 0,
+                     D == 3 ? sc[f][2] + kk / (B::W1 * B::W1) - S : 0};
+        if (!mr_nbr_mesh_d<D>(g, L, ac)) continue;  // outside: the stencil clamps to a cell of the box
+        const uint32_t ga = g.base[L] + mr_encode_d<D>(g, L, ac);
+        if (cls[ga] & (3u | MR_C_GHOST)) continue;
+        const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
+        if ((o2 & (3u | MR_C_GHOST)) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
+        sl[sp] = L - 1;
+        sk[sp] = 0;
+        for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? ac[a] >> 1 : 0;
+        ++sp;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ prediction of ghosts and new leaves
+// Ghosts and newly created leaves of level J_min + kl: the prediction of
+// half-width s applied to the level-1 values of the new mesh.
+template <int D, int S, int F>
+__global__ void __launch_bounds__(128) k_predict_level_w(const InstDev* __restrict__ IB, int ngrp, int dst, int kl) {
+  using St = typename FormT<F>::S;
+  using C = typename FormT<F>::C;
+  using B = WBox<D, S>;
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, ngrp);
+  mr_grid_dep();
+  const int tiles = mr_group_prefix(pre, ngrp, [&](int b) {
+    const Geo& gb = IB[b].g;
+    const int l = gb.Jmin + kl;
+    if (l > gb.J) return 0;
+    const MeshCounts* c = IB[b].mesh[dst].cnt;
+    return (c->off[MR_CLS_GHOST][l + 1] - c->off[MR_CLS_GHOST][l] + c->off[MR_CLS_LEAF][l + 1] -
+            c->off[MR_CLS_LEAF][l] + 127) / 128;
+  });
+  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+    const int b = mr_group_find(pre, ngrp, tt);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    const MeshDev& Bm = si.mesh[dst];
+    void* LF = si.fscratch;
+    const int level = g.Jmin + kl;
+    const int gb = Bm.cnt->off[MR_CLS_GHOST][level], ge = Bm.cnt->off[MR_CLS_GHOST][level + 1];
+    const int lb = Bm.cnt->off[MR_CLS_LEAF][level], le = Bm.cnt->off[MR_CLS_LEAF][level + 1];
+    const int ng = ge - gb, total = ng + (le - lb);
+    const int t = (tt - pre[b]) * 128 + threadIdx.x;
+    if (t >= total) continue;
+    uint32_t code;
+    St* out;
+    size_t ostride;
+    if (t < ng) {
+      const int i = gb + t;
+      code = Bm.code[MR_CLS_GHOST][i];
+      out = (St*)Bm.GF + i;
+      ostride = g.cap[2];
+    } else {
+      const int i = lb + (t - ng);
+      if (Bm.src[i] >= 0) continue;  // a leaf carried over keeps its transferred values
+      code = Bm.code[MR_CLS_LEAF][i];
+      out = (St*)LF + i;
+      ostride = g.cap[0];
+    }
+    int pc[3] = {0, 0, 0};
+    mr_decode_d<D>(g, level - 1, code >> D, pc);
+    int32_t ent[B::N];
+    if (!wide_stencil<D, S>(g, Bm, level - 1, pc, ent)) {
+      mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
+      continue;
+    }
+    const int ci = (int)(code & ((1u << D) - 1u));
+    for (int p = 0; p < g.Q; ++p) {
+      C v[B::N];
+      for (int k = 0; k < B::N; ++k) v[k] = ld_c<C>(mr_resolve<St>(g, Bm, LF, ent[k]), p);
+      out[(size_t)p * ostride] = mr_from_d<St>((double)wide_predict<D, S, C, false>(v, ci, g.cross_sign));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ uniform-level reconstruction
+// Conserved moments on the uniform level `level`: values of the complete
+// tree where present, the prediction of half-width s of the level above
+// otherwise (the prediction is linear, so it acts on the moments).
+template <int D, int S, int F>
+__global__ void __launch_bounds__(256) k_project_dense_w(Geo g, MeshDev Bm, const void* __restrict__ LF, int level,
+                                                         const double* __restrict__ prev, double* cur) {
+  using St = typename FormT<F>::S;
+  using B = WBox<D, S>;
+  const int n0 = g.n[level][0], n1 = g.n[level][1];
+  const long long N = (long long)n0 * n1 * g.n[level][2];
+  const int p0 = level > g.Jmin ? g.n[level - 1][0] : 1, p1 = level > g.Jmin ? g.n[level - 1][1] : 1;
+  const long long PN = level > g.Jmin ? (long long)p0 * p1 * g.n[level - 1][2] : 1;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
+    const int c[3] = {(int)(r % n0), (int)((r / n0) % n1), (int)(r / ((long long)n0 * n1))};
+    const int32_t e = Bm.map[g.base[level] + mr_encode_d<D>(g, level, c)];
+    if (e != MR_MAP_NONE && (((uint32_t)e) >> 30) <= MR_CLS_INT) {
+      const ValPtr<St> v = mr_resolve<St>(g, Bm, LF, e);
+      for (int k = 0; k < g.ncons; ++k) {
+        double acc = 0.0;
+        for (int p = 0; p < g.Q; ++p) acc += g.consw[k][p] * (mr_ld(v, p) + (FormT<F>::offs ? g.off[p] : 0.0));
+        cur[k * N + r] = acc;
+      }
+    } else if (level > g.Jmin) {
+      int ci = 0;
+      for (int a = 0; a < D; ++a) ci |= (c[a] & 1) << a;
+      for (int k = 0; k < g.ncons; ++k) {
+        double v[B::N];
+        for (int q = 0; q < B::N; ++q) {
+          int s[3] = {(c[0] >> 1) + q % B::W1 - S, D >= 2 ? (c[1] >> 1) + (q / B::W1) % B::W1 - S : 0,
+                      D == 3 ? (c[2] >> 1) + q / (B::W1 * B::W1) - S : 0};
+          mr_nbr_stencil_d<D>(g, level - 1, s);
+          v[q] = prev[k * PN + ((long long)s[2] * p1 + s[1]) * p0 + s[0]];
+        }
+        cur[k * N + r] = wide_predict<D, S, double, false>(v, ci, g.cross_sign);
+      }
+    } else {
+      mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ transport + collision
+#define MR_WOUT ((int32_t)0xC0000000)  // window cell outside a non-periodic domain
+
+template <class C>
+__device__ __forceinline__ const C* wide_tab(const InstDev& si);
+template <>
+__device__ __forceinline__ const double* wide_tab<double>(const InstDev& si) { return si.Ws; }
+template <>
+__device__ __forceinline__ const float* wide_tab<float>(const InstDev& si) { return si.Wsf; }
+
+// One thread per leaf, lattices with axis velocities.  Along each axis a the
+// populations moving along a take the flattened weights of the leaf's slot
+// over its row k - W .. k + W (W = 2s), the boundary value of a
+// non-periodic face they enter through, and for every refined cell of the
+// window the details of its children through the level-(j+1) edge weights:
+// for a velocity +1 the finest cell upwind of the leaf is the right edge of
+// level-(j+1) cell 2k - 1 and the leaf's last finest cell the right edge of
+// 2k + 1; for -1 the left edges of 2k + 2 and 2k.  A child's detail is
+// averaged over the 2^{d-1} children on the row (their transverse sum is
+// what the row-collapsed reconstruction sees).
+template <int SC, int S, int F>
+__global__ void __launch_bounds__(128) k_stream_collide_w(const InstDev* __restrict__ IB, int ngrp, int dst,
+                                                          int do_stream, int do_collide, int count) {
+  using Sc = Scheme<SC>;
+  using St = typename FormT<F>::S;
+  using C = typename FormT<F>::C;
+  using B = WBox<Sc::D, S>;
+  constexpr bool OFFS = FormT<F>::offs;
+  constexpr int D = Sc::D, Q = Sc::Q, W = 2 * S, NW = 2 * W + 1;
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, ngrp);
+  mr_grid_dep();
+  const int tiles =
+      mr_group_prefix(pre, ngrp, [&](int b) { return (IB[b].mesh[dst].cnt->total[MR_CLS_LEAF] + 127) / 128; });
+  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+    const int b = mr_group_find(pre, ngrp, tt);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    const MeshDev& Bm = si.mesh[dst];
+    const St* __restrict__ LFin = (const St*)si.fscratch;
+    St* __restrict__ LFout = (St*)si.fstate;
+    const C* __restrict__ Wt = wide_tab<C>(si);
+    const int i = (tt - pre[b]) * 128 + threadIdx.x;
+    if (count && tt == pre[b] && threadIdx.x == 0) {
+      Bm.cnt->leaf_updates += Bm.cnt->total[MR_CLS_LEAF];
+      Bm.cnt->steps += 1;
+    }
+    if (i >= Bm.cnt->total[MR_CLS_LEAF]) continue;
+    const int l = Bm.lvl[MR_CLS_LEAF][i];
+    const uint32_t code = Bm.code[MR_CLS_LEAF][i];
+    const C* offv = mr_offv<C>(g);
+    C fs[Q], out[Q];
+    for (int p = 0; p < Q; ++p) {
+      const ValPtr<St> me{LFin + i, g.cap[0]};
+      fs[p] = ld_off<F>(me, p, offv);
+      out[p] = fs[p];
+    }
+    if (do_stream) {
+      int xc[3] = {0, 0, 0};
+      mr_decode_d<D>(g, l, code, xc);
+      const C scale = (C)__longlong_as_double((long long)(1023 + l - g.J) << 52);  // 2^{l-J}, exact
+#pragma unroll 1
+      for (int a = 0; a < D; ++a) {
+        const int k = xc[a], N = g.n[l][a], per = g.periodic[a];
+        const int slot = mr_slot_w(k, N, per, W);
+        const C* wP = Wt + MR_WWIDX(l, a, slot, 0, W);
+        const C* wM = Wt + MR_WWIDX(l, a, slot, 1, W);
+        const bool lo = !per && k == 0, hi = !per && k == N - 1;
+        int32_t ent[NW];
+        for (int o = 0; o < NW; ++o) {
+          ent[o] = MR_WOUT;
+          if (o == W) continue;
+          int nb[3] = {xc[0], xc[1], xc[2]};
+          nb[a] += o - W;
+          if (!mr_nbr_mesh_d<D>(g, l, nb)) continue;
+          const int32_t e = Bm.map[g.base[l] + mr_encode_d<D>(g, l, nb)];
+          if (e == MR_MAP_NONE)
+            mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
+          else
+            ent[o] = e;
+        }
+        for (int p = 0; p < Q; ++p) {
+          const int sgn = eta_of<Sc>(p, a);
+          if (sgn == 0) continue;
+          const C* w = sgn > 0 ? wP : wM;
+          C acc = w[W] * fs[p];
+          for (int o = 0; o < NW; ++o)
+            if (ent[o] != MR_WOUT) acc += w[o] * ld_off<F>(mr_resolve<St>(g, Bm, LFin, ent[o]), p, offv);
+          if (sgn > 0 && lo) acc += bc_value<C>(g, g.bc[2 * a], fs, p, Sc::opp(p));
+          if (sgn < 0 && hi) acc += bc_value<C>(g, g.bc[2 * a + 1], fs, p, Sc::opp(p));
+          out[p] += scale * acc;
+        }
+        // the critical case: refined cells of the window
+        for (int o = 0; o < NW; ++o) {
+          if (ent[o] == MR_WOUT || (((uint32_t)ent[o]) >> 30) != MR_CLS_INT) continue;
+          const int dlt = o - W;
+          int nb[3] = {xc[0], xc[1], xc[2]};
+          nb[a] += dlt;
+          mr_nbr_mesh_d<D>(g, l, nb);  // inside: only such cells have an entry
+          int32_t st[B::N], ce[1 << D];
+          bool ok = wide_stencil<D, S>(g, Bm, l, nb, st);
+          const uint32_t ncode = mr_encode_d<D>(g, l, nb);
+          for (int ci = 0; ci < (1 << D); ++ci) {
+            ce[ci] = Bm.map[g.base[l + 1] + ((ncode << D) | (uint32_t)ci)];
+            ok = ok && ce[ci] != MR_MAP_NONE;
+          }
+          if (!ok) {
+            mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
+            continue;
+          }
+          const int N1 = g.n[l + 1][a];
+          for (int p = 0; p < Q; ++p) {
+            const int sgn = eta_of<Sc>(p, a);
+            if (sgn == 0) continue;
+            const int rE = sgn > 0 ? -1 : 2, rA = sgn > 0 ? 1 : 0;  // edge cells, relative to 2k
+            const int tab = sgn > 0 ? 2 : 3;
+            const bool eIn = per || (sgn > 0 ? k > 0 : k < N - 1);
+            const C* wE = eIn ? Wt + MR_WWIDX(l + 1, a, mr_slot_w(2 * k + rE, N1, per, W), tab, W) : nullptr;
+            const C* wA = Wt + MR_WWIDX(l + 1, a, mr_slot_w(2 * k + rA, N1, per, W), tab, W);
+            // details are exact on constants: stored values suffice
+            C v[B::N];
+            for (int kk = 0; kk < B::N; ++kk) v[kk] = ld_c<C>(mr_resolve<St>(g, Bm, LFin, st[kk]), p);
+            C corr = (C)0;
+            for (int ci = 0; ci < (1 << D); ++ci) {
+              const int cx = 2 * dlt + ((ci >> a) & 1);
+              const int oE = cx - rE, oA = cx - rA;
+              C wgt = (C)0;
+              if (wE && oE >= -W && oE <= W) wgt += wE[oE + W];
+              if (oA >= -W && oA <= W) wgt -= wA[oA + W];
+              if (wgt == (C)0) continue;
+              const C det =
+                  ld_c<C>(mr_resolve<St>(g, Bm, LFin, ce[ci]), p) - wide_predict<D, S, C, false>(v, ci, g.cross_sign);
+              corr += wgt * det;
+            }
+            out[p] += scale * (corr * ((C)1 / (C)(1 << (D - 1))));
+          }
+        }
+      }
+    }
+    if (do_collide) Sc::template collide<C>(g, out);
+    bool finite = true;
+    for (int p = 0; p < Q; ++p) {
+      finite = finite && is_finite_bits(out[p]);
+      if constexpr (OFFS)
+        LFout[(size_t)p * g.cap[0] + i] = mr_from_f<St>((float)(out[p] - offv[p]));
+      else
+        LFout[(size_t)p * g.cap[0] + i] = (St)out[p];
+    }
+    if (!finite) mr_set_err(Bm.cnt, MR_DERR_NONFINITE);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <int D, int S, int F>
+void launch_details_w(const Group& G, int cur, cudaStream_t st) {
+  mr_launch_pdl(k_details_w<D, S, F>, mr_tile_grid(G, G.capI, 128, 8), 128, mr_pre_bytes(G), st, G.dev, G.n, cur);
+}
+template <int D, int S, int F>
+void launch_predict_w(const Group& G, int dst, int kl, cudaStream_t st) {
+  mr_launch_pdl(k_predict_level_w<D, S, F>, mr_tile_grid(G, 2 * G.pred_cells[kl], 128, 8), 128, mr_pre_bytes(G), st,
+                G.dev, G.n, dst, kl);
+}
+template <int SC, int S, int F>
+void launch_stream_w(const Group& G, int dst, int ds, int dc, int count, cudaStream_t st) {
+  mr_launch_pdl(k_stream_collide_w<SC, S, F>, mr_tile_grid(G, G.capL, 128, 8), 128, mr_pre_bytes(G), st, G.dev, G.n,
+                dst, ds, dc, count);
+}
+template <int D, int S, int F>
+void launch_dense_w(const Geo& g, const MeshDev& B, const void* LF, int level, const double* prev, double* cur,
+                    cudaStream_t st, int grid) {
+  k_project_dense_w<D, S, F><<<grid, 256, 0, st>>>(g, B, LF, level, prev, cur);
+}
+
+}  // namespace
+
+// form, then half-width
+#define MR_W_FORMS(FN, FORM, PRE, ...)                                          \
+  switch (FORM) {                                                               \
+    case MR_FORM_F64: FN<PRE, MR_FORM_F64>(__VA_ARGS__); break;                 \
+    case MR_FORM_F32: FN<PRE, MR_FORM_F32>(__VA_ARGS__); break;                 \
+    case MR_FORM_F32_F16: FN<PRE, MR_FORM_F32_F16>(__VA_ARGS__); break;         \
+    case MR_FORM_F32_BF16: FN<PRE, MR_FORM_F32_BF16>(__VA_ARGS__); break;       \
+  }
+#define MR_W_S(FN, FORM, S_, A1, ...)                                   \
+  do {                                                                  \
+    if ((S_) == 2) {                                                    \
+      MR_W_FORMS(FN, FORM, MR_W_PAIR(A1, 2), __VA_ARGS__);              \
+    } else {                                                            \
+      MR_W_FORMS(FN, FORM, MR_W_PAIR(A1, 3), __VA_ARGS__);              \
+    }                                                                   \
+  } while (0)
+#define MR_W_PAIR(a, b) a, b
+
+void mr_launch_details_w(const Group& G, int cur, cudaStream_t st) {
+  if (G.d == 1) MR_W_S(launch_details_w, G.form, G.s, 1, G, cur, st);
+  else if (G.d == 2) MR_W_S(launch_details_w, G.form, G.s, 2, G, cur, st);
+  else MR_W_S(launch_details_w, G.form, G.s, 3, G, cur, st);
+}
+
+void mr_launch_predict_level_w(const Group& G, int dst, int kl, cudaStream_t st) {
+  if (G.d == 1) MR_W_S(launch_predict_w, G.form, G.s, 1, G, dst, kl, st);
+  else if (G.d == 2) MR_W_S(launch_predict_w, G.form, G.s, 2, G, dst, kl, st);
+  else MR_W_S(launch_predict_w, G.form, G.s, 3, G, dst, kl, st);
+}
+
+void mr_launch_stream_collide_w(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st, int count) {
+  switch (G.scheme) {  // the schemes with axis velocities (D2Q9 keeps s = 1)
+    case 0: MR_W_S(launch_stream_w, G.form, G.s, 0, G, dst, do_stream, do_collide, count, st); break;
+    case 1: MR_W_S(launch_stream_w, G.form, G.s, 1, G, dst, do_stream, do_collide, count, st); break;
+    case 2: MR_W_S(launch_stream_w, G.form, G.s, 2, G, dst, do_stream, do_collide, count, st); break;
+    case 3: MR_W_S(launch_stream_w, G.form, G.s, 3, G, dst, do_stream, do_collide, count, st); break;
+    case 5: MR_W_S(launch_stream_w, G.form, G.s, 5, G, dst, do_stream, do_collide, count, st); break;
+    default: break;
+  }
+}
+
+void mr_launch_grade_w(const Group& G, cudaStream_t st) {
+  if (!G.grade) return;
+  const int grid = mr_tile_grid(G, (long long)G.chunks * MR_DENSE_ALIGN, 256, 4);
+  const size_t sm = mr_pre_bytes(G);
+  if (G.d == 1) {
+    if (G.s == 2) mr_launch_pdl(k_grade_w<1, 2>, grid, 256, sm, st, G.dev, G.n);
+    else mr_launch_pdl(k_grade_w<1, 3>, grid, 256, sm, st, G.dev, G.n);
+  } else if (G.d == 2) {
+    if (G.s == 2) mr_launch_pdl(k_grade_w<2, 2>, grid, 256, sm, st, G.dev, G.n);
+    else mr_launch_pdl(k_grade_w<2, 3>, grid, 256, sm, st, G.dev, G.n);
+  } else {
+    if (G.s == 2) mr_launch_pdl(k_grade_w<3, 2>, grid, 256, sm, st, G.dev, G.n);
+    else mr_launch_pdl(k_grade_w<3, 3>, grid, 256, sm, st, G.dev, G.n);
+  }
+}
+
+void mr_launch_mark_ghosts_w(const Group& G, cudaStream_t st) {
+  if (G.d == 1) {
+    if (G.s == 2) mr_launch_pdl(k_mark_ghosts_w<1, 2>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+    else mr_launch_pdl(k_mark_ghosts_w<1, 3>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+  } else if (G.d == 2) {
+    if (G.s == 2) mr_launch_pdl(k_mark_ghosts_w<2, 2>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+    else mr_launch_pdl(k_mark_ghosts_w<2, 3>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+  } else {
+    if (G.s == 2) mr_launch_pdl(k_mark_ghosts_w<3, 2>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+    else mr_launch_pdl(k_mark_ghosts_w<3, 3>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+  }
+}
+
+void mr_launch_project_dense_w(const Geo& g, const MeshDev& B, const void* LF, int level, const double* prev,
+                               double* cur, cudaStream_t st, int grid) {
+  if (g.d == 1) MR_W_S(launch_dense_w, g.form, g.s_pred, 1, g, B, LF, level, prev, cur, st, grid);
+  else if (g.d == 2) MR_W_S(launch_dense_w, g.form, g.s_pred, 2, g, B, LF, level, prev, cur, st, grid);
+  else MR_W_S(launch_dense_w, g.form, g.s_pred, 3, g, B, LF, level, prev, cur, st, grid);
+}

@@ -159,3 +159,12 @@ def test_exact_collision_J10_steps_from_the_oracle_state():
     cfg["exact_collision"] = 1
     levels = _per_step(cfg, u, 3, "exact collision euler J10")
     assert len(levels) >= 3
+
+
+def test_euler_J10_wide_prediction_steps_from_the_oracle_state():
+    """The benchmarked configuration with the prediction of half-width s = 2
+    (5^2 stencils, windows of 4 cells on either side of each leaf)."""
+    cfg, u = W.euler_2d(seed=3, max_level=10)
+    cfg["pred_s"] = 2
+    levels = _per_step(cfg, u, 4, "euler J10 s=2")
+    assert len(levels) >= 3
