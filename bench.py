@@ -106,6 +106,8 @@ def _args():
     p.add_argument("--serving-n", type=int, default=256,
                    help="instances of the batched serving measurement (0: skip it)")
     p.add_argument("--serving-steps", type=int, default=30)
+    p.add_argument("--autotune-steps", type=int, default=3,
+                   help="steps per candidate of the batch autotuner before the batched timing; 0 skips it")
     p.add_argument("--serving-loop", type=int, default=1,
                    help="also step every instance alone in the plain form (one-at-a-time baseline)")
     p.add_argument("--minimal", action="store_true",
@@ -308,6 +310,19 @@ def run_serving(args, stream, flush, local):
     b.step(args.warmup)
     b.synchronize()
     setup_s = time.perf_counter() - t0
+    tune = None
+    if args.autotune_steps > 0:
+        # schedules picked by the library's autotuner from the warmed-up state
+        # (the batch is put back as it was); the timed steps below use them
+        t1 = time.perf_counter()
+        default = b.schedule()
+        ms_fixed, ms_tuned = b.autotune(args.autotune_steps)
+        tune = {"trial_steps": args.autotune_steps, "ms_per_step_default_schedule": ms_fixed,
+                "ms_per_step_tuned_schedule": ms_tuned, "gain": ms_fixed / ms_tuned,
+                "default_schedule": default[0], "chosen_schedule_per_part": b.schedule(),
+                "phases": ["projection", "details", "mesh flags and grading", "compaction", "data transfer",
+                           "prediction", "transport + collision"],
+                "unit": "blocks per SM of each phase's grid", "tuning_s": time.perf_counter() - t1}
     K = args.serving_steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     per0 = [s.counters()[0] for s in b.instances]
@@ -341,7 +356,7 @@ def run_serving(args, stream, flush, local):
         "value": total / (step_ms.sum() / 1e3), "unit": UNIT, "steps": K,
         "ms_per_step": float(step_ms.mean()), "latency_ms_p50": float(np.percentile(step_ms, 50)),
         "latency_ms_p99": float(np.percentile(step_ms, 99)),
-        "leaves_per_step_avg": total / K, "gpu_launches": launches,
+        "leaves_per_step_avg": total / K, "gpu_launches": launches, "autotune": tune,
         "launches_per_step": launches / K, "setup_s": setup_s,
         "roofline": {"kernel": "k_stream_collide (transport + collision), both schemes", "bound": "hbm",
                      "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -311,6 +311,40 @@ long long mr_lbm_batch_launch_count(mr_lbm_batch_t b);
  * mr_lbm_profile_enable). */
 mr_status mr_lbm_batch_profile_enable(mr_lbm_batch_t b, int group);
 mr_status mr_lbm_batch_profile_read(mr_lbm_batch_t b, double* total_ms, long long* launches);
+
+/* Launch schedules of the batched form (the paper has no counterpart: this
+ * is how the batch maps onto the GPU).  The instances of one half-width,
+ * scheme and storage form make a part, stepped by shared grid-stride
+ * launches; a part's schedule gives, for each of its MR_LBM_NPHASE phases,
+ * the blocks per SM its tiled kernels may use (the grid is capped at that
+ * many blocks per SM; blocks stride over the tiles).  Phases, in order:
+ * projection, details, mesh flags and grading, compaction, data transfer,
+ * ghost / new-leaf prediction, transport + collision.  Defaults
+ * {8, 8, 4, 8, 8, 8, 8}.  mr_lbm_batch_parts gives the number of parts;
+ * get / set read and write one part's schedule (values 1..64, else
+ * MR_EINVAL; set synchronises the batch's stream). */
+#define MR_LBM_NPHASE 7
+mr_status mr_lbm_batch_parts(mr_lbm_batch_t b, int* nparts);
+mr_status mr_lbm_batch_get_schedule(mr_lbm_batch_t b, int part, int* bps /* [MR_LBM_NPHASE] */);
+mr_status mr_lbm_batch_set_schedule(mr_lbm_batch_t b, int part, const int* bps /* [MR_LBM_NPHASE] */);
+
+/* Autotuner of the schedules: coordinate descent over each part and phase,
+ * candidates 1, 2, 4, 8, 16, 32 blocks per SM, each candidate timed (CUDA
+ * events on the batch's stream, graph replay) over `trial_steps` batched
+ * steps (1..1000) from the same state, a change kept only if the step gets
+ * more than 1 % faster.  Every instance is snapshotted first (device
+ * buffers the tuner allocates and frees) and put back afterwards, with its
+ * counters: the batch leaves the call in the state it entered it.
+ * *ms_fixed / *ms_tuned (may be NULL): time per step of the schedule on
+ * entry and of the chosen one.  The result is cached for the batch's
+ * signature (per part: half-width, scheme, form, instance count and the
+ * power of two of the mean finest-cell count): later batches of the same
+ * signature in the process start from it, and so do those of later
+ * processes when the environment variable MR_LBM_TUNE_CACHE names a file
+ * (one line per tuning is appended).  Synchronises; minutes for large
+ * batches (7 phases x 5 candidates x parts trials). */
+mr_status mr_lbm_batch_autotune(mr_lbm_batch_t b, int trial_steps, double* ms_fixed, double* ms_tuned);
+
 /* Release the batch and all its instances.  Accepts NULL. */
 mr_status mr_lbm_batch_destroy(mr_lbm_batch_t b);
 

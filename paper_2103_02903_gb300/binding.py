@@ -102,13 +102,18 @@ def library():
         L.mr_lbm_batch_profile_enable.argtypes = [vp, i]
         L.mr_lbm_batch_profile_read.argtypes = [vp, C.POINTER(d), C.POINTER(ll)]
         L.mr_lbm_batch_destroy.argtypes = [vp]
+        L.mr_lbm_batch_parts.argtypes = [vp, C.POINTER(i)]
+        L.mr_lbm_batch_get_schedule.argtypes = [vp, i, C.POINTER(i)]
+        L.mr_lbm_batch_set_schedule.argtypes = [vp, i, C.POINTER(i)]
+        L.mr_lbm_batch_autotune.argtypes = [vp, i, C.POINTER(d), C.POINTER(d)]
         for name in ("mr_lbm_create", "mr_lbm_destroy", "mr_lbm_init", "mr_lbm_step", "mr_lbm_adapt",
                      "mr_lbm_project", "mr_lbm_project_noalloc", "mr_lbm_get_leaves", "mr_lbm_set_leaves", "mr_lbm_stats",
                      "mr_lbm_counters", "mr_lbm_profile_enable", "mr_lbm_profile_read",
                      "mr_lbm_synchronize", "mr_lbm_flattened_weights", "mr_lbm_flattened_weights_s", "mr_lbm_batch_create",
                      "mr_lbm_batch_instance", "mr_lbm_batch_step", "mr_lbm_batch_synchronize",
                      "mr_lbm_batch_counters", "mr_lbm_batch_profile_enable", "mr_lbm_batch_profile_read",
-                     "mr_lbm_batch_destroy"):
+                     "mr_lbm_batch_destroy", "mr_lbm_batch_parts", "mr_lbm_batch_get_schedule",
+                     "mr_lbm_batch_set_schedule", "mr_lbm_batch_autotune"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -363,6 +368,33 @@ class Batch:
         ms, n = C.c_double(), C.c_longlong()
         _check(library().mr_lbm_batch_profile_read(self.b, C.byref(ms), C.byref(n)), "mr_lbm_batch_profile_read")
         return ms.value, n.value
+
+    NPHASE = 7
+
+    def parts(self) -> int:
+        n = C.c_int()
+        _check(library().mr_lbm_batch_parts(self.b, C.byref(n)), "mr_lbm_batch_parts")
+        return n.value
+
+    def schedule(self):
+        """[parts][7] blocks per SM of each phase (mr_lbm_batch_get_schedule)."""
+        out = []
+        for p in range(self.parts()):
+            v = (C.c_int * self.NPHASE)()
+            _check(library().mr_lbm_batch_get_schedule(self.b, p, v), "mr_lbm_batch_get_schedule")
+            out.append(list(v))
+        return out
+
+    def set_schedule(self, part: int, bps):
+        v = (C.c_int * self.NPHASE)(*[int(x) for x in bps])
+        _check(library().mr_lbm_batch_set_schedule(self.b, part, v), "mr_lbm_batch_set_schedule")
+
+    def autotune(self, trial_steps: int = 4):
+        """mr_lbm_batch_autotune: (ms per step before, after)."""
+        a, b = C.c_double(), C.c_double()
+        _check(library().mr_lbm_batch_autotune(self.b, int(trial_steps), C.byref(a), C.byref(b)),
+               "mr_lbm_batch_autotune")
+        return a.value, b.value
 
     def close(self):
         if getattr(self, "b", None):

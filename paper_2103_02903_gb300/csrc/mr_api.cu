@@ -10,6 +10,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "mr_handle.cuh"
@@ -424,6 +427,10 @@ bool make_group(Group& G, const std::vector<const mr_lbm*>& members, const InstD
   G.scheme = g0.scheme;
   G.form = g0.form;
   G.s = g0.s_pred;
+  {
+    const int def[MR_NPH] = MR_DEFAULT_BPS;
+    for (int ph = 0; ph < MR_NPH; ++ph) G.bps[ph] = def[ph];
+  }
   std::vector<int> pre(G.n + 1, 0);
   for (int b = 0; b < G.n; ++b) {
     const Geo& g = members[b]->g;
@@ -1460,6 +1467,79 @@ void free_batch(mr_lbm_batch* b) {
   delete b;
 }
 
+// ---- launch schedules: the autotuner's cache
+// A batch's signature names each part by half-width, scheme, form, size and
+// the power of two of its mean finest-cell count; the cache maps it to the
+// parts' schedules (MR_NPH blocks-per-SM values each).  It lives in the
+// process and, when MR_LBM_TUNE_CACHE names a file, in that file (one line
+// per tuning, the last line of a signature wins).
+std::mutex g_tune_mutex;
+std::map<std::string, std::vector<int>> g_tune_cache;
+bool g_tune_file_read = false;
+
+std::string batch_signature(const mr_lbm_batch* b) {
+  std::string sig;
+  for (const auto& p : b->parts) {
+    const long long avg = std::max<long long>(1, p.G.capL / std::max(1, p.G.n));
+    int band = 0;
+    while ((1ll << (band + 1)) <= avg) ++band;
+    char buf[96];
+    snprintf(buf, sizeof buf, "%d.%d.%d.%d.%d/", p.G.s, p.G.scheme, p.G.form, p.G.n, band);
+    sig += buf;
+  }
+  return sig;
+}
+
+void tune_cache_read_file() {  // under g_tune_mutex
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char* path = getenv("MR_LBM_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fp = fopen(path, "r");
+  if (!fp) return;
+  char line[4096];
+  while (fgets(line, sizeof line, fp)) {
+    char* save = nullptr;
+    char* tok = strtok_r(line, " \t\n", &save);
+    if (!tok) continue;
+    std::string sig = tok;
+    std::vector<int> v;
+    while ((tok = strtok_r(nullptr, " \t\n", &save))) v.push_back(atoi(tok));
+    if (!v.empty()) g_tune_cache[sig] = v;
+  }
+  fclose(fp);
+}
+
+// Schedules of a batch's parts from the cache, if it holds its signature.
+void apply_cached_schedule(mr_lbm_batch* b) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_cache_read_file();
+  auto it = g_tune_cache.find(batch_signature(b));
+  if (it == g_tune_cache.end() || it->second.size() != b->parts.size() * MR_NPH) return;
+  for (size_t p = 0; p < b->parts.size(); ++p)
+    for (int ph = 0; ph < MR_NPH; ++ph) {
+      const int v = it->second[p * MR_NPH + ph];
+      if (v >= 1 && v <= 64) b->parts[p].G.bps[ph] = v;
+    }
+}
+
+void store_schedule(const mr_lbm_batch* b) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_cache_read_file();
+  std::vector<int> v;
+  for (const auto& p : b->parts) v.insert(v.end(), p.G.bps, p.G.bps + MR_NPH);
+  const std::string sig = batch_signature(b);
+  g_tune_cache[sig] = v;
+  const char* path = getenv("MR_LBM_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fp = fopen(path, "a");
+  if (!fp) return;
+  fprintf(fp, "%s", sig.c_str());
+  for (int x : v) fprintf(fp, " %d", x);
+  fprintf(fp, "\n");
+  fclose(fp);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1519,6 +1599,7 @@ mr_status mr_lbm_batch_create(const mr_lbm_config* cfgs, int n, void* cuda_strea
     free_batch(b);
     return MR_ECUDA;
   }
+  apply_cached_schedule(b);
   *out = b;
   return MR_OK;
 }
@@ -1584,6 +1665,162 @@ mr_status mr_lbm_batch_profile_read(mr_lbm_batch_t b, double* total_ms, long lon
   const double tot = profile_total(*b, launches);
   if (tot < 0) return MR_ECUDA;
   if (total_ms) *total_ms = tot;
+  return MR_OK;
+}
+
+mr_status mr_lbm_batch_parts(mr_lbm_batch_t b, int* nparts) {
+  if (!b || !nparts) return MR_EINVAL;
+  *nparts = (int)b->parts.size();
+  return MR_OK;
+}
+
+mr_status mr_lbm_batch_get_schedule(mr_lbm_batch_t b, int part, int* bps) {
+  if (!b || !bps || part < 0 || part >= (int)b->parts.size()) return MR_EINVAL;
+  for (int ph = 0; ph < MR_NPH; ++ph) bps[ph] = b->parts[part].G.bps[ph];
+  return MR_OK;
+}
+
+mr_status mr_lbm_batch_set_schedule(mr_lbm_batch_t b, int part, const int* bps) {
+  if (!b || !bps || part < 0 || part >= (int)b->parts.size()) return MR_EINVAL;
+  for (int ph = 0; ph < MR_NPH; ++ph)
+    if (bps[ph] < 1 || bps[ph] > 64) return MR_EINVAL;
+  if (b->st && cudaStreamSynchronize(b->st) != cudaSuccess) return MR_ECUDA;
+  for (int ph = 0; ph < MR_NPH; ++ph) b->parts[part].G.bps[ph] = bps[ph];
+  drop_graphs(*b);  // the captured steps carry the old grids
+  return MR_OK;
+}
+
+mr_status mr_lbm_batch_autotune(mr_lbm_batch_t b, int trial_steps, double* ms_fixed, double* ms_tuned) {
+  if (!b || trial_steps < 1 || trial_steps > 1000) return MR_EINVAL;
+  if (b->sticky != MR_OK) return b->sticky;
+  for (mr_lbm* h : b->inst) {
+    if (h->sticky != MR_OK) return h->sticky;
+    if (!h->initialized || h->cur != b->cur) return MR_ESTATE;
+  }
+  const size_t ni = b->inst.size();
+  // snapshot of every instance: leaves, counters and launch counts
+  struct Snap {
+    long long n = 0;
+    unsigned long long* k = nullptr;
+    signed char* l = nullptr;
+    double* f = nullptr;
+    MeshCounts cnt[2];
+    long long launches = 0;
+  };
+  std::vector<Snap> snap(ni);
+  const long long launches0 = b->launches;
+  mr_status st = MR_OK;
+  auto release = [&]() {
+    for (Snap& s : snap) {
+      if (s.k) cudaFree(s.k);
+      if (s.l) cudaFree(s.l);
+      if (s.f) cudaFree(s.f);
+    }
+  };
+  for (size_t i = 0; i < ni && st == MR_OK; ++i) {
+    mr_lbm* h = b->inst[i];
+    Snap& s = snap[i];
+    st = mr_lbm_get_leaves(h, &s.n, nullptr, nullptr, nullptr, 1);
+    if (st != MR_OK) break;
+    if (cudaMalloc(&s.k, s.n * sizeof(unsigned long long)) != cudaSuccess || cudaMalloc(&s.l, s.n) != cudaSuccess ||
+        cudaMalloc(&s.f, (size_t)h->g.Q * s.n * sizeof(double)) != cudaSuccess) {
+      st = MR_ENOMEM;
+      break;
+    }
+    long long n = s.n;
+    st = mr_lbm_get_leaves(h, &n, s.k, s.l, s.f, 1);
+    if (st == MR_OK && cudaMemcpy(s.cnt, h->cntbuf, 2 * sizeof(MeshCounts), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = MR_ECUDA;
+    s.launches = h->launches;
+  }
+  if (st != MR_OK) {
+    release();
+    return st;
+  }
+  auto restore = [&]() -> mr_status {
+    for (size_t i = 0; i < ni; ++i) {
+      const mr_status r = mr_lbm_set_leaves(b->inst[i], snap[i].n, snap[i].k, snap[i].l, snap[i].f, 1);
+      if (r != MR_OK) return r;
+    }
+    return cudaStreamSynchronize(b->st) == cudaSuccess ? MR_OK : MR_ECUDA;
+  };
+  auto body = [b]() { run_batch_step(b); };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    release();
+    return MR_ECUDA;
+  }
+  // one trial: the snapshot, a step that captures the graphs, then the timed steps
+  auto trial = [&](double* ms) -> mr_status {
+    mr_status r = restore();
+    if (r != MR_OK) return r;
+    drop_graphs(*b);
+    queue_steps(*b, 1, body);
+    for (mr_lbm* h : b->inst) h->cur = b->cur;
+    cudaEventRecord(e0, b->st);
+    queue_steps(*b, trial_steps, body);
+    cudaEventRecord(e1, b->st);
+    for (mr_lbm* h : b->inst) h->cur = b->cur;
+    if (cudaEventSynchronize(e1) != cudaSuccess) return MR_ECUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return MR_ECUDA;
+    for (mr_lbm* h : b->inst) {
+      MeshCounts hc[2];
+      r = read_counts(h, hc);
+      if (r != MR_OK) return r;
+    }
+    *ms = t / trial_steps;
+    return MR_OK;
+  };
+  // coordinate descent: one phase of one part at a time over the candidates,
+  // keeping a change only if it gains more than 1 % (timing noise)
+  static const int cand[] = {1, 2, 4, 8, 16, 32};
+  double base = 0.0, best = 0.0;
+  st = trial(&base);
+  best = base;
+  for (size_t p = 0; p < b->parts.size() && st == MR_OK; ++p)
+    for (int ph = 0; ph < MR_NPH && st == MR_OK; ++ph) {
+      int keep = b->parts[p].G.bps[ph];
+      for (int c : cand) {
+        if (c == keep) continue;
+        b->parts[p].G.bps[ph] = c;
+        double ms = 0.0;
+        st = trial(&ms);
+        if (st != MR_OK) break;
+        if (ms < 0.99 * best) {
+          best = ms;
+          keep = c;
+        }
+      }
+      b->parts[p].G.bps[ph] = keep;
+    }
+  double tuned = 0.0;
+  if (st == MR_OK) st = trial(&tuned);  // the chosen schedule, measured once more
+  // the batch as it was: leaves, counters, launch counts, no captured step
+  if (st == MR_OK) st = restore();
+  for (size_t i = 0; i < ni && st == MR_OK; ++i) {
+    mr_lbm* h = b->inst[i];
+    MeshCounts hc[2];
+    if (cudaMemcpy(hc, h->cntbuf, 2 * sizeof(MeshCounts), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = MR_ECUDA;
+      break;
+    }
+    for (int m = 0; m < 2; ++m) {
+      hc[m].leaf_updates = snap[i].cnt[m].leaf_updates;
+      hc[m].steps = snap[i].cnt[m].steps;
+    }
+    if (cudaMemcpy(h->cntbuf, hc, 2 * sizeof(MeshCounts), cudaMemcpyHostToDevice) != cudaSuccess) st = MR_ECUDA;
+    h->launches = snap[i].launches;
+  }
+  b->launches = launches0;
+  drop_graphs(*b);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  release();
+  if (st != MR_OK) return st;
+  store_schedule(b);
+  if (ms_fixed) *ms_fixed = base;
+  if (ms_tuned) *ms_tuned = tuned;
   return MR_OK;
 }
 

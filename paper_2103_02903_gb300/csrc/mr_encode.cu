@@ -231,12 +231,12 @@ __global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB,
 
 template <int D, int Q, int F>
 void launch_project_t(const Group& G, int cur, int k, cudaStream_t st) {
-  mr_launch_pdl(k_project<D, Q, F>, mr_tile_grid(G, G.proj_cells[k], 32, 8), dim3(32, PopRows<Q>::value),
+  mr_launch_pdl(k_project<D, Q, F>, mr_tile_grid(G, G.proj_cells[k], 32, G.bps[MR_PH_PROJECT]), dim3(32, PopRows<Q>::value),
                 mr_pre_bytes(G), st, G.dev, G.n, cur, k);
 }
 template <int D, int Q, int F>
 void launch_details_t(const Group& G, int cur, cudaStream_t st) {
-  mr_launch_pdl(k_details<D, Q, F>, mr_tile_grid(G, G.capI, 32, 8), dim3(32, PopRows<Q>::value), mr_pre_bytes(G),
+  mr_launch_pdl(k_details<D, Q, F>, mr_tile_grid(G, G.capI, 32, G.bps[MR_PH_DETAILS]), dim3(32, PopRows<Q>::value), mr_pre_bytes(G),
                 st, G.dev, G.n, cur);
 }
 

@@ -309,6 +309,13 @@ struct __align__(16) InstDev {
   const float* Wsf;   // the same in FP32
 };
 
+// Launch schedule of a group: for each phase, the blocks per SM its tiled
+// kernels may use (the grid is at most nsm times that; blocks stride over
+// the tiles).  Defaults below; mr_lbm_batch_autotune picks them per group.
+enum { MR_PH_PROJECT = 0, MR_PH_DETAILS, MR_PH_FLAGS, MR_PH_COMPACT, MR_PH_REMESH, MR_PH_PREDICT, MR_PH_STREAM,
+       MR_NPH };
+#define MR_DEFAULT_BPS {8, 8, 4, 8, 8, 8, 8}
+
 // Instances of one scheme and storage form, stepped by shared launches: every
 // step kernel covers all of them (a single solver is a group of one).  All
 // instances of a group are on the same mesh parity.
@@ -318,6 +325,7 @@ struct Group {
   int n;
   int d, Q, scheme, form;
   int s;                 // half-width of the prediction (all instances alike)
+  int bps[MR_NPH];       // launch schedule: blocks per SM of each phase
   int chunks;            // dense chunks of all instances
   int span;              // maximum of J - J_min
   bool grade;            // some instance has J > J_min + 1

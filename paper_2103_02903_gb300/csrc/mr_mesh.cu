@@ -706,17 +706,17 @@ __global__ void __launch_bounds__(256) k_leaves_check(Geo g, const uint8_t* __re
 
 void mr_launch_flags_T(const Group& G, int cur, cudaStream_t st) {
   const int D_ = G.d;
-  MR_DISPATCH_D_PDL(k_flags_T, mr_tile_grid(G, G.capI, 256, 4), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
+  MR_DISPATCH_D_PDL(k_flags_T, mr_tile_grid(G, G.capI, 256, G.bps[MR_PH_FLAGS]), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
 }
 void mr_launch_flags_H(const Group& G, int cur, cudaStream_t st) {
   const int D_ = G.d;
-  MR_DISPATCH_D_PDL(k_flags_H, mr_tile_grid(G, G.capI, 256, 4), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
+  MR_DISPATCH_D_PDL(k_flags_H, mr_tile_grid(G, G.capI, 256, G.bps[MR_PH_FLAGS]), 256, mr_pre_bytes(G), st, G.dev, G.n, cur);
 }
 void mr_launch_grade(const Group& G, cudaStream_t st) {
   if (G.s > 1) return mr_launch_grade_w(G, st);
   const int D_ = G.d;
   if (G.grade)
-    MR_DISPATCH_D_PDL(k_grade, mr_tile_grid(G, (long long)G.chunks * MR_DENSE_ALIGN, 256, 4), 256, mr_pre_bytes(G), st,
+    MR_DISPATCH_D_PDL(k_grade, mr_tile_grid(G, (long long)G.chunks * MR_DENSE_ALIGN, 256, G.bps[MR_PH_FLAGS]), 256, mr_pre_bytes(G), st,
                   G.dev, G.n);
 }
 // dense kernels: one block per 1024-cell chunk of every instance
@@ -734,7 +734,7 @@ void mr_launch_mark_ghosts(const Group& G, cudaStream_t st) {
 }
 void mr_launch_compact(const Group& G, int dst, cudaStream_t st) {
   // one warp per chunk, 8 warps per block, at most 8 blocks per SM
-  const int grid = std::min((G.chunks + 7) / 8, 8 * G.nsm);
+  const int grid = std::min((G.chunks + 7) / 8, G.bps[MR_PH_COMPACT] * G.nsm);
   mr_launch_pdl(k_count, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
   mr_launch_pdl(k_scan_blocks, G.n, 1024, 0, st, G.dev, dst);
   mr_launch_pdl(k_scatter, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, dst, G.chunks);

@@ -720,18 +720,18 @@ __global__ void __launch_bounds__(256) k_project_dense(Geo g, MeshDev B, const v
 
 template <int Q, int F>
 void launch_remesh_t(const Group& G, int cur, cudaStream_t st) {
-  mr_launch_pdl(k_remesh_copy<Q, F>, mr_tile_grid(G, G.capL + G.capI, 32, 8), dim3(32, PopRows<Q>::value),
+  mr_launch_pdl(k_remesh_copy<Q, F>, mr_tile_grid(G, G.capL + G.capI, 32, G.bps[MR_PH_REMESH]), dim3(32, PopRows<Q>::value),
                 mr_pre_bytes(G), st, G.dev, G.n, cur);
 }
 template <int D, int Q, int F>
 void launch_predict_t(const Group& G, int dst, int kl, cudaStream_t st) {
   // ghosts and leaves of one level: at most twice its cells
-  mr_launch_pdl(k_predict_level<D, Q, F>, mr_tile_grid(G, 2 * G.pred_cells[kl], 32, 8), dim3(32, PopRows<Q>::value),
+  mr_launch_pdl(k_predict_level<D, Q, F>, mr_tile_grid(G, 2 * G.pred_cells[kl], 32, G.bps[MR_PH_PREDICT]), dim3(32, PopRows<Q>::value),
                 mr_pre_bytes(G), st, G.dev, G.n, dst, kl);
 }
 template <int SC, int F>
 void launch_stream_t(const Group& G, int dst, int ds, int dc, int count, cudaStream_t st) {
-  mr_launch_pdl(k_stream_collide<SC, F>, mr_tile_grid(G, G.capL, MR_WIN_TPB, 8), MR_WIN_TPB, mr_pre_bytes(G), st, G.dev,
+  mr_launch_pdl(k_stream_collide<SC, F>, mr_tile_grid(G, G.capL, MR_WIN_TPB, G.bps[MR_PH_STREAM]), MR_WIN_TPB, mr_pre_bytes(G), st, G.dev,
                 G.n, dst, ds, dc, count);
 }
 template <int SC, int F>

@@ -583,16 +583,16 @@ __global__ void __launch_bounds__(128) k_stream_collide_w(const InstDev* __restr
 // ------------------------------------------------------------------ launchers
 template <int D, int S, int F>
 void launch_details_w(const Group& G, int cur, cudaStream_t st) {
-  mr_launch_pdl(k_details_w<D, S, F>, mr_tile_grid(G, G.capI, 128, 8), 128, mr_pre_bytes(G), st, G.dev, G.n, cur);
+  mr_launch_pdl(k_details_w<D, S, F>, mr_tile_grid(G, G.capI, 128, G.bps[MR_PH_DETAILS]), 128, mr_pre_bytes(G), st, G.dev, G.n, cur);
 }
 template <int D, int S, int F>
 void launch_predict_w(const Group& G, int dst, int kl, cudaStream_t st) {
-  mr_launch_pdl(k_predict_level_w<D, S, F>, mr_tile_grid(G, 2 * G.pred_cells[kl], 128, 8), 128, mr_pre_bytes(G), st,
+  mr_launch_pdl(k_predict_level_w<D, S, F>, mr_tile_grid(G, 2 * G.pred_cells[kl], 128, G.bps[MR_PH_PREDICT]), 128, mr_pre_bytes(G), st,
                 G.dev, G.n, dst, kl);
 }
 template <int SC, int S, int F>
 void launch_stream_w(const Group& G, int dst, int ds, int dc, int count, cudaStream_t st) {
-  mr_launch_pdl(k_stream_collide_w<SC, S, F>, mr_tile_grid(G, G.capL, 128, 8), 128, mr_pre_bytes(G), st, G.dev, G.n,
+  mr_launch_pdl(k_stream_collide_w<SC, S, F>, mr_tile_grid(G, G.capL, 128, G.bps[MR_PH_STREAM]), 128, mr_pre_bytes(G), st, G.dev, G.n,
                 dst, ds, dc, count);
 }
 template <int D, int S, int F>
@@ -646,7 +646,7 @@ void mr_launch_stream_collide_w(const Group& G, int dst, int do_stream, int do_c
 
 void mr_launch_grade_w(const Group& G, cudaStream_t st) {
   if (!G.grade) return;
-  const int grid = mr_tile_grid(G, (long long)G.chunks * MR_DENSE_ALIGN, 256, 4);
+  const int grid = mr_tile_grid(G, (long long)G.chunks * MR_DENSE_ALIGN, 256, G.bps[MR_PH_FLAGS]);
   const size_t sm = mr_pre_bytes(G);
   if (G.d == 1) {
     if (G.s == 2) mr_launch_pdl(k_grade_w<1, 2>, grid, 256, sm, st, G.dev, G.n);

@@ -89,3 +89,53 @@ def test_batch_rules():
     b.synchronize()
     assert all(s.num_leaves() > 0 for s in b.instances)
     b.close()
+
+
+def _small_serving(n=8, seed=3):
+    cases = W.serving_batch(seed=seed, n=n, levels=(6, 7), precision="fp16")
+    return cases
+
+
+def test_autotune_leaves_the_batch_as_it_was_and_results_do_not_depend_on_the_schedule():
+    """mr_lbm_batch_autotune times candidate schedules from a snapshot of
+    every instance and puts the snapshot back: the leaves and the counters
+    after the call are those before it.  Schedules change grid sizes only,
+    so the tuned batch steps to the same bits as one on the default
+    schedule; a batch of the same signature created later starts from the
+    cached schedule."""
+    from paper_2103_02903_gb300.binding import Batch, MrError
+    cases = _small_serving()
+    a = Batch([c for c, _ in cases])
+    ref = Batch([c for c, _ in cases])
+    for bb in (a, ref):
+        for inst, (c, u) in zip(bb.instances, cases):
+            inst.init(u)
+        bb.step(3)
+        bb.synchronize()
+    before = [inst.get_leaves() for inst in a.instances]
+    counts = [inst.counters() for inst in a.instances]
+    default = a.schedule()
+    ms_fixed, ms_tuned = a.autotune(trial_steps=2)
+    assert ms_fixed > 0 and ms_tuned > 0
+    after = [inst.get_leaves() for inst in a.instances]
+    for x, y in zip(before, after):
+        for u, v in zip(x, y):
+            assert np.array_equal(u, v)
+    assert [inst.counters() for inst in a.instances] == counts
+    tuned = a.schedule()
+    assert len(tuned) == a.parts() and all(len(p) == 7 for p in tuned)
+    assert all(1 <= v <= 32 for p in tuned for v in p)
+    a.step(4)
+    ref.step(4)
+    for x, y in zip(a.instances, ref.instances):
+        for u, v in zip(x.get_leaves(), y.get_leaves()):
+            assert np.array_equal(u, v)
+    # the cache: a new batch of the same configurations starts tuned
+    c = Batch([c for c, _ in cases])
+    assert c.schedule() == tuned
+    with pytest.raises(MrError):
+        c.set_schedule(0, [0] * 7)
+    c.set_schedule(0, default[0])
+    assert c.schedule()[0] == default[0]
+    for bb in (a, ref, c):
+        bb.close()
