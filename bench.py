@@ -68,14 +68,15 @@ ALG_BYTES_PER_LEAF = 2 * 16 * 8 + 5
 ALG_FLOPS_PER_LEAF = 320.0
 FORM_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
 # DRAM bytes (read + write) of one launch of the transport + collision kernel
-# per leaf, from an ncu capture of the 7th launch of this workload (about
-# 45.7k leaves, cold cache: 2.93 MB read, 0 written in FP16 storage; 8.97 MB
-# read, 0 written in FP64); `traffic` scales them by the leaves of the timed
-# launches.  They hold for the kernel as captured and must be retaken when it
-# changes.
-CAPTURED_DRAM_BYTES_PER_LEAF = {"fp16": 2.928896e6 / 45729.25, "fp64": 8.9728e6 / 45729.25}
-CAPTURED_DRAM_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one cold launch (~45.7k leaves), "
-                      "scaled by the leaves of the timed launches")
+# per leaf, from ncu captures of this workload: FP16 storage, the first timed
+# launch after the 200-step advance (about 105.2k leaves: 6.20 MB read, 1.8 kB
+# written); FP64, the 7th launch from the initial condition (about 45.7k
+# leaves: 8.97 MB read, nothing written).  `traffic` scales them by the
+# leaves of the timed launches.  They hold for the kernel as captured and
+# must be retaken when it changes.
+CAPTURED_DRAM_BYTES_PER_LEAF = {"fp16": (6.201088e6 + 1.792e3) / 105187.0, "fp64": 8.9728e6 / 45729.25}
+CAPTURED_DRAM_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one cold launch, per leaf, scaled "
+                      "by the leaves of the timed launches")
 FORM_DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}
 
 
