@@ -22,8 +22,8 @@
 //   cell below a level-(j+1) cell c needs c's +-s neighbourhood in the tree,
 //   which excludes the leaf's own children, so such cells lie 2s or more
 //   level-(j+2) cells away from the leaf's faces, beyond the W = 2s window.
-// Lattices with diagonal velocities keep s = 1 (their corner terms are
-// built on the 5 x 5 block of that window).
+// Lattices with diagonal velocities (D2Q9) add the four corner cells of each
+// diagonal velocity over the (2W+1)^2 block around the leaf.
 //
 // The tuned s = 1 kernels are untouched; these are plain one-thread-per-cell
 // kernels that look cells up through the dense index map.
@@ -259,9 +259,10 @@ __global__ void __launch_bounds__(256) k_grade_w(const InstDev* __restrict__ IB,
 
 // ------------------------------------------------------------------ ghosts
 // Cells the transport of a leaf reads that are not in the tree: the window
-// of W = 2s cells on either side along each axis.  Each one not yet marked
-// becomes a ghost, and its parent's (2s+1)^D stencil is marked the same way
-// (cells outside the tree become ghosts), towards J_min.
+// of W = 2s cells on either side along each axis, and for a lattice with
+// diagonal velocities the whole (2W+1)^2 block around the leaf.  Each one
+// not yet marked becomes a ghost, and its parent's (2s+1)^D stencil is
+// marked the same way (cells outside the tree become ghosts), towards J_min.
 template <int D, int S>
 __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict__ IB,
                                                        const int* __restrict__ chunk_pre, int n) {
@@ -281,10 +282,18 @@ __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict
     if (c >= g.ncode[l] || (cls[c0 + (c - cb)] & 3u) != MR_C_LEAF) continue;
     int x[3] = {0, 0, 0};
     mr_decode_d<D>(g, l, c, x);
-    for (int w = 0; w < D * 2 * W; ++w) {
-      const int axis = w / (2 * W), o = w % (2 * W), off = o < W ? o - W : o - W + 1;  // -W..-1, 1..W
+    const bool block = D == 2 && g.diag;
+    const int nw = block ? (2 * W + 1) * (2 * W + 1) : D * 2 * W;
+    for (int w = 0; w < nw; ++w) {
       int nb[3] = {x[0], x[1], x[2]};
-      nb[axis] += off;
+      if (block) {
+        if (w == (2 * W + 1) * W + W) continue;  // the leaf itself
+        nb[0] += w % (2 * W + 1) - W;
+        nb[1] += w / (2 * W + 1) - W;
+      } else {
+        const int axis = w / (2 * W), o = w % (2 * W), off = o < W ? o - W : o - W + 1;  // -W..-1, 1..W
+        nb[axis] += off;
+      }
       if (!mr_nbr_mesh_d<D>(g, l, nb)) continue;
       const uint32_t gw = g.base[l] + mr_encode_d<D>(g, l, nb);
       if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
@@ -436,7 +445,26 @@ __device__ __forceinline__ const double* wide_tab<double>(const InstDev& si) { r
 template <>
 __device__ __forceinline__ const float* wide_tab<float>(const InstDev& si) { return si.Wsf; }
 
-// One thread per leaf, lattices with axis velocities.  Along each axis a the
+// Weight of the level-l1 cell at position 2k + rel along axis a in the
+// incoming-minus-outgoing finest values of the level-(l1 - 1) leaf k, for
+// the velocity sign s (the corner cells of a diagonal velocity): s > 0:
+// R_{2k-1} - R_{2k+1}, s < 0: L_{2k+2} - L_{2k}; the upwind term is absent at
+// a non-periodic face (that cell is outside the domain).
+template <class C>
+__device__ __forceinline__ C wide_corner_weight(const Geo& g, const C* __restrict__ Wt, int l1, int a, int k, int rel,
+                                                int s, int W) {
+  const int per = g.periodic[a], N1 = g.n[l1][a], N = g.n[l1 - 1][a];
+  const int tab = s > 0 ? 2 : 3;
+  const int ru = s > 0 ? -1 : 2, ro = s > 0 ? 1 : 0;
+  const int du = rel - ru, dd = rel - ro;
+  C w = (C)0;
+  if ((per || (s > 0 ? k > 0 : k < N - 1)) && du >= -W && du <= W)
+    w += Wt[MR_WWIDX(l1, a, mr_slot_w(2 * k + ru, N1, per, W), tab, W) + du + W];
+  if (dd >= -W && dd <= W) w -= Wt[MR_WWIDX(l1, a, mr_slot_w(2 * k + ro, N1, per, W), tab, W) + dd + W];
+  return w;
+}
+
+// One thread per leaf.  Along each axis a the
 // populations moving along a take the flattened weights of the leaf's slot
 // over its row k - W .. k + W (W = 2s), the boundary value of a
 // non-periodic face they enter through, and for every refined cell of the
@@ -446,6 +474,18 @@ __device__ __forceinline__ const float* wide_tab<float>(const InstDev& si) { ret
 // 2k + 1; for -1 the left edges of 2k + 2 and 2k.  A child's detail is
 // averaged over the 2^{d-1} children on the row (their transverse sum is
 // what the row-collapsed reconstruction sees).
+//
+// Diagonal velocities (D2Q9): the sum over E minus the sum over A is the
+// two axis strips (above) plus four single finest cells: + the one
+// diagonally upwind of the leaf, + the leaf's own downwind corner cell, -
+// the two that mix the two.  With the tensor-product prediction each is the
+// product of two one-dimensional reconstructions, so together they are the
+// product of the two axes' in-minus-out weights applied to the (2W+1)^2
+// block of level-j values, plus, for every refined cell of the block, its
+// children's details through the products of the level-(j+1) weights.  At
+// a corner of a non-periodic domain the outside cells take the boundary
+// value of the face crossed first along x, so the four cells leave minus
+// the value of the y face.
 template <int SC, int S, int F>
 __global__ void __launch_bounds__(128) k_stream_collide_w(const InstDev* __restrict__ IB, int ngrp, int dst,
                                                           int do_stream, int do_collide, int count) {
@@ -566,8 +606,107 @@ __global__ void __launch_bounds__(128) k_stream_collide_w(const InstDev* __restr
           }
         }
       }
+      if constexpr (Sc::DIAG) {
+        using B2 = WBox<2, S>;
+        constexpr int P0 = Sc::DIAG0;
+        const int x = xc[0], y = xc[1], Nx = g.n[l][0], Ny = g.n[l][1];
+        const int slx = mr_slot_w(x, Nx, g.periodic[0], W), sly = mr_slot_w(y, Ny, g.periodic[1], W);
+        const C* wx[2] = {Wt + MR_WWIDX(l, 0, slx, 0, W), Wt + MR_WWIDX(l, 0, slx, 1, W)};
+        const C* wy[2] = {Wt + MR_WWIDX(l, 1, sly, 0, W), Wt + MR_WWIDX(l, 1, sly, 1, W)};
+        C acc[4] = {(C)0, (C)0, (C)0, (C)0};
+        for (int bb = 0; bb < NW; ++bb) {
+          const C wy0 = wy[0][bb], wy1 = wy[1][bb];
+          if (wy0 == (C)0 && wy1 == (C)0) continue;  // zero row: adds nothing
+          for (int aa = 0; aa < NW; ++aa) {
+            const C wx0 = wx[0][aa], wx1 = wx[1][aa];
+            if (wx0 == (C)0 && wx1 == (C)0) continue;
+            const bool self = aa == W && bb == W;
+            int32_t e = 0;
+            if (!self) {
+              int nb[3] = {x + aa - W, y + bb - W, 0};
+              if (!mr_nbr_mesh_d<2>(g, l, nb)) continue;  // outside a non-periodic domain: zero weight
+              e = Bm.map[g.base[l] + mr_encode_d<2>(g, l, nb)];
+              if (e == MR_MAP_NONE) {
+                mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
+                continue;
+              }
+            }
+            const ValPtr<St> vp = mr_resolve<St>(g, Bm, LFin, e);
+            for (int t = 0; t < 4; ++t) {
+              const int p = P0 + t;
+              const C wab = (Sc::eta(p, 0) > 0 ? wx0 : wx1) * (Sc::eta(p, 1) > 0 ? wy0 : wy1);
+              if (wab == (C)0) continue;
+              acc[t] += wab * (self ? fs[p] : ld_off<F>(vp, p, offv));
+            }
+          }
+        }
+        // refined cells of the block: their children's details
+        if (l < g.J) {
+          for (int bb = 0; bb < NW; ++bb)
+            for (int aa = 0; aa < NW; ++aa) {
+              if (aa == W && bb == W) continue;
+              C wcx[2][2], wcy[2][2];  // [sign index][child offset]
+              bool any = false;
+              for (int si = 0; si < 2; ++si)
+                for (int o = 0; o < 2; ++o) {
+                  wcx[si][o] = wide_corner_weight<C>(g, Wt, l + 1, 0, x, 2 * (aa - W) + o, si == 0 ? 1 : -1, W);
+                  wcy[si][o] = wide_corner_weight<C>(g, Wt, l + 1, 1, y, 2 * (bb - W) + o, si == 0 ? 1 : -1, W);
+                  any = any || wcx[si][o] != (C)0;
+                }
+              if (!any) continue;
+              int nb[3] = {x + aa - W, y + bb - W, 0};
+              if (!mr_nbr_mesh_d<2>(g, l, nb)) continue;
+              const int32_t e = Bm.map[g.base[l] + mr_encode_d<2>(g, l, nb)];
+              if (e == MR_MAP_NONE || (((uint32_t)e) >> 30) != MR_CLS_INT) continue;
+              int32_t st[B2::N], ce[4];
+              bool ok = wide_stencil<2, S>(g, Bm, l, nb, st);
+              const uint32_t ncode = mr_encode_d<2>(g, l, nb);
+              for (int ci = 0; ci < 4; ++ci) {
+                ce[ci] = Bm.map[g.base[l + 1] + ((ncode << 2) | (uint32_t)ci)];
+                ok = ok && ce[ci] != MR_MAP_NONE;
+              }
+              if (!ok) {
+                mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
+                continue;
+              }
+              for (int t = 0; t < 4; ++t) {
+                const int p = P0 + t;
+                const int ix = Sc::eta(p, 0) > 0 ? 0 : 1, iy = Sc::eta(p, 1) > 0 ? 0 : 1;
+                // details are exact on constants: stored values suffice
+                C v[B2::N];
+                for (int kk = 0; kk < B2::N; ++kk) v[kk] = ld_c<C>(mr_resolve<St>(g, Bm, LFin, st[kk]), p);
+                C corr = (C)0;
+                for (int ci = 0; ci < 4; ++ci) {
+                  const C w = wcx[ix][ci & 1] * wcy[iy][ci >> 1];
+                  if (w == (C)0) continue;
+                  corr += w * (ld_c<C>(mr_resolve<St>(g, Bm, LFin, ce[ci]), p) -
+                               wide_predict<2, S, C, false>(v, ci, g.cross_sign));
+                }
+                acc[t] += corr;
+              }
+            }
+        }
+        const C scale2 = scale * scale;
+        for (int t = 0; t < 4; ++t) {
+          const int p = P0 + t;
+          const int sx = Sc::eta(p, 0), sy = Sc::eta(p, 1);
+          const bool outx = !g.periodic[0] && (sx > 0 ? x == 0 : x == Nx - 1);
+          const bool outy = !g.periodic[1] && (sy > 0 ? y == 0 : y == Ny - 1);
+          if (outx && outy) acc[t] -= bc_value<C>(g, g.bc[sy > 0 ? 2 : 3], fs, p, Sc::opp(p));
+          out[p] += scale2 * acc[t];
+        }
+      }
     }
-    if (do_collide) Sc::template collide<C>(g, out);
+    if (do_collide) {
+      Sc::template collide<C>(g, out);
+      if constexpr (Sc::DIAG) {
+        if (g.obstacle) {
+          const double phi = obstacle_fraction(g, l, code);
+          if (phi > 0.0)
+            for (int p = 0; p < Q; ++p) out[p] = (C)phi * MR_K(C, g, feq0[p]) + ((C)1 - (C)phi) * out[p];
+        }
+      }
+    }
     bool finite = true;
     for (int p = 0; p < Q; ++p) {
       finite = finite && is_finite_bits(out[p]);
@@ -634,11 +773,12 @@ void mr_launch_predict_level_w(const Group& G, int dst, int kl, cudaStream_t st)
 }
 
 void mr_launch_stream_collide_w(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st, int count) {
-  switch (G.scheme) {  // the schemes with axis velocities (D2Q9 keeps s = 1)
+  switch (G.scheme) {
     case 0: MR_W_S(launch_stream_w, G.form, G.s, 0, G, dst, do_stream, do_collide, count, st); break;
     case 1: MR_W_S(launch_stream_w, G.form, G.s, 1, G, dst, do_stream, do_collide, count, st); break;
     case 2: MR_W_S(launch_stream_w, G.form, G.s, 2, G, dst, do_stream, do_collide, count, st); break;
     case 3: MR_W_S(launch_stream_w, G.form, G.s, 3, G, dst, do_stream, do_collide, count, st); break;
+    case 4: MR_W_S(launch_stream_w, G.form, G.s, 4, G, dst, do_stream, do_collide, count, st); break;
     case 5: MR_W_S(launch_stream_w, G.form, G.s, 5, G, dst, do_stream, do_collide, count, st); break;
     default: break;
   }

@@ -14,7 +14,9 @@ each population field's max norm, per step from the oracle's state (the
 decisions must then agree bit for bit) and along independent trajectories
 (a decision may differ only within rounding of its threshold, see
 test_gpu_fullsize_parity.py), on periodic and copy faces, in 1D, 2D and 3D,
-plus the reduced-precision forms, the batch and the refusals.
+plus the reduced-precision forms, the batch and the refusals.  D2Q9 adds the
+diagonal velocities' corner terms over the (4s+1)^2 block around each leaf,
+with moving-wall bounce back, the obstacle and the corners of a closed box.
 """
 import numpy as np
 import pytest
@@ -39,6 +41,9 @@ CASES = [
     ("euler_2d copy", lambda s: W.euler_2d(seed=s, max_level=6), 12),
     ("euler_2d periodic", lambda s: _euler_periodic(s, max_level=6), 12),
     ("advection_3d periodic", lambda s: W.advection_3d(seed=s, max_level=4), 4),
+    ("d2q9 vortices periodic", lambda s: W.vortices_2d(seed=s, max_level=6), 10),
+    ("d2q9 obstacle, moving walls", lambda s: W.ns_obstacle_2d(seed=s, max_level=6), 10),
+    ("d2q9 closed box, bounce back", lambda s: W.vortices_2d(seed=s, max_level=6, bc="bounce_back"), 10),
 ]
 
 
