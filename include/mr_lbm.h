@@ -114,8 +114,7 @@ typedef struct {
   int pred_s;            /* half-width s of the prediction operator, 1, 2 or 3 (Table 1; 0
                             reads as 1): (2s+1)^d stencils, grading of radius s, transport
                             windows of 2s cells (blocks of (4s+1)^2 cells for D2Q9).
-                            s = 2, 3: not with the exact collision (MR_EINVAL);
-                            mr_lbm_adjoint needs s = 1 */
+                            mr_lbm_adjoint needs s = 1 (MR_EINVAL otherwise) */
   int bc[6];             /* mr_bc per face: -x, +x, -y, +y, -z, +z */
   int cross_sign;        /* +1: tensor-product prediction (default, also when 0);
                             -1: diagonal term with the sign printed in Sec. 4.1 */

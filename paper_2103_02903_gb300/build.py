@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmrlbm.so")
 SOURCES = ["mr_api.cu", "mr_encode.cu", "mr_mesh.cu", "mr_stream.cu", "mr_noalloc.cu", "mr_adjoint.cu",
            "mr_exact.cu", "mr_wide.cu"]
-HEADERS = ["mr_internal.cuh", "mr_common.cuh", "mr_handle.cuh", "mr_schemes.cuh"]
+HEADERS = ["mr_internal.cuh", "mr_common.cuh", "mr_handle.cuh", "mr_schemes.cuh", "mr_wide.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -337,8 +337,6 @@ mr_status validate(const mr_lbm_config* c) {
   if (!(c->lambda > 0) || !(c->eps >= 0) || c->mu_bar < 0) return MR_EINVAL;
   if (c->pred_s < 0 || c->pred_s > 3) return MR_EINVAL;
   const int s_pred = c->pred_s ? c->pred_s : 1;
-  // s = 2, 3: the leaf collision (the exact collision is built for s = 1)
-  if (s_pred > 1 && c->exact_collision) return MR_EINVAL;
   if (c->mu_bar > 2 * s_pred + 1) return MR_EINVAL;  // the regularity guess lies in [0, 2s + 1] (Sec. 5.1)
   if (c->precision < MR_FP64 || c->precision > MR_FP32_BF16STORE) return MR_EINVAL;
   if (c->min_level < 2 || c->max_level < c->min_level || c->max_level > 15) return MR_EINVAL;

@@ -9,10 +9,10 @@
 //   up   (J .. J_min): a leaf takes its post-transport value, an internal
 //        cell the average of its children (Def. Projection, children in
 //        index order, then 2^-d);
-//   down (J_min+1 .. J): every cell outside the tree takes the s = 1
-//        prediction from its parent's 3^d stencil (the reconstruction
-//        operator of Sec. 4.4); on level J every cell is then collided in
-//        place;
+//   down (J_min+1 .. J): every cell outside the tree takes the prediction
+//        of half-width s from its parent's (2s+1)^d stencil (the
+//        reconstruction operator of Sec. 4.4); on level J every cell is
+//        then collided in place;
 //   average (J-1 .. J_min): every cell outside the tree, and every leaf,
 //        takes the average of its children (collided on level J, averaged
 //        below): the leaf's average over its finest cells, 2^{-d(J-j)} times
@@ -21,7 +21,7 @@
 //        penalisation follows as after the leaf collision.
 // Single instances in the FP64 form; the cost is that of the dense level-J
 // grid, the explosion the paper warns about, which 2D grids up to J = 10 fit.
-#include "mr_schemes.cuh"
+#include "mr_wide.cuh"
 
 namespace {
 
@@ -103,6 +103,49 @@ __global__ void __launch_bounds__(256) k_exact_down(const InstDev* __restrict__ 
   for (int p = 0; p < Q; ++p) Fd[(size_t)p * nd + gi] = f[p];
 }
 
+// The same for the prediction of half-width s = 2, 3.
+template <int SC, int S>
+__global__ void __launch_bounds__(256) k_exact_down_w(const InstDev* __restrict__ IB, int dst, int kl,
+                                                      double* __restrict__ Fd, long long nd) {
+  using Sc = Scheme<SC>;
+  using B = WBox<Sc::D, S>;
+  constexpr int D = Sc::D, Q = Sc::Q;
+  __shared__ InstDev si;
+  int have = -1;
+  mr_inst_use(si, have, IB, 0);
+  mr_grid_dep();
+  const Geo& g = si.g;
+  const MeshDev& Bm = si.mesh[dst];
+  const int l = g.Jmin + kl;
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncode[l]) return;
+  const uint32_t gi = g.base[l] + c;
+  const int32_t e = Bm.map[gi];
+  const bool tree = e != MR_MAP_NONE && (((uint32_t)e) >> 30) <= MR_CLS_INT;
+  double f[Q];
+  if (tree) {
+    if (l < g.J) return;  // set on the way up
+    for (int p = 0; p < Q; ++p) f[p] = Fd[(size_t)p * nd + gi];
+  } else {
+    int x[3] = {0, 0, 0};
+    mr_decode_d<D>(g, l, c, x);
+    uint32_t st[B::N];
+    for (int k = 0; k < B::N; ++k) {
+      int s[3] = {(x[0] >> 1) + k % B::W1 - S, D >= 2 ? (x[1] >> 1) + (k / B::W1) % B::W1 - S : 0, 0};
+      mr_nbr_stencil_d<D>(g, l - 1, s);
+      st[k] = g.base[l - 1] + mr_encode_d<D>(g, l - 1, s);
+    }
+    const int ci = (x[0] & 1) | (D == 2 ? (x[1] & 1) << 1 : 0);
+    for (int p = 0; p < Q; ++p) {
+      double v[B::N];
+      for (int k = 0; k < B::N; ++k) v[k] = Fd[(size_t)p * nd + st[k]];
+      f[p] = wide_predict<D, S, double, false>(v, ci, g.cross_sign);
+    }
+  }
+  if (l == g.J) Sc::template collide<double>(g, f);
+  for (int p = 0; p < Q; ++p) Fd[(size_t)p * nd + gi] = f[p];
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_exact_average(const InstDev* __restrict__ IB, int dst, int kl,
                                                        double* __restrict__ Fd, long long nd) {
@@ -174,8 +217,15 @@ void launch_exact_t(const Group& G, int dst, double* Fd, long long nd, cudaStrea
   auto cells = [&](int k) { return k == 0 ? G.proj_cells[span] : G.pred_cells[k]; };  // level J_min + k
   for (int k = span; k >= 0; --k)
     mr_launch_pdl(k_exact_up<D>, (unsigned)((cells(k) + 255) / 256), 256, 0, st, G.dev, dst, k, Fd, nd);
-  for (int k = 1; k <= span; ++k)
-    mr_launch_pdl(k_exact_down<SC>, (unsigned)((cells(k) + 255) / 256), 256, 0, st, G.dev, dst, k, Fd, nd);
+  for (int k = 1; k <= span; ++k) {
+    const unsigned grid = (unsigned)((cells(k) + 255) / 256);
+    if (G.s == 2)
+      mr_launch_pdl(k_exact_down_w<SC, 2>, grid, 256, 0, st, G.dev, dst, k, Fd, nd);
+    else if (G.s == 3)
+      mr_launch_pdl(k_exact_down_w<SC, 3>, grid, 256, 0, st, G.dev, dst, k, Fd, nd);
+    else
+      mr_launch_pdl(k_exact_down<SC>, grid, 256, 0, st, G.dev, dst, k, Fd, nd);
+  }
   for (int k = span - 1; k >= 0; --k)
     mr_launch_pdl(k_exact_average<D>, (unsigned)((cells(k) + 255) / 256), 256, 0, st, G.dev, dst, k, Fd, nd);
   mr_launch_pdl(k_exact_leaves<SC>, (unsigned)(G.nsm * 8), 128, 0, st, G.dev, dst, (const double*)Fd, nd);

@@ -70,7 +70,6 @@ def _bad(name):
         "max_below_min": (W.advection_1d, dict(max_level=6), dict(min_level=5, max_level=4)),
         "max_level_16": (W.advection_1d, dict(max_level=6), dict(max_level=16)),
         "prediction_s4": (W.advection_1d, dict(max_level=6), dict(pred_s=4)),
-        "prediction_s3_exact_collision": (W.euler_2d, dict(max_level=5), dict(pred_s=3, exact_collision=1)),
         "mu_bar_above_order_s2": (W.advection_1d, dict(max_level=6), dict(pred_s=2, mu_bar=6)),
         "half_periodic_axis": (W.advection_1d, dict(max_level=6),
                                dict(bc=["periodic", "copy"] + ["periodic"] * 4)),
@@ -93,7 +92,7 @@ def _bad(name):
 @pytest.mark.parametrize("name", [
     "negative_eps", "lambda_zero", "relaxation_above_2", "mu_bar_negative", "mu_bar_above_order",
     "min_level_below_2",
-    "max_below_min", "max_level_16", "prediction_s4", "prediction_s3_exact_collision",
+    "max_below_min", "max_level_16", "prediction_s4",
     "mu_bar_above_order_s2", "half_periodic_axis", "obstacle_not_d2q9",
     "moving_wall_not_d2q9", "printed_sign_d2q9", "exact_collision_fp16", "exact_collision_3d",
     "d3q6_level_11", "d3q6_dense_space", "d2_dense_space", "roots_overflow_codes"])

@@ -178,3 +178,24 @@ def test_adjoint_refuses_wide_prediction():
     with pytest.raises(MrError) as ei:
         s.adjoint(u, 4, checkpoint_every=2)
     assert ei.value.status == 1  # MR_EINVAL
+
+
+@pytest.mark.parametrize("s", [2, 3])
+@pytest.mark.parametrize("name,make", [("euler_2d", lambda sd: W.euler_2d(seed=sd, max_level=6)),
+                                       ("burgers_1d", lambda sd: W.burgers_1d(seed=sd, max_level=8)),
+                                       ("d2q9 obstacle", lambda sd: W.ns_obstacle_2d(seed=sd, max_level=6))])
+def test_exact_collision(name, make, s):
+    """The original adaptive collision (Eq. sourceoferror) on the
+    reconstruction of half-width s, per step from the oracle's state."""
+    cfg, u = _cfg(make, 8, s)
+    cfg["exact_collision"] = 1
+    ref = Oracle(cfg)
+    ref.init(u)
+    gpu = _solver(cfg)
+    gpu.init(u)
+    for it in range(6):
+        if it:
+            _load(gpu, ref, cfg)
+        gpu.step(1)
+        ref.step(1)
+        _check(gpu, ref, cfg, "exact %s s=%d step %d" % (name, s, it))
