@@ -122,7 +122,7 @@ def _args():
                    help="also measure the other configurations: D1Q2 advection J=9, D1Q2 Burgers and D1Q3 "
                         "dam break J=12 per form, D2Q9 obstacle J=10 with its adjoint (1) or not (0)")
     p.add_argument("--ns-steps", type=int, default=50, help="timed steps of the D2Q9 obstacle leg")
-    p.add_argument("--adjoint-steps", type=int, default=400,
+    p.add_argument("--adjoint-steps", type=int, default=4000,
                    help="forward steps of the timed adjoint run (D2Q9 obstacle, J=10); 0 skips it")
     p.add_argument("--adjoint-every", type=int, default=100, help="checkpoint interval of the adjoint run")
     p.add_argument("--legs-only", action="store_true", help="run only the configuration legs")

@@ -107,6 +107,14 @@ def test_adjoint_d2q9_obstacle_moving_walls():
     _fd_check(cfg, u, 30, 10, "ke_sum", rates=(0, 1))
 
 
+def test_adjoint_d2q9_obstacle_J9_200_steps_checkpoint_100():
+    """The obstacle configuration at J = 9 (1024 x 512 finest cells), 200
+    steps with a checkpoint every 100 (two replayed segments): initial field
+    and both relaxation rates against central differences."""
+    cfg, u = W.ns_obstacle_2d(seed=5, max_level=9)
+    _fd_check(cfg, u, 200, 100, "ke_sum", rates=(0, 1))
+
+
 def test_adjoint_d2q9_closed_box_bounce_back():
     cfg, u = W.vortices_2d(seed=4, max_level=6, bc="bounce_back")
     _fd_check(cfg, u, 20, 6, "ke_sum", rates=(1,))
