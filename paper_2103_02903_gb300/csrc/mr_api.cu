@@ -387,6 +387,7 @@ void fill_desc(const mr_lbm* h, InstDev& d) {
   d.bcounts = h->bcounts;
   d.W = h->W;
   d.Wf = h->Wf;
+  d.det = h->det;
   d.Ws = h->Ws;
   d.Wsf = h->Wsf;
   auto& k = d.g.f32;  // FP32 copies for the FP32 arithmetic of the forms
@@ -513,6 +514,10 @@ void run_adapt(Exec& x, const Group& G, int cur) {
 
 void run_stream(Exec& x, const Group& G, int dst, int do_stream, int do_collide) {
   prof_begin(x, PG_STREAM);
+  if (do_stream && G.scheme == MR_D2Q9_NS && G.s == 1) {
+    mr_launch_edge_details(G, dst, x.st);  // the critical-case details, once per refined cell
+    x.launches += 1;
+  }
   mr_launch_stream_collide(G, dst, do_stream, do_collide, x.st, 1);  // counts the step
   prof_end(x, PG_STREAM);
   x.launches += 1;
@@ -836,6 +841,11 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   build_tables(g, W);
   ok = ok && dalloc(h, &h->W, W.size()) && dalloc(h, &h->Wf, W.size());
   std::vector<float> Wf(W.begin(), W.end());
+  if (g.diag && g.s_pred == 1) {
+    char* dp = nullptr;
+    ok = ok && dalloc(h, &dp, (size_t)4 * g.Q * g.cap[1] * (g.form == MR_FORM_F64 ? 8 : 4));
+    h->det = dp;
+  }
   std::vector<double> Ws;
   if (g.s_pred > 1) {
     build_tables_w(g, Ws);
@@ -1351,6 +1361,10 @@ mr_status mr_lbm_adjoint(mr_lbm_t h, const double* conserved0, int on_device, in
     for (int n = n0; n < n1; ++n) {
       const int j = n - n0;
       run_adapt(*h, h->grp, h->cur);
+      if (g.scheme == MR_D2Q9_NS) {  // the transport's critical-case details
+        mr_launch_edge_details(h->grp, 1 - h->cur, h->st);
+        h->launches += 1;
+      }
       mr_launch_stream_collide(h->grp, 1 - h->cur, 1, 0, h->st);  // stored state <- transport only
       if (!cuda_ok(h, cudaMemcpyAsync(z[j], h->fstate, QL * sizeof(double), cudaMemcpyDeviceToDevice, h->st)) ||
           !cuda_ok(h, cudaMemcpyAsync(h->fscratch, h->fstate, QL * sizeof(double), cudaMemcpyDeviceToDevice, h->st)))

@@ -52,6 +52,7 @@ struct mr_lbm : Exec {
   double* W = nullptr;
   float* Wf = nullptr;
   double* Ws = nullptr;  // s = 2, 3: flattened weights of half-width 2s
+  void* det = nullptr;   // D2Q9, s = 1: critical-case details (see InstDev::det)
   float* Wsf = nullptr;
   double* dense[2] = {nullptr, nullptr};
   size_t dense_elems = 0;

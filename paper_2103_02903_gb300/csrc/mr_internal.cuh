@@ -305,6 +305,8 @@ struct __align__(16) InstDev {
   int* bcounts;       // per dense chunk: leaf / internal / ghost counts, then offsets
   const double* W;    // flattened weights, MR_WIDX layout
   const float* Wf;    // the same in FP32
+  void* det;          // D2Q9, s = 1: children's details of the refined cells leaves border,
+                      // [(child * Q + p) * cap_int + internal index] in the form's arithmetic type
   const double* Ws;   // s = 2, 3: flattened weights of half-width 2s, MR_WWIDX layout (else null)
   const float* Wsf;   // the same in FP32
 };
@@ -388,6 +390,9 @@ void mr_launch_mark_ghosts(const Group& G, cudaStream_t st);
 void mr_launch_compact(const Group& G, int dst, cudaStream_t st);  // count + scan + scatter into mesh dst
 void mr_launch_remesh_copy(const Group& G, int cur, cudaStream_t st);
 void mr_launch_predict_level(const Group& G, int dst, int k, cudaStream_t st);  // level J_min + k
+// D2Q9, s = 1: the details of the children of every refined cell of mesh dst
+// that a leaf of its own level borders, for the transport's critical case.
+void mr_launch_edge_details(const Group& G, int dst, cudaStream_t st);
 // count = 1: also add the step to the instances' counters (once per step)
 void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st,
                               int count = 0);

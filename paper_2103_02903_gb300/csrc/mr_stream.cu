@@ -232,6 +232,42 @@ __device__ __forceinline__ void crit_axis_terms(const Geo& g, const typename For
   }
 }
 
+// The same terms from the children's details computed once per refined cell
+// (k_edge_details; D2Q9): det[(child * Q + p) * cap_int + ridx].
+template <class Sc, int F>
+__device__ __forceinline__ void crit_axis_terms_det(const Geo& g, const typename FormT<F>::C* __restrict__ W,
+                                                    const typename FormT<F>::C* __restrict__ det, int l, int a, int k,
+                                                    int side, int per, uint32_t ridx, typename FormT<F>::C scale,
+                                                    typename FormT<F>::C* tmp) {
+  using C = typename FormT<F>::C;
+  constexpr int D = Sc::D;
+  const int N1 = g.n[l + 1][a];
+  const size_t cap1 = g.cap[1];
+#pragma unroll 1
+  for (int p = 0; p < Sc::Q; ++p) {
+    const int sgn = eta_of<Sc>(p, a);
+    if (sgn == 0) continue;
+    const bool incoming = (sgn > 0) == (side < 0);
+    int c;  // child-level cell whose edge value is corrected
+    if (sgn > 0)
+      c = side < 0 ? 2 * k - 1 : 2 * k + 1;
+    else
+      c = side > 0 ? 2 * k + 2 : 2 * k;
+    const int cslot = mr_slot(per ? 2 : c, N1, per);
+    const C* wt = W + MR_WIDX(l + 1, a, cslot, sgn > 0 ? 2 : 3);
+    C corr = (C)0;
+#pragma unroll
+    for (int ci = 0; ci < (1 << D); ++ci) {
+      const int sa = (ci >> a) & 1;
+      const int delta = 2 * (k + side) + sa - c;
+      if (delta < -2 || delta > 2) continue;
+      corr += wt[delta + 2] * det[((size_t)ci * Sc::Q + p) * cap1 + ridx];
+    }
+    corr *= (C)1 / (C)(1 << (D - 1));  // average over the 2^{d-1} children on the shared face
+    tmp[p] = scale * (incoming ? corr : -corr);
+  }
+}
+
 __device__ __forceinline__ bool win_stencil(const Geo& g, int l, int x, int y, int ox, int oy,
                                             const int32_t (*win)[MR_WIN_TPB], int32_t* st);
 
@@ -249,7 +285,8 @@ __device__ __forceinline__ void stream_axis(const Geo& g, const MeshDev& B,
                                             const int32_t* ent, const typename FormT<F>::C* fs,
                                             const typename FormT<F>::C* offv, typename FormT<F>::C* out,
                                             typename FormT<F>::C scale, typename FormT<F>::C* tmp,
-                                            const int32_t (*win)[MR_WIN_TPB]) {
+                                            const int32_t (*win)[MR_WIN_TPB],
+                                            const typename FormT<F>::C* __restrict__ det = nullptr) {
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
   constexpr int D = Sc::D, Q = Sc::Q, NS = Pow3<D>::value;
@@ -281,6 +318,14 @@ __device__ __forceinline__ void stream_axis(const Geo& g, const MeshDev& B,
   for (int si = 0; si < 2; ++si) {
     if (!((refined >> si) & 1u)) continue;
     const int side = si == 0 ? -1 : 1;
+    if constexpr (Sc::DIAG) {  // the details were computed once per refined cell
+      crit_axis_terms_det<Sc, F>(g, W, det, l, a, k, side, per, (uint32_t)ent[si == 0 ? 1 : 2] & 0x3FFFFFFFu, scale,
+                                 tmp);
+#pragma unroll
+      for (int p = 0; p < Q; ++p)
+        if (eta_of<Sc>(p, a) != 0) out[p] += tmp[p];
+      continue;
+    }
     const int ox = a == 0 ? side : 0, oy = a == 1 ? side : 0;
     int nb[3] = {x, y, z};
     nb[a] += side;
@@ -377,7 +422,8 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
                                                  int i, const typename FormT<F>::C* fs,
                                                  const typename FormT<F>::C* offv, typename FormT<F>::C* out,
                                                  typename FormT<F>::C scale, typename FormT<F>::C* tmp,
-                                                 int32_t (*win)[MR_WIN_TPB]) {
+                                                 int32_t (*win)[MR_WIN_TPB],
+                                                 const typename FormT<F>::C* __restrict__ det) {
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
   const C cs = MR_K(C, g, cross_sign);
@@ -417,7 +463,7 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
       has[w] = win_valid(ent[w]);
       vp[w] = mr_resolve<S>(g, B, LFin, has[w] ? ent[w] : 0);
     }
-    stream_axis<Sc, F>(g, B, LFin, W, l, a, x, y, 0, vp, has, ent, fs, offv, out, scale, tmp, win);
+    stream_axis<Sc, F>(g, B, LFin, W, l, a, x, y, 0, vp, has, ent, fs, offv, out, scale, tmp, win, det);
   }
 
   // ---- the four single finest cells of each diagonal velocity
@@ -454,20 +500,8 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
       const int dx = nb % 3 - 1, dy = nb / 3 - 1;
       const int32_t e = win[(dy + 2) * 5 + dx + 2][tid];
       if (!win_valid(e) || (((uint32_t)e) >> 30) != MR_CLS_INT) continue;
-      int32_t st[9], ce[4];
-      bool ok = win_stencil(g, l, x, y, dx, dy, win, st);
-      int nx = x + dx, ny = y + dy;
-      mr_nbr_mesh(g, l, nx, ny);
-      const uint32_t ncode = mr_encode(g, l, nx, ny);
-#pragma unroll
-      for (int ci = 0; ci < 4; ++ci) {
-        ce[ci] = B.map[g.base[l + 1] + ((ncode << 2) | (uint32_t)ci)];
-        ok = ok && ce[ci] != MR_MAP_NONE;
-      }
-      if (!ok) {
-        mr_set_err(B.cnt, MR_DERR_INTERNAL);
-        continue;
-      }
+      const uint32_t ridx = (uint32_t)e & 0x3FFFFFFFu;  // its children's details: det (k_edge_details)
+      const size_t cap1 = g.cap[1];
       C wcx[2][2], wcy[2][2];  // [sign index][child offset]
 #pragma unroll
       for (int si = 0; si < 2; ++si)
@@ -480,17 +514,12 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
       for (int t = 0; t < 4; ++t) {
         const int p = P0 + t;
         const int ix = Sc::eta(p, 0) > 0 ? 0 : 1, iy = Sc::eta(p, 1) > 0 ? 0 : 1;
-        C v[9];
-#pragma unroll
-        for (int kk = 0; kk < 9; ++kk) v[kk] = ld_c<C>(mr_resolve<S>(g, B, LFin, st[kk]), p);
         C corr = (C)0;
 #pragma unroll
         for (int ci = 0; ci < 4; ++ci) {
           const C w = wcx[ix][ci & 1] * wcy[iy][ci >> 1];
           if (w == (C)0) continue;
-          // details are exact on constants: stored values suffice
-          const C det = ld_c<C>(mr_resolve<S>(g, B, LFin, ce[ci]), p) - predict_c<2, C>(v, ci, cs);
-          corr += w * det;
+          corr += w * det[((size_t)ci * Sc::Q + p) * cap1 + ridx];
         }
         acc[t] += corr;
       }
@@ -505,6 +534,78 @@ __device__ __forceinline__ void stream_window_d2(const Geo& g, const MeshDev& B,
     const bool outy = !g.periodic[1] && (sy > 0 ? y == 0 : y == Ny - 1);
     if (outx && outy) acc[t] -= bc_value<C>(g, g.bc[sy > 0 ? 2 : 3], fs, p, Sc::opp(p));
     out[p] += scale2 * acc[t];
+  }
+}
+
+// ------------------------------------------------------------------ critical-case details (D2Q9)
+// The details of the children of every refined cell that a leaf of its own
+// level borders (within its 3 x 3 neighbourhood), for every population:
+// det[(child * Q + p) * cap_int + i] = child value - its prediction from the
+// refined cell's 3 x 3 stencil, in the form's arithmetic, the operations the
+// transport would perform.  The transport of a D2Q9 leaf then reads them for
+// its refined neighbours (axis strips and diagonal corner cells) instead of
+// predicting the children again: each refined cell is done once, not by
+// each of up to eight leaves around it, for up to eight populations each.
+template <int F>
+__global__ void __launch_bounds__(128) k_edge_details(const InstDev* __restrict__ IB, int ngrp, int dst) {
+  using S = typename FormT<F>::S;
+  using C = typename FormT<F>::C;
+  constexpr int Q = Scheme<4>::Q;
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, ngrp);
+  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
+  const int tiles =
+      mr_group_prefix(pre, ngrp, [&](int b) { return (IB[b].mesh[dst].cnt->total[MR_CLS_INT] + 127) / 128; });
+  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+    const int b = mr_group_find(pre, ngrp, tt);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    const MeshDev& B = si.mesh[dst];
+    const int i = (tt - pre[b]) * 128 + threadIdx.x;
+    if (i >= B.cnt->total[MR_CLS_INT]) continue;
+    const int l = B.lvl[MR_CLS_INT][i];
+    const uint32_t code = B.code[MR_CLS_INT][i];
+    int x, y;
+    mr_decode(g, l, code, x, y);
+    // does a leaf of level l border it?
+    MortonBox<1> bx;
+    bx.init(g, l, x, y);
+    const int32_t* map = B.map + g.base[l];
+    bool need = false;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      if (k == 4 || !bx.in(k % 3, k / 3)) continue;
+      const int32_t e = map[bx.code(k % 3, k / 3)];
+      need = need || (e != MR_MAP_NONE && (((uint32_t)e) >> 30) == MR_CLS_LEAF);
+    }
+    if (!need) continue;
+    int32_t st[9], ce[4];
+    bool ok = mr_stencil_entries<2>(g, B, l, x, y, st);
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci) {
+      ce[ci] = B.map[g.base[l + 1] + ((code << 2) | (uint32_t)ci)];
+      ok = ok && ce[ci] != MR_MAP_NONE;
+    }
+    if (!ok) {
+      mr_set_err(B.cnt, MR_DERR_INTERNAL);
+      continue;
+    }
+    const S* LFin = (const S*)si.fscratch;
+    C* det = (C*)si.det;
+    const C cs = MR_K(C, g, cross_sign);
+    const size_t cap1 = g.cap[1];
+#pragma unroll 1
+    for (int p = 0; p < Q; ++p) {
+      C v[9];
+#pragma unroll
+      for (int kk = 0; kk < 9; ++kk) v[kk] = ld_c<C>(mr_resolve<S>(g, B, LFin, st[kk]), p);
+#pragma unroll
+      for (int ci = 0; ci < 4; ++ci)
+        det[((size_t)ci * Q + p) * cap1 + i] =
+            ld_c<C>(mr_resolve<S>(g, B, LFin, ce[ci]), p) - predict_c<2, C>(v, ci, cs);
+    }
   }
 }
 
@@ -565,7 +666,7 @@ __global__ void __launch_bounds__(MR_WIN_TPB) k_stream_collide(const InstDev* __
       const C scale = (C)__longlong_as_double((long long)(1023 + l - g.J) << 52);  // 2^{l-J}, exact
       if constexpr (Sc::DIAG) {
         __shared__ int32_t win[25][MR_WIN_TPB];
-        stream_window_d2<Sc, F>(g, B, LFin, W, l, x, y, i, fs, offv, out, scale, tmp, win);
+        stream_window_d2<Sc, F>(g, B, LFin, W, l, x, y, i, fs, offv, out, scale, tmp, win, (const C*)si.det);
       } else {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -729,6 +830,11 @@ void launch_predict_t(const Group& G, int dst, int kl, cudaStream_t st) {
   mr_launch_pdl(k_predict_level<D, Q, F>, mr_tile_grid(G, 2 * G.pred_cells[kl], 32, G.bps[MR_PH_PREDICT]), dim3(32, PopRows<Q>::value),
                 mr_pre_bytes(G), st, G.dev, G.n, dst, kl);
 }
+template <int F>
+void launch_edge_t(const Group& G, int dst, cudaStream_t st) {
+  mr_launch_pdl(k_edge_details<F>, mr_tile_grid(G, G.capI, 128, G.bps[MR_PH_STREAM]), 128, mr_pre_bytes(G), st, G.dev,
+                G.n, dst);
+}
 template <int SC, int F>
 void launch_stream_t(const Group& G, int dst, int ds, int dc, int count, cudaStream_t st) {
   mr_launch_pdl(k_stream_collide<SC, F>, mr_tile_grid(G, G.capL, MR_WIN_TPB, G.bps[MR_PH_STREAM]), MR_WIN_TPB, mr_pre_bytes(G), st, G.dev,
@@ -804,6 +910,8 @@ void mr_launch_stream_collide(const Group& G, int dst, int do_stream, int do_col
     case 5: MR_FORMS2(launch_stream_t, 5, G, dst, do_stream, do_collide, count, st); break;
   }
 }
+
+void mr_launch_edge_details(const Group& G, int dst, cudaStream_t st) { MR_FORMS(launch_edge_t, G, dst, st); }
 
 void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, void* LF, cudaStream_t st, int grid) {
   const Geo& G = g;
