@@ -514,8 +514,11 @@ void run_adapt(Exec& x, const Group& G, int cur) {
 
 void run_stream(Exec& x, const Group& G, int dst, int do_stream, int do_collide) {
   prof_begin(x, PG_STREAM);
-  if (do_stream && G.scheme == MR_D2Q9_NS && G.s == 1) {
-    mr_launch_edge_details(G, dst, x.st);  // the critical-case details, once per refined cell
+  if (do_stream && G.s > 1) {
+    mr_launch_edge_details_w(G, dst, x.st);  // the critical-case details, once per refined cell
+    x.launches += 1;
+  } else if (do_stream && G.scheme == MR_D2Q9_NS) {
+    mr_launch_edge_details(G, dst, x.st);
     x.launches += 1;
   }
   mr_launch_stream_collide(G, dst, do_stream, do_collide, x.st, 1);  // counts the step
@@ -841,9 +844,9 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   build_tables(g, W);
   ok = ok && dalloc(h, &h->W, W.size()) && dalloc(h, &h->Wf, W.size());
   std::vector<float> Wf(W.begin(), W.end());
-  if (g.diag && g.s_pred == 1) {
+  if ((g.diag && g.s_pred == 1) || g.s_pred > 1) {  // critical-case details of the transport
     char* dp = nullptr;
-    ok = ok && dalloc(h, &dp, (size_t)4 * g.Q * g.cap[1] * (g.form == MR_FORM_F64 ? 8 : 4));
+    ok = ok && dalloc(h, &dp, ((size_t)1 << g.d) * g.Q * g.cap[1] * (g.form == MR_FORM_F64 ? 8 : 4));
     h->det = dp;
   }
   std::vector<double> Ws;

@@ -305,7 +305,8 @@ struct __align__(16) InstDev {
   int* bcounts;       // per dense chunk: leaf / internal / ghost counts, then offsets
   const double* W;    // flattened weights, MR_WIDX layout
   const float* Wf;    // the same in FP32
-  void* det;          // D2Q9, s = 1: children's details of the refined cells leaves border,
+  void* det;          // D2Q9 with s = 1, and every scheme with s = 2, 3: the children's details of
+                      // the refined cells that leaves reach with their transport windows,
                       // [(child * Q + p) * cap_int + internal index] in the form's arithmetic type
   const double* Ws;   // s = 2, 3: flattened weights of half-width 2s, MR_WWIDX layout (else null)
   const float* Wsf;   // the same in FP32
@@ -425,6 +426,7 @@ void mr_launch_details_w(const Group& G, int cur, cudaStream_t st);
 void mr_launch_grade_w(const Group& G, cudaStream_t st);
 void mr_launch_mark_ghosts_w(const Group& G, cudaStream_t st);
 void mr_launch_predict_level_w(const Group& G, int dst, int k, cudaStream_t st);
+void mr_launch_edge_details_w(const Group& G, int dst, cudaStream_t st);  // before the wide transport
 void mr_launch_stream_collide_w(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st, int count);
 void mr_launch_project_dense_w(const Geo& g, const MeshDev& B, const void* LF, int level, const double* prev,
                                double* cur, cudaStream_t st, int grid);

@@ -334,6 +334,81 @@ __global__ void __launch_bounds__(256) k_project_dense_w(Geo g, MeshDev Bm, cons
   }
 }
 
+// ------------------------------------------------------------------ critical-case details
+// The details of the children of every refined cell that a leaf of its own
+// level can reach with its window (W = 2s cells along an axis, or the
+// (2W+1)^2 block of a lattice with diagonal velocities), for every
+// population: det[(child * Q + p) * cap_int + i] = child value minus its
+// prediction from the refined cell's (2s+1)^d stencil, in the form's
+// arithmetic, the operations the transport would perform.  The transport
+// then reads them for every refined cell of its window instead of
+// predicting the children again for each leaf and population.
+template <int D, int S, int F>
+__global__ void __launch_bounds__(128) k_edge_details_w(const InstDev* __restrict__ IB, int ngrp, int dst) {
+  using St = typename FormT<F>::S;
+  using C = typename FormT<F>::C;
+  using B = WBox<D, S>;
+  constexpr int W = 2 * S, NW = 2 * W + 1;
+  extern __shared__ int pre[];
+  __shared__ InstDev si;
+  int have = -1;
+  mr_inst_prefetch(si, have, IB, ngrp);
+  mr_grid_dep();
+  const int tiles =
+      mr_group_prefix(pre, ngrp, [&](int b) { return (IB[b].mesh[dst].cnt->total[MR_CLS_INT] + 127) / 128; });
+  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+    const int b = mr_group_find(pre, ngrp, tt);
+    mr_inst_use(si, have, IB, b);
+    const Geo& g = si.g;
+    const MeshDev& Bm = si.mesh[dst];
+    const int i = (tt - pre[b]) * 128 + threadIdx.x;
+    if (i >= Bm.cnt->total[MR_CLS_INT]) continue;
+    const int l = Bm.lvl[MR_CLS_INT][i];
+    const uint32_t code = Bm.code[MR_CLS_INT][i];
+    int c[3] = {0, 0, 0};
+    mr_decode_d<D>(g, l, code, c);
+    // does a leaf of level l reach it?
+    const bool block = D == 2 && g.diag;
+    const int nw = block ? NW * NW : D * 2 * W;
+    bool need = false;
+    for (int w = 0; w < nw && !need; ++w) {
+      int nb[3] = {c[0], c[1], c[2]};
+      if (block) {
+        if (w == NW * W + W) continue;
+        nb[0] += w % NW - W;
+        nb[1] += w / NW - W;
+      } else {
+        const int axis = w / (2 * W), o = w % (2 * W);
+        nb[axis] += o < W ? o - W : o - W + 1;
+      }
+      if (!mr_nbr_mesh_d<D>(g, l, nb)) continue;
+      const int32_t e = Bm.map[g.base[l] + mr_encode_d<D>(g, l, nb)];
+      need = e != MR_MAP_NONE && (((uint32_t)e) >> 30) == MR_CLS_LEAF;
+    }
+    if (!need) continue;
+    int32_t st[B::N], ce[1 << D];
+    bool ok = wide_stencil<D, S>(g, Bm, l, c, st);
+    for (int ci = 0; ci < (1 << D); ++ci) {
+      ce[ci] = Bm.map[g.base[l + 1] + ((code << D) | (uint32_t)ci)];
+      ok = ok && ce[ci] != MR_MAP_NONE;
+    }
+    if (!ok) {
+      mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
+      continue;
+    }
+    const St* LFin = (const St*)si.fscratch;
+    C* det = (C*)si.det;
+    const size_t cap1 = g.cap[1];
+    for (int p = 0; p < g.Q; ++p) {
+      C v[B::N];
+      for (int kk = 0; kk < B::N; ++kk) v[kk] = ld_c<C>(mr_resolve<St>(g, Bm, LFin, st[kk]), p);
+      for (int ci = 0; ci < (1 << D); ++ci)
+        det[((size_t)ci * g.Q + p) * cap1 + i] =
+            ld_c<C>(mr_resolve<St>(g, Bm, LFin, ce[ci]), p) - wide_predict<D, S, C, false>(v, ci, g.cross_sign);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ transport + collision
 #define MR_WOUT ((int32_t)0xC0000000)  // window cell outside a non-periodic domain
 
@@ -459,24 +534,14 @@ __global__ void __launch_bounds__(128) k_stream_collide_w(const InstDev* __restr
           if (sgn < 0 && hi) acc += bc_value<C>(g, g.bc[2 * a + 1], fs, p, Sc::opp(p));
           out[p] += scale * acc;
         }
-        // the critical case: refined cells of the window
+        // the critical case: refined cells of the window, their children's
+        // details from the pre-pass (k_edge_details_w)
+        const C* __restrict__ det = (const C*)si.det;
+        const size_t cap1 = g.cap[1];
         for (int o = 0; o < NW; ++o) {
           if (ent[o] == MR_WOUT || (((uint32_t)ent[o]) >> 30) != MR_CLS_INT) continue;
           const int dlt = o - W;
-          int nb[3] = {xc[0], xc[1], xc[2]};
-          nb[a] += dlt;
-          mr_nbr_mesh_d<D>(g, l, nb);  // inside: only such cells have an entry
-          int32_t st[B::N], ce[1 << D];
-          bool ok = wide_stencil<D, S>(g, Bm, l, nb, st);
-          const uint32_t ncode = mr_encode_d<D>(g, l, nb);
-          for (int ci = 0; ci < (1 << D); ++ci) {
-            ce[ci] = Bm.map[g.base[l + 1] + ((ncode << D) | (uint32_t)ci)];
-            ok = ok && ce[ci] != MR_MAP_NONE;
-          }
-          if (!ok) {
-            mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
-            continue;
-          }
+          const uint32_t ridx = (uint32_t)ent[o] & 0x3FFFFFFFu;
           const int N1 = g.n[l + 1][a];
           for (int p = 0; p < Q; ++p) {
             const int sgn = eta_of<Sc>(p, a);
@@ -486,9 +551,6 @@ __global__ void __launch_bounds__(128) k_stream_collide_w(const InstDev* __restr
             const bool eIn = per || (sgn > 0 ? k > 0 : k < N - 1);
             const C* wE = eIn ? Wt + MR_WWIDX(l + 1, a, mr_slot_w(2 * k + rE, N1, per, W), tab, W) : nullptr;
             const C* wA = Wt + MR_WWIDX(l + 1, a, mr_slot_w(2 * k + rA, N1, per, W), tab, W);
-            // details are exact on constants: stored values suffice
-            C v[B::N];
-            for (int kk = 0; kk < B::N; ++kk) v[kk] = ld_c<C>(mr_resolve<St>(g, Bm, LFin, st[kk]), p);
             C corr = (C)0;
             for (int ci = 0; ci < (1 << D); ++ci) {
               const int cx = 2 * dlt + ((ci >> a) & 1);
@@ -497,9 +559,7 @@ __global__ void __launch_bounds__(128) k_stream_collide_w(const InstDev* __restr
               if (wE && oE >= -W && oE <= W) wgt += wE[oE + W];
               if (oA >= -W && oA <= W) wgt -= wA[oA + W];
               if (wgt == (C)0) continue;
-              const C det =
-                  ld_c<C>(mr_resolve<St>(g, Bm, LFin, ce[ci]), p) - wide_predict<D, S, C, false>(v, ci, g.cross_sign);
-              corr += wgt * det;
+              corr += wgt * det[((size_t)ci * Q + p) * cap1 + ridx];
             }
             out[p] += scale * (corr * ((C)1 / (C)(1 << (D - 1))));
           }
@@ -546,40 +606,28 @@ __global__ void __launch_bounds__(128) k_stream_collide_w(const InstDev* __restr
               if (aa == W && bb == W) continue;
               C wcx[2][2], wcy[2][2];  // [sign index][child offset]
               bool any = false;
-              for (int si = 0; si < 2; ++si)
+              for (int sg = 0; sg < 2; ++sg)
                 for (int o = 0; o < 2; ++o) {
-                  wcx[si][o] = wide_corner_weight<C>(g, Wt, l + 1, 0, x, 2 * (aa - W) + o, si == 0 ? 1 : -1, W);
-                  wcy[si][o] = wide_corner_weight<C>(g, Wt, l + 1, 1, y, 2 * (bb - W) + o, si == 0 ? 1 : -1, W);
-                  any = any || wcx[si][o] != (C)0;
+                  wcx[sg][o] = wide_corner_weight<C>(g, Wt, l + 1, 0, x, 2 * (aa - W) + o, sg == 0 ? 1 : -1, W);
+                  wcy[sg][o] = wide_corner_weight<C>(g, Wt, l + 1, 1, y, 2 * (bb - W) + o, sg == 0 ? 1 : -1, W);
+                  any = any || wcx[sg][o] != (C)0;
                 }
               if (!any) continue;
               int nb[3] = {x + aa - W, y + bb - W, 0};
               if (!mr_nbr_mesh_d<2>(g, l, nb)) continue;
               const int32_t e = Bm.map[g.base[l] + mr_encode_d<2>(g, l, nb)];
               if (e == MR_MAP_NONE || (((uint32_t)e) >> 30) != MR_CLS_INT) continue;
-              int32_t st[B2::N], ce[4];
-              bool ok = wide_stencil<2, S>(g, Bm, l, nb, st);
-              const uint32_t ncode = mr_encode_d<2>(g, l, nb);
-              for (int ci = 0; ci < 4; ++ci) {
-                ce[ci] = Bm.map[g.base[l + 1] + ((ncode << 2) | (uint32_t)ci)];
-                ok = ok && ce[ci] != MR_MAP_NONE;
-              }
-              if (!ok) {
-                mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
-                continue;
-              }
+              const uint32_t ridx = (uint32_t)e & 0x3FFFFFFFu;  // its children's details: det (pre-pass)
+              const C* __restrict__ det = (const C*)si.det;
+              const size_t cap1 = g.cap[1];
               for (int t = 0; t < 4; ++t) {
                 const int p = P0 + t;
                 const int ix = Sc::eta(p, 0) > 0 ? 0 : 1, iy = Sc::eta(p, 1) > 0 ? 0 : 1;
-                // details are exact on constants: stored values suffice
-                C v[B2::N];
-                for (int kk = 0; kk < B2::N; ++kk) v[kk] = ld_c<C>(mr_resolve<St>(g, Bm, LFin, st[kk]), p);
                 C corr = (C)0;
                 for (int ci = 0; ci < 4; ++ci) {
                   const C w = wcx[ix][ci & 1] * wcy[iy][ci >> 1];
                   if (w == (C)0) continue;
-                  corr += w * (ld_c<C>(mr_resolve<St>(g, Bm, LFin, ce[ci]), p) -
-                               wide_predict<2, S, C, false>(v, ci, g.cross_sign));
+                  corr += w * det[((size_t)ci * Q + p) * cap1 + ridx];
                 }
                 acc[t] += corr;
               }
@@ -628,6 +676,11 @@ void launch_predict_w(const Group& G, int dst, int kl, cudaStream_t st) {
   mr_launch_pdl(k_predict_level_w<D, S, F>, mr_tile_grid(G, 2 * G.pred_cells[kl], 128, G.bps[MR_PH_PREDICT]), 128, mr_pre_bytes(G), st,
                 G.dev, G.n, dst, kl);
 }
+template <int D, int S, int F>
+void launch_edge_w(const Group& G, int dst, cudaStream_t st) {
+  mr_launch_pdl(k_edge_details_w<D, S, F>, mr_tile_grid(G, G.capI, 128, G.bps[MR_PH_STREAM]), 128, mr_pre_bytes(G), st,
+                G.dev, G.n, dst);
+}
 template <int SC, int S, int F>
 void launch_stream_w(const Group& G, int dst, int ds, int dc, int count, cudaStream_t st) {
   mr_launch_pdl(k_stream_collide_w<SC, S, F>, mr_tile_grid(G, G.capL, 128, G.bps[MR_PH_STREAM]), 128, mr_pre_bytes(G), st, G.dev, G.n,
@@ -669,6 +722,12 @@ void mr_launch_predict_level_w(const Group& G, int dst, int kl, cudaStream_t st)
   if (G.d == 1) MR_W_S(launch_predict_w, G.form, G.s, 1, G, dst, kl, st);
   else if (G.d == 2) MR_W_S(launch_predict_w, G.form, G.s, 2, G, dst, kl, st);
   else MR_W_S(launch_predict_w, G.form, G.s, 3, G, dst, kl, st);
+}
+
+void mr_launch_edge_details_w(const Group& G, int dst, cudaStream_t st) {
+  if (G.d == 1) MR_W_S(launch_edge_w, G.form, G.s, 1, G, dst, st);
+  else if (G.d == 2) MR_W_S(launch_edge_w, G.form, G.s, 2, G, dst, st);
+  else MR_W_S(launch_edge_w, G.form, G.s, 3, G, dst, st);
 }
 
 void mr_launch_stream_collide_w(const Group& G, int dst, int do_stream, int do_collide, cudaStream_t st, int count) {
