@@ -47,53 +47,89 @@ __device__ __forceinline__ bool wide_stencil(const Geo& g, const MeshDev& M, int
   return ok;
 }
 
+// Entry k (x fastest) of the (2s+1)^D stencil around cell c of level l.
+template <int D, int S>
+__device__ __forceinline__ int32_t wide_stencil_entry(const Geo& g, const MeshDev& M, int l, const int* c, int k) {
+  using B = WBox<D, S>;
+  int s[3] = {c[0] + k % B::W1 - S, D >= 2 ? c[1] + (k / B::W1) % B::W1 - S : 0,
+              D == 3 ? c[2] + k / (B::W1 * B::W1) - S : 0};
+  mr_nbr_stencil_d<D>(g, l, s);
+  return M.map[g.base[l] + mr_encode_d<D>(g, l, s)];
+}
+
+// Thread layout of the wide details and prediction kernels: a tile of TC
+// cells (threadIdx.x) by 8 population rows (threadIdx.y); the rows share one
+// lookup of each cell's stencil (and children) through shared memory.
+template <int D, int S>
+struct WTile {
+  static constexpr int TC = (D == 3 && S == 3) ? 16 : 32;  // 343-cell stencils: half the cells per tile
+};
+
 // ------------------------------------------------------------------ details
 // Group norm of the details of every internal cell's children (Def. Details,
 // max over the 2^d children and all populations), FP64 on stored values.
 template <int D, int S, int F>
-__global__ void __launch_bounds__(128) k_details_w(const InstDev* __restrict__ IB, int n, int cur) {
+__global__ void __launch_bounds__(256) k_details_w(const InstDev* __restrict__ IB, int n, int cur) {
   using St = typename FormT<F>::S;
   using B = WBox<D, S>;
+  constexpr int TC = WTile<D, S>::TC, NE = B::N + (1 << D);
   extern __shared__ int pre[];
   __shared__ InstDev si;
+  __shared__ int32_t sent[NE][TC];
+  __shared__ double red[8][TC];
   int have = -1;
   mr_inst_prefetch(si, have, IB, n);
   mr_grid_dep();
-  const int tiles = mr_group_prefix(pre, n, [&](int b) { return (IB[b].mesh[cur].cnt->total[MR_CLS_INT] + 127) / 128; });
-  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+  const int tiles =
+      mr_group_prefix(pre, n, [&](int b) { return (IB[b].mesh[cur].cnt->total[MR_CLS_INT] + TC - 1) / TC; });
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {  // uniform over the block
     const int b = mr_group_find(pre, n, t);
     mr_inst_use(si, have, IB, b);
     const Geo& g = si.g;
     const MeshDev& A = si.mesh[cur];
-    const int i = (t - pre[b]) * 128 + threadIdx.x;
-    if (i >= A.cnt->total[MR_CLS_INT]) continue;
-    const int L = A.lvl[MR_CLS_INT][i];
-    const uint32_t code = A.code[MR_CLS_INT][i];
-    int c[3] = {0, 0, 0};
-    mr_decode_d<D>(g, L, code, c);
-    int32_t ent[B::N], che[1 << D];
-    bool ok = wide_stencil<D, S>(g, A, L, c, ent);
-    for (int ci = 0; ci < (1 << D); ++ci) {
-      che[ci] = A.map[g.base[L + 1] + ((code << D) | (uint32_t)ci)];
-      ok = ok && che[ci] != MR_MAP_NONE && (((uint32_t)che[ci]) >> 30) <= MR_CLS_INT;
+    const int nI = A.cnt->total[MR_CLS_INT];
+    const int i = (t - pre[b]) * TC + tx;
+    if (i < nI) {
+      const int L = A.lvl[MR_CLS_INT][i];
+      const uint32_t code = A.code[MR_CLS_INT][i];
+      int c[3] = {0, 0, 0};
+      mr_decode_d<D>(g, L, code, c);
+      for (int e = ty; e < NE; e += 8)
+        sent[e][tx] = e < B::N ? wide_stencil_entry<D, S>(g, A, L, c, e)
+                               : A.map[g.base[L + 1] + ((code << D) | (uint32_t)(e - B::N))];
     }
-    for (int k = 0; k < B::N && ok; ++k) ok = (((uint32_t)ent[k]) >> 30) <= MR_CLS_INT;
-    if (!ok) {
-      mr_set_err(A.cnt, MR_DERR_INTERNAL);
-      continue;
-    }
+    __syncthreads();
     double gmax = 0.0;
-    for (int p = 0; p < g.Q; ++p) {
-      double v[B::N];
-      for (int k = 0; k < B::N; ++k) v[k] = mr_ld(mr_resolve<St>(g, A, si.fstate, ent[k]), p);
+    bool ok = i < nI;
+    if (ok) {
+      for (int e = 0; e < NE; ++e) {
+        const int32_t en = sent[e][tx];
+        ok = ok && en != MR_MAP_NONE && (((uint32_t)en) >> 30) <= MR_CLS_INT;
+      }
+      if (!ok) {
+        if (ty == 0) mr_set_err(A.cnt, MR_DERR_INTERNAL);
+      } else {
+        for (int p = ty; p < g.Q; p += 8) {
+          double v[B::N];
+          for (int k = 0; k < B::N; ++k) v[k] = mr_ld(mr_resolve<St>(g, A, si.fstate, sent[k][tx]), p);
 #pragma unroll 1
-      for (int ci = 0; ci < (1 << D); ++ci) {
-        const double pr = wide_predict<D, S, double, true>(v, ci, g.cross_sign);
-        const double d = fabs(__dsub_rn(mr_ld(mr_resolve<St>(g, A, si.fstate, che[ci]), p), pr));
-        gmax = d > gmax ? d : gmax;
+          for (int ci = 0; ci < (1 << D); ++ci) {
+            const double pr = wide_predict<D, S, double, true>(v, ci, g.cross_sign);
+            const double d = fabs(__dsub_rn(mr_ld(mr_resolve<St>(g, A, si.fstate, sent[B::N + ci][tx]), p), pr));
+            gmax = d > gmax ? d : gmax;
+          }
+        }
       }
     }
-    A.G[i] = gmax;
+    red[ty][tx] = gmax;
+    __syncthreads();
+    if (ty == 0 && ok) {
+      double m = red[0][tx];
+      for (int r = 1; r < 8; ++r) m = red[r][tx] > m ? red[r][tx] : m;
+      A.G[i] = m;
+    }
+    __syncthreads();
   }
 }
 
@@ -168,6 +204,8 @@ __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict
   using B = WBox<D, S>;
   constexpr int W = 2 * S;
   __shared__ InstDev si;
+  __shared__ uint16_t queue[MR_DENSE_ALIGN];  // the chunk's leaves (offsets in the chunk)
+  __shared__ int qn;
   int chunk, have = -1;
   mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
   mr_grid_dep();
@@ -176,54 +214,70 @@ __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict
   const uint32_t c0 = (uint32_t)chunk * MR_DENSE_ALIGN;
   const int l = mr_level_of(g, c0);
   const uint32_t cb = c0 - g.base[l];
-  for (int k = 0; k < (int)(MR_DENSE_ALIGN / 256u); ++k) {
-    const uint32_t c = cb + (uint32_t)k * 256u + threadIdx.x;
-    if (c >= g.ncode[l] || (cls[c0 + (c - cb)] & 3u) != MR_C_LEAF) continue;
-    int x[3] = {0, 0, 0};
-    mr_decode_d<D>(g, l, c, x);
-    const bool block = D == 2 && g.diag;
-    const int nw = block ? (2 * W + 1) * (2 * W + 1) : D * 2 * W;
-    for (int w = 0; w < nw; ++w) {
-      int nb[3] = {x[0], x[1], x[2]};
-      if (block) {
-        if (w == (2 * W + 1) * W + W) continue;  // the leaf itself
-        nb[0] += w % (2 * W + 1) - W;
-        nb[1] += w / (2 * W + 1) - W;
-      } else {
-        const int axis = w / (2 * W), o = w % (2 * W), off = o < W ? o - W : o - W + 1;  // -W..-1, 1..W
-        nb[axis] += off;
+  if (threadIdx.x == 0) qn = 0;
+  __syncthreads();
+  // the leaves are a few per cent of the cells: gather them, then spread the
+  // (leaf, window cell) pairs over the whole block (the marks are a union of
+  // atomic ORs, so the order does not matter)
+  {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < (int)(MR_DENSE_ALIGN / 256u); ++k) {
+      const uint32_t off = (uint32_t)k * 256u + threadIdx.x;
+      const bool leaf = cb + off < g.ncode[l] && (cls[c0 + off] & 3u) == MR_C_LEAF;
+      const uint32_t bal = __ballot_sync(0xffffffffu, leaf);
+      int at = 0;
+      if (lane == 0 && bal) at = atomicAdd(&qn, __popc(bal));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (leaf) queue[at + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)off;
+    }
+  }
+  __syncthreads();
+  const bool block = D == 2 && g.diag;
+  const int nw = block ? (2 * W + 1) * (2 * W + 1) : D * 2 * W;
+  const int items = qn * nw;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int w = it % nw;
+    if (block && w == (2 * W + 1) * W + W) continue;  // the leaf itself
+    const uint32_t c = cb + queue[it / nw];
+    int nb[3] = {0, 0, 0};
+    mr_decode_d<D>(g, l, c, nb);
+    if (block) {
+      nb[0] += w % (2 * W + 1) - W;
+      nb[1] += w / (2 * W + 1) - W;
+    } else {
+      const int axis = w / (2 * W), o = w % (2 * W);
+      nb[axis] += o < W ? o - W : o - W + 1;  // -W..-1, 1..W
+    }
+    if (!mr_nbr_mesh_d<D>(g, l, nb)) continue;
+    const uint32_t gw = g.base[l] + mr_encode_d<D>(g, l, nb);
+    if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
+    const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
+    if ((old & (3u | MR_C_GHOST)) || l - 1 < g.Jmin) continue;
+    // cascade over the stencils of the ghosts' parents
+    int sl[MR_MAXL], sc[MR_MAXL][3], sk[MR_MAXL];
+    int sp = 1;
+    sl[0] = l - 1;
+    sk[0] = 0;
+    for (int a = 0; a < 3; ++a) sc[0][a] = a < D ? nb[a] >> 1 : 0;
+    while (sp > 0) {
+      const int f = sp - 1;
+      if (sk[f] == B::N) {
+        --sp;
+        continue;
       }
-      if (!mr_nbr_mesh_d<D>(g, l, nb)) continue;
-      const uint32_t gw = g.base[l] + mr_encode_d<D>(g, l, nb);
-      if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
-      const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
-      if ((old & (3u | MR_C_GHOST)) || l - 1 < g.Jmin) continue;
-      // cascade over the stencils of the ghosts' parents
-      int sl[MR_MAXL], sc[MR_MAXL][3], sk[MR_MAXL];
-      int sp = 1;
-      sl[0] = l - 1;
-      sk[0] = 0;
-      for (int a = 0; a < 3; ++a) sc[0][a] = a < D ? nb[a] >> 1 : 0;
-      while (sp > 0) {
-        const int f = sp - 1;
-        if (sk[f] == B::N) {
-          --sp;
-          continue;
-        }
-        const int kk = sk[f]++;
-        const int L = sl[f];
-        int ac[3] = {sc[f][0] + kk % B::W1 - S, D >= 2 ? sc[f][1] + (kk / B::W1) % B::W1 - S : 0,
-                     D == 3 ? sc[f][2] + kk / (B::W1 * B::W1) - S : 0};
-        if (!mr_nbr_mesh_d<D>(g, L, ac)) continue;  // outside: the stencil clamps to a cell of the box
-        const uint32_t ga = g.base[L] + mr_encode_d<D>(g, L, ac);
-        if (cls[ga] & (3u | MR_C_GHOST)) continue;
-        const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
-        if ((o2 & (3u | MR_C_GHOST)) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
-        sl[sp] = L - 1;
-        sk[sp] = 0;
-        for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? ac[a] >> 1 : 0;
-        ++sp;
-      }
+      const int kk = sk[f]++;
+      const int L = sl[f];
+      int ac[3] = {sc[f][0] + kk % B::W1 - S, D >= 2 ? sc[f][1] + (kk / B::W1) % B::W1 - S : 0,
+                   D == 3 ? sc[f][2] + kk / (B::W1 * B::W1) - S : 0};
+      if (!mr_nbr_mesh_d<D>(g, L, ac)) continue;  // outside: the stencil clamps to a cell of the box
+      const uint32_t ga = g.base[L] + mr_encode_d<D>(g, L, ac);
+      if (cls[ga] & (3u | MR_C_GHOST)) continue;
+      const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
+      if ((o2 & (3u | MR_C_GHOST)) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
+      sl[sp] = L - 1;
+      sk[sp] = 0;
+      for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? ac[a] >> 1 : 0;
+      ++sp;
     }
   }
 }
@@ -232,12 +286,14 @@ __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict
 // Ghosts and newly created leaves of level J_min + kl: the prediction of
 // half-width s applied to the level-1 values of the new mesh.
 template <int D, int S, int F>
-__global__ void __launch_bounds__(128) k_predict_level_w(const InstDev* __restrict__ IB, int ngrp, int dst, int kl) {
+__global__ void __launch_bounds__(256) k_predict_level_w(const InstDev* __restrict__ IB, int ngrp, int dst, int kl) {
   using St = typename FormT<F>::S;
   using C = typename FormT<F>::C;
   using B = WBox<D, S>;
+  constexpr int TC = WTile<D, S>::TC;
   extern __shared__ int pre[];
   __shared__ InstDev si;
+  __shared__ int32_t sent[B::N][TC];
   int have = -1;
   mr_inst_prefetch(si, have, IB, ngrp);
   mr_grid_dep();
@@ -247,9 +303,10 @@ __global__ void __launch_bounds__(128) k_predict_level_w(const InstDev* __restri
     if (l > gb.J) return 0;
     const MeshCounts* c = IB[b].mesh[dst].cnt;
     return (c->off[MR_CLS_GHOST][l + 1] - c->off[MR_CLS_GHOST][l] + c->off[MR_CLS_LEAF][l + 1] -
-            c->off[MR_CLS_LEAF][l] + 127) / 128;
+            c->off[MR_CLS_LEAF][l] + TC - 1) / TC;
   });
-  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {  // uniform over the block
     const int b = mr_group_find(pre, ngrp, tt);
     mr_inst_use(si, have, IB, b);
     const Geo& g = si.g;
@@ -259,34 +316,43 @@ __global__ void __launch_bounds__(128) k_predict_level_w(const InstDev* __restri
     const int gb = Bm.cnt->off[MR_CLS_GHOST][level], ge = Bm.cnt->off[MR_CLS_GHOST][level + 1];
     const int lb = Bm.cnt->off[MR_CLS_LEAF][level], le = Bm.cnt->off[MR_CLS_LEAF][level + 1];
     const int ng = ge - gb, total = ng + (le - lb);
-    const int t = (tt - pre[b]) * 128 + threadIdx.x;
-    if (t >= total) continue;
-    uint32_t code;
-    St* out;
-    size_t ostride;
-    if (t < ng) {
-      const int i = gb + t;
-      code = Bm.code[MR_CLS_GHOST][i];
-      out = (St*)Bm.GF + i;
-      ostride = g.cap[2];
-    } else {
-      const int i = lb + (t - ng);
-      if (Bm.src[i] >= 0) continue;  // a leaf carried over keeps its transferred values
-      code = Bm.code[MR_CLS_LEAF][i];
-      out = (St*)LF + i;
-      ostride = g.cap[0];
+    const int t = (tt - pre[b]) * TC + tx;
+    bool active = t < total;
+    uint32_t code = 0;
+    St* out = nullptr;
+    size_t ostride = 0;
+    if (active) {
+      if (t < ng) {
+        const int i = gb + t;
+        code = Bm.code[MR_CLS_GHOST][i];
+        out = (St*)Bm.GF + i;
+        ostride = g.cap[2];
+      } else {
+        const int i = lb + (t - ng);
+        active = Bm.src[i] < 0;  // a leaf carried over keeps its transferred values
+        code = Bm.code[MR_CLS_LEAF][i];
+        out = (St*)LF + i;
+        ostride = g.cap[0];
+      }
     }
-    int pc[3] = {0, 0, 0};
-    mr_decode_d<D>(g, level - 1, code >> D, pc);
-    int32_t ent[B::N];
-    if (!wide_stencil<D, S>(g, Bm, level - 1, pc, ent)) {
-      mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
+    __syncthreads();  // the previous tile's readers of sent are done
+    if (active) {
+      int pc[3] = {0, 0, 0};
+      mr_decode_d<D>(g, level - 1, code >> D, pc);
+      for (int e = ty; e < B::N; e += 8) sent[e][tx] = wide_stencil_entry<D, S>(g, Bm, level - 1, pc, e);
+    }
+    __syncthreads();
+    if (!active) continue;
+    bool ok = true;
+    for (int k = 0; k < B::N; ++k) ok = ok && sent[k][tx] != MR_MAP_NONE;
+    if (!ok) {
+      if (ty == 0) mr_set_err(Bm.cnt, MR_DERR_INTERNAL);
       continue;
     }
     const int ci = (int)(code & ((1u << D) - 1u));
-    for (int p = 0; p < g.Q; ++p) {
+    for (int p = ty; p < g.Q; p += 8) {
       C v[B::N];
-      for (int k = 0; k < B::N; ++k) v[k] = ld_c<C>(mr_resolve<St>(g, Bm, LF, ent[k]), p);
+      for (int k = 0; k < B::N; ++k) v[k] = ld_c<C>(mr_resolve<St>(g, Bm, LF, sent[k][tx]), p);
       out[(size_t)p * ostride] = mr_from_d<St>((double)wide_predict<D, S, C, false>(v, ci, g.cross_sign));
     }
   }
@@ -669,12 +735,15 @@ __global__ void __launch_bounds__(128) k_stream_collide_w(const InstDev* __restr
 // ------------------------------------------------------------------ launchers
 template <int D, int S, int F>
 void launch_details_w(const Group& G, int cur, cudaStream_t st) {
-  mr_launch_pdl(k_details_w<D, S, F>, mr_tile_grid(G, G.capI, 128, G.bps[MR_PH_DETAILS]), 128, mr_pre_bytes(G), st, G.dev, G.n, cur);
+  constexpr int TC = WTile<D, S>::TC;
+  mr_launch_pdl(k_details_w<D, S, F>, mr_tile_grid(G, G.capI, TC, G.bps[MR_PH_DETAILS]), dim3(TC, 8), mr_pre_bytes(G),
+                st, G.dev, G.n, cur);
 }
 template <int D, int S, int F>
 void launch_predict_w(const Group& G, int dst, int kl, cudaStream_t st) {
-  mr_launch_pdl(k_predict_level_w<D, S, F>, mr_tile_grid(G, 2 * G.pred_cells[kl], 128, G.bps[MR_PH_PREDICT]), 128, mr_pre_bytes(G), st,
-                G.dev, G.n, dst, kl);
+  constexpr int TC = WTile<D, S>::TC;
+  mr_launch_pdl(k_predict_level_w<D, S, F>, mr_tile_grid(G, 2 * G.pred_cells[kl], TC, G.bps[MR_PH_PREDICT]),
+                dim3(TC, 8), mr_pre_bytes(G), st, G.dev, G.n, dst, kl);
 }
 template <int D, int S, int F>
 void launch_edge_w(const Group& G, int dst, cudaStream_t st) {
