@@ -281,56 +281,41 @@ __device__ __forceinline__ uint32_t ghost_need3(const Geo& g, const uint8_t* cls
   return m;
 }
 
-__device__ void mark_ghosts3(const Geo& g, uint8_t* cls, int l, uint32_t code) {
-  int x[3];
-  mr_decode_d<3>(g, l, code, x);
-  uint32_t need = 0;
-  {
-    // the window's classes first, as independent loads
-    MortonBox3<2> bx;
-    bx.init(g, l, x);
-    const uint8_t* cl = cls + g.base[l];
-#pragma unroll
-    for (int w = 0; w < 12; ++w) {
-      const int axis = w >> 2, k = w & 3, o = k < 2 ? k : k + 1;  // offsets -2, -1, +1, +2
-      const int i = axis == 0 ? o : 2, j = axis == 1 ? o : 2, kk = axis == 2 ? o : 2;
-      if (bx.inside(i, j, kk) && !(cl[bx.code(i, j, kk)] & (3u | MR_C_GHOST))) need |= 1u << w;
+// A cell of level L + 1 became a ghost: mark its parent's 3^D stencil
+// (cell c of level L), cells outside the tree becoming ghosts, and so on
+// towards J_min, depth first; only the thread that marks a cell first walks
+// on from it.
+template <int D>
+__device__ void ghost_cascade(const Geo& g, uint8_t* cls, int L0, const int* c0) {
+  int sl[MR_MAXL], sc[MR_MAXL][3];
+  uint32_t sm[MR_MAXL];
+  sl[0] = L0;
+  for (int a = 0; a < 3; ++a) sc[0][a] = c0[a];
+  if constexpr (D == 3)
+    sm[0] = ghost_need3(g, cls, L0, sc[0]);
+  else
+    sm[0] = ghost_stencil_need<D>(g, cls, L0, sc[0][0], sc[0][1]);
+  int sp = 1;
+  while (sp > 0) {
+    const int t = sp - 1;
+    if (sm[t] == 0u) {
+      --sp;
+      continue;
     }
-  }
-  while (need) {
-    const int w = __ffs(need) - 1;
-    need &= need - 1u;
-    const int axis = w >> 2, k = w & 3;
-    int nb[3] = {x[0], x[1], x[2]};
-    nb[axis] += k < 2 ? k - 2 : k - 1;
-    mr_nbr_mesh_d<3>(g, l, nb);  // inside: only such cells enter the mask
-    const uint32_t gw = g.base[l] + mr_encode_d<3>(g, l, nb);
-    const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
-    if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
-    int sl[MR_MAXL], sc[MR_MAXL][3];
-    uint32_t sm[MR_MAXL];
-    sl[0] = l - 1;
-    for (int a = 0; a < 3; ++a) sc[0][a] = nb[a] >> 1;
-    sm[0] = ghost_need3(g, cls, l - 1, sc[0]);
-    int sp = 1;
-    while (sp > 0) {
-      const int t = sp - 1;
-      if (sm[t] == 0u) {
-        --sp;
-        continue;
-      }
-      const int kk = __ffs(sm[t]) - 1;
-      sm[t] &= sm[t] - 1u;
-      const int L = sl[t];
-      int ac[3] = {sc[t][0] + kk % 3 - 1, sc[t][1] + (kk / 3) % 3 - 1, sc[t][2] + kk / 9 - 1};
-      mr_nbr_mesh_d<3>(g, L, ac);
-      const uint32_t o2 = mr_atomic_or_byte(cls, g.base[L] + mr_encode_d<3>(g, L, ac), MR_C_GHOST);
-      if ((o2 & MR_C_GHOST) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
-      sl[sp] = L - 1;
-      for (int a = 0; a < 3; ++a) sc[sp][a] = ac[a] >> 1;
+    const int k = __ffs(sm[t]) - 1;
+    sm[t] &= sm[t] - 1u;
+    const int L = sl[t];
+    int ac[3] = {sc[t][0] + k % 3 - 1, D >= 2 ? sc[t][1] + (k / 3) % 3 - 1 : 0, D == 3 ? sc[t][2] + k / 9 - 1 : 0};
+    mr_nbr_mesh_d<D>(g, L, ac);  // inside: only such cells enter the mask
+    const uint32_t o2 = mr_atomic_or_byte(cls, g.base[L] + mr_encode_d<D>(g, L, ac), MR_C_GHOST);
+    if ((o2 & MR_C_GHOST) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
+    sl[sp] = L - 1;
+    for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? ac[a] >> 1 : 0;
+    if constexpr (D == 3)
       sm[sp] = ghost_need3(g, cls, L - 1, sc[sp]);
-      ++sp;
-    }
+    else
+      sm[sp] = ghost_stencil_need<D>(g, cls, L - 1, sc[sp][0], sc[sp][1]);
+    ++sp;
   }
 }
 
@@ -370,12 +355,25 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
   }
   __syncthreads();
   const int nq = qn;
+  if constexpr (D == 3) {
+    // (leaf, window cell) pairs over the whole block: the 12 axis window
+    // cells of a leaf are independent, and most are in the tree already
+    for (int it = threadIdx.x; it < nq * 12; it += blockDim.x) {
+      const int w = it % 12, k = w & 3;
+      int nb[3];
+      mr_decode_d<3>(g, l, cb + queue[it / 12], nb);
+      nb[w >> 2] += k < 2 ? k - 2 : k - 1;  // -2, -1, +1, +2 along axis w / 4
+      if (!mr_nbr_mesh_d<3>(g, l, nb)) continue;
+      const uint32_t gw = g.base[l] + mr_encode_d<3>(g, l, nb);
+      if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
+      const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
+      if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
+      const int pc[3] = {nb[0] >> 1, nb[1] >> 1, nb[2] >> 1};
+      ghost_cascade<3>(g, cls, l - 1, pc);
+    }
+  } else {
   for (int qi = threadIdx.x; qi < nq; qi += blockDim.x) {
     const uint32_t c = cb + queue[qi];
-    if constexpr (D == 3) {
-      mark_ghosts3(g, cls, l, c);
-      continue;
-    }
     int x, y;
     mr_decode(g, l, c, x, y);
     uint32_t need = 0;
@@ -416,33 +414,10 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
       const uint32_t old = mr_atomic_or_byte(cls, g.base[l] + mr_encode(g, l, nx, ny), MR_C_GHOST);
       if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
       // cascade: the stencil of the ghost's parent, towards coarser levels
-      int sl[MR_MAXL], sx[MR_MAXL], sy[MR_MAXL];
-      uint32_t sm[MR_MAXL];
-      sl[0] = l - 1;
-      sx[0] = nx >> 1;
-      sy[0] = ny >> 1;
-      sm[0] = ghost_stencil_need<D>(g, cls, l - 1, sx[0], sy[0]);
-      int sp = 1;
-      while (sp > 0) {
-        const int t = sp - 1;
-        if (sm[t] == 0u) {
-          --sp;
-          continue;
-        }
-        const int k = __ffs(sm[t]) - 1;
-        sm[t] &= sm[t] - 1u;
-        const int L = sl[t];
-        int ax = sx[t] + (k % 3) - 1, ay = D == 2 ? sy[t] + (k / 3) - 1 : 0;
-        mr_nbr_mesh(g, L, ax, ay);
-        const uint32_t o2 = mr_atomic_or_byte(cls, g.base[L] + mr_encode(g, L, ax, ay), MR_C_GHOST);
-        if ((o2 & MR_C_GHOST) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
-        sl[sp] = L - 1;
-        sx[sp] = ax >> 1;
-        sy[sp] = ay >> 1;
-        sm[sp] = ghost_stencil_need<D>(g, cls, L - 1, sx[sp], sy[sp]);
-        ++sp;
-      }
+      const int pc[3] = {nx >> 1, ny >> 1, 0};
+      ghost_cascade<D>(g, cls, l - 1, pc);
     }
+  }
   }
 }
 
