@@ -546,22 +546,24 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict_
       for (int c = 0; c < 3; ++c) carry[c] = run[c];
     __syncthreads();
   }
-  // per-level offsets: every level starts on a block boundary
-  if (threadIdx.x < 3) {
-    const int c = threadIdx.x;
-    // counts are clamped to the capacity so that no later kernel can run
-    // past an array; the overflow itself is reported through err
-    cnt->total[c] = carry[c] < g.cap[c] ? carry[c] : g.cap[c];
-    if (carry[c] > g.cap[c]) atomicOr(&cnt->err, MR_DERR_CAPACITY);
-    for (int l = 0; l <= MR_MAXL; ++l) {
-      int v;
-      if (l < g.Jmin)
-        v = 0;
-      else if (l <= g.J)
-        v = bc[(g.base[l] / MR_DENSE_ALIGN) * 3 + c];
-      else
-        v = cnt->total[c];
-      cnt->off[c][l] = v < g.cap[c] ? v : g.cap[c];
+  // per-level offsets (every level starts on a block boundary), one thread
+  // per class and level so that the loads are issued together; counts are
+  // clamped to the capacity so that no later kernel can run past an array,
+  // and the overflow itself is reported through err
+  if (threadIdx.x < 3 * (MR_MAXL + 1)) {
+    const int c = threadIdx.x % 3, l = threadIdx.x / 3;
+    const int total = carry[c] < g.cap[c] ? carry[c] : g.cap[c];
+    int v;
+    if (l < g.Jmin)
+      v = 0;
+    else if (l <= g.J)
+      v = bc[(g.base[l] / MR_DENSE_ALIGN) * 3 + c];
+    else
+      v = total;
+    cnt->off[c][l] = v < g.cap[c] ? v : g.cap[c];
+    if (l == 0) {
+      cnt->total[c] = total;
+      if (carry[c] > g.cap[c]) atomicOr(&cnt->err, MR_DERR_CAPACITY);
     }
   }
 }
