@@ -384,6 +384,8 @@ void fill_desc(const mr_lbm* h, InstDev& d) {
   d.fscratch = h->fscratch;
   d.flags = h->flags;
   d.cls = h->cls;
+  d.act = h->act;
+  d.acth = h->act + h->g.base[h->g.J + 1] / MR_DENSE_ALIGN;
   d.bcounts = h->bcounts;
   d.W = h->W;
   d.Wf = h->Wf;
@@ -825,8 +827,9 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   const size_t dense = g.base[g.J + 1];
   const size_t eb = mr_form_bytes(g.form);  // bytes per stored population value
   char *fs = nullptr, *fsc = nullptr;
+  const size_t nch = dense / MR_DENSE_ALIGN;  // every level starts on a chunk boundary
   bool ok = dalloc(h, &h->cntbuf, 2) && dalloc(h, &h->flags, dense) && dalloc(h, &h->cls, dense) &&
-            dalloc(h, &h->bcounts, 3 * (dense / MR_DENSE_ALIGN + 1)) && dalloc(h, &h->inidx, dense) &&
+            dalloc(h, &h->act, 2 * nch) && dalloc(h, &h->bcounts, 3 * (nch + 1)) && dalloc(h, &h->inidx, dense) &&
             dalloc(h, &h->vol, 1) && dalloc(h, &fs, eb * g.Q * g.cap[0]) && dalloc(h, &fsc, eb * g.Q * g.cap[0]);
   h->fstate = fs;
   h->fscratch = fsc;
@@ -834,7 +837,7 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
     MeshDev& M = h->mesh[mi];
     for (int c = 0; c < 3 && ok; ++c) ok = dalloc(h, &M.code[c], g.cap[c]) && dalloc(h, &M.lvl[c], g.cap[c]);
     char *ifp = nullptr, *gfp = nullptr;
-    ok = ok && dalloc(h, &M.map, dense) && dalloc(h, &ifp, eb * g.Q * g.cap[1]) &&
+    ok = ok && dalloc(h, &M.map, dense) && dalloc(h, &M.mact, nch) && dalloc(h, &ifp, eb * g.Q * g.cap[1]) &&
          dalloc(h, &gfp, eb * g.Q * g.cap[2]) && dalloc(h, &M.G, g.cap[1]) && dalloc(h, &M.src, g.cap[0]);
     M.IF = ifp;
     M.GF = gfp;
@@ -875,6 +878,9 @@ mr_status mr_lbm_create(const mr_lbm_config* cfg, void* cuda_stream, mr_lbm_t* o
   bool cok = cudaMemsetAsync(h->cntbuf, 0, 2 * sizeof(MeshCounts), h->st) == cudaSuccess &&
              cudaMemsetAsync(h->flags, 0, dense, h->st) == cudaSuccess &&
              cudaMemsetAsync(h->cls, 0, dense, h->st) == cudaSuccess &&
+             cudaMemsetAsync(h->act, 0, 2 * nch, h->st) == cudaSuccess &&
+             cudaMemsetAsync(h->mesh[0].mact, 0, nch, h->st) == cudaSuccess &&
+             cudaMemsetAsync(h->mesh[1].mact, 0, nch, h->st) == cudaSuccess &&
              cudaMemsetAsync(h->inidx, 0xff, dense * sizeof(int32_t), h->st) == cudaSuccess &&
              cudaMemsetAsync(h->mesh[0].map, 0xff, dense * sizeof(int32_t), h->st) == cudaSuccess &&
              cudaMemsetAsync(h->mesh[1].map, 0xff, dense * sizeof(int32_t), h->st) == cudaSuccess &&
@@ -960,7 +966,7 @@ static mr_status init_impl(mr_lbm_t h, const double* conserved, int on_device) {
     src = (const double*)h->staging;
   }
   MeshDev& B = h->mesh[h->cur];
-  mr_launch_full_mesh(g, h->cls, h->st, grid_for(h));
+  mr_launch_full_mesh(g, h->cls, h->act, h->st, grid_for(h));
   count_launch(h);
   run_build(*h, h->grp, h->cur);
   mr_launch_init_eq(g, B, src, h->fstate, h->st, grid_for(h));
@@ -1137,7 +1143,7 @@ mr_status mr_lbm_set_leaves(mr_lbm_t h, long long n, const unsigned long long* k
     release();
     return MR_ECUDA;
   }
-  mr_launch_leaves_in(g, n, dk, dl, h->inidx, h->cls, B.cnt, h->vol, h->st, grid_for(h));
+  mr_launch_leaves_in(g, n, dk, dl, h->inidx, h->cls, h->act, B.cnt, h->vol, h->st, grid_for(h));
   mr_launch_leaves_check(g, h->cls, B.cnt, h->st, grid_for(h));
   count_launch(h, 2);
   unsigned long long vol = 0;

@@ -143,6 +143,10 @@ __device__ __forceinline__ uint32_t mr_atomic_or_byte(uint8_t* base, uint32_t id
 
 __device__ __forceinline__ void mr_set_err(MeshCounts* c, int bits) { atomicOr(&c->err, bits); }
 
+// The cell of dense index gi was flagged, classified or marked: the dense
+// passes of this step visit its 1024-cell chunk (every writer stores 1).
+__device__ __forceinline__ void mr_touch(uint8_t* act, uint32_t gi) { act[gi / MR_DENSE_ALIGN] = 1; }
+
 // level of a dense index (levels J_min..J)
 __device__ __forceinline__ int mr_level_of(const Geo& g, uint32_t gi) {
   int l = g.Jmin;

@@ -46,6 +46,7 @@ struct mr_lbm : Exec {
   void* fscratch = nullptr;  // pre-transport leaf populations, same layout
   uint8_t* flags = nullptr;
   uint8_t* cls = nullptr;
+  uint8_t* act = nullptr;  // two bytes per dense chunk: InstDev::act, then InstDev::acth
   int* bcounts = nullptr;
   int32_t* inidx = nullptr;
   unsigned long long* vol = nullptr;

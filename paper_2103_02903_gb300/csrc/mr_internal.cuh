@@ -101,6 +101,7 @@ struct MeshDev {
   double* G;           // group norm per internal cell
   int32_t* src;        // per leaf: source entry in the previous mesh, -1 if predicted
   MeshCounts* cnt;
+  uint8_t* mact;       // per dense chunk: 1 if map holds an entry (not -1) in it
 };
 
 // ------------------------------------------------------------------------
@@ -302,6 +303,8 @@ struct __align__(16) InstDev {
   void* fscratch;
   uint8_t* flags;     // dense: T / H / G marks
   uint8_t* cls;       // dense: classification of the new mesh
+  uint8_t* act;       // per dense chunk: 1 if a cell of it may be flagged, in the new tree or a ghost
+  uint8_t* acth;      // per dense chunk: 1 if a cell of it may carry the H flag (grading seeds)
   int* bcounts;       // per dense chunk: leaf / internal / ghost counts, then offsets
   const double* W;    // flattened weights, MR_WIDX layout
   const float* Wf;    // the same in FP32
@@ -388,6 +391,7 @@ void mr_launch_flags_H(const Group& G, int cur, cudaStream_t st);
 void mr_launch_grade(const Group& G, cudaStream_t st);
 void mr_launch_classify(const Group& G, cudaStream_t st);
 void mr_launch_mark_ghosts(const Group& G, cudaStream_t st);
+int mr_chunk_blocks_grid(const Group& G);  // grid of the dense kernels that take a block per chunk
 void mr_launch_compact(const Group& G, int dst, cudaStream_t st);  // count + scan + scatter into mesh dst
 void mr_launch_remesh_copy(const Group& G, int cur, cudaStream_t st);
 void mr_launch_predict_level(const Group& G, int dst, int k, cudaStream_t st);  // level J_min + k
@@ -404,9 +408,9 @@ int mr_launch_exact_collision(const Group& G, int dst, double* Fd, long long nd,
 // Input / output kernels of one instance.
 void mr_launch_init_eq(const Geo& g, const MeshDev& B, const double* cons, void* LF,
                        cudaStream_t st, int grid);
-void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int grid);
+void mr_launch_full_mesh(const Geo& g, uint8_t* cls, uint8_t* act, cudaStream_t st, int grid);
 void mr_launch_leaves_in(const Geo& g, long long n, const unsigned long long* keys,
-                         const signed char* levels, int32_t* inidx, uint8_t* cls, MeshCounts* cnt,
+                         const signed char* levels, int32_t* inidx, uint8_t* cls, uint8_t* act, MeshCounts* cnt,
                          unsigned long long* vol, cudaStream_t st, int grid);
 void mr_launch_leaves_check(const Geo& g, uint8_t* cls, MeshCounts* cnt, cudaStream_t st, int grid);
 void mr_launch_gather_input(const Geo& g, const MeshDev& B, const int32_t* inidx, long long n,

@@ -11,11 +11,31 @@
 // are benign; the closure under ancestors and the grading cascade are
 // walked by the thread that first sets a flag, which makes each of them a
 // single kernel whatever the number of levels.
+//
+// The dense arrays are visited chunk by chunk (1024 cells of one level), and
+// only the chunks a writer touched: every flag, class or ghost mark also
+// stores 1 into the chunk's activity byte (act; acth for the H flags that
+// seed the grading), a refined cell touching the chunk of its children too,
+// so that a chunk never touched keeps all its flag and class bytes at 0 and
+// is skipped.  The compaction clears the bytes of the chunks it visits, and
+// rewrites a chunk of the new index map only if it holds entries now or did
+// in the mesh last written there (mact).
 #include "mr_common.cuh"
 
 namespace {
 
 __device__ __forceinline__ double level_eps(const Geo& g, int l) { return ldexp(g.eps, g.d * (l - g.J)); }
+
+// A cell (level L < J, code c) newly refined (H or G): its own chunk and the
+// chunk of its children (all 2^D of them in one chunk) hold cells of the new
+// tree; an H cell also seeds the grading from its chunk.
+template <int D>
+__device__ __forceinline__ void touch_refined(const InstDev& si, int L, uint32_t c, bool seed) {
+  const uint32_t gi = si.g.base[L] + c;
+  mr_touch(si.act, gi);
+  mr_touch(si.act, si.g.base[L + 1] + (c << D));
+  if (seed) mr_touch(si.acth, gi);
+}
 
 // ---------------------------------------------------------------- T_eps
 // Tiled step kernels over the internal cells of the current mesh: a tile is
@@ -49,6 +69,7 @@ __global__ void __launch_bounds__(256) k_flags_T(const InstDev* __restrict__ IB,
       // a plain load first: most ancestors are already marked
       if (flags[g.base[l] + c] & MR_F_T) break;
       uint32_t old = mr_atomic_or_byte(flags, g.base[l] + c, MR_F_T);
+      if (!old) mr_touch(si.act, g.base[l] + c);
       if ((old & MR_F_T) || l == g.Jmin) break;
       --l;
       c >>= D;
@@ -65,6 +86,7 @@ __global__ void __launch_bounds__(256) k_flags_H(const InstDev* __restrict__ IB,
     const uint32_t code = A.code[MR_CLS_INT][i];
     if (!(flags[g.base[L] + code] & MR_F_T)) continue;
     mr_atomic_or_byte(flags, g.base[L] + code, MR_F_H);
+    touch_refined<D>(si, L, code, true);
     int c0[3] = {0, 0, 0};
     mr_decode_d<D>(g, L, code, c0);
     // neighbour rule (Eq. AdditionNeigh) on the children, which are the
@@ -75,14 +97,16 @@ __global__ void __launch_bounds__(256) k_flags_H(const InstDev* __restrict__ IB,
         for (int a = 0; a < D; ++a) nb[a] = 2 * c0[a] + ((ci >> a) & 1) - g.eta[h][a];
         if (!mr_nbr_mesh_d<D>(g, L + 1, nb)) continue;
         for (int a = 0; a < D; ++a) nb[a] >>= 1;
-        const uint32_t gi = g.base[L] + mr_encode_d<D>(g, L, nb);
-        if (!(flags[gi] & MR_F_H)) mr_atomic_or_byte(flags, gi, MR_F_H);
+        const uint32_t nc = mr_encode_d<D>(g, L, nb), gi = g.base[L] + nc;
+        if (!(flags[gi] & MR_F_H) && !(mr_atomic_or_byte(flags, gi, MR_F_H) & MR_F_H))
+          touch_refined<D>(si, L, nc, true);
       }
     }
     // refinement rule (Sec. 5.1): J_min < L+1 < J and group norm >= 2^{mu+d} eps_{L+1}
     if (L + 1 > g.Jmin && L + 1 < g.J && A.G[i] >= ldexp(level_eps(g, L + 1), g.mu_bar + D)) {
       for (int ci = 0; ci < (1 << D); ++ci)
         mr_atomic_or_byte(flags, g.base[L + 1] + ((code << D) | (uint32_t)ci), MR_F_H);
+      touch_refined<D>(si, L + 1, code << D, true);  // the children share their chunks
     }
   MR_INT_TILES_END
 }
@@ -147,7 +171,8 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
     mr_inst_use(si, have, IB, b);
     const Geo& g = si.g;
     uint8_t* flags = si.flags;
-    const uint32_t gi = g.base[g.Jmin + 1] + (uint32_t)(t - pre[b]) * 256u + threadIdx.x;
+    const uint32_t t0 = g.base[g.Jmin + 1] + (uint32_t)(t - pre[b]) * 256u, gi = t0 + threadIdx.x;
+    if (!si.acth[t0 / MR_DENSE_ALIGN]) continue;  // no H flag in this tile's chunk
     if (gi >= g.base[g.J]) continue;
     if (!(flags[gi] & MR_F_H)) continue;
     const int l0 = mr_level_of(g, gi);
@@ -181,7 +206,9 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
       mr_nbr_mesh_d<D>(g, L, nb);  // inside: only such cells enter the mask
       const int tl = L - 1;
       for (int a = 0; a < D; ++a) nb[a] >>= 1;
-      const uint32_t old = mr_atomic_or_byte(flags, g.base[tl] + mr_encode_d<D>(g, tl, nb), MR_F_G);
+      const uint32_t nc = mr_encode_d<D>(g, tl, nb);
+      const uint32_t old = mr_atomic_or_byte(flags, g.base[tl] + nc, MR_F_G);
+      if (!(old & (MR_F_H | MR_F_G))) touch_refined<D>(si, tl, nc, false);
       if (!(old & (MR_F_H | MR_F_G)) && tl > g.Jmin && sp < MR_MAXL) {
         sl[sp] = tl;
         sx[sp] = nb[0];
@@ -198,24 +225,69 @@ __global__ void __launch_bounds__(256) k_grade(const InstDev* __restrict__ IB, i
 }
 
 // ---------------------------------------------------------------- classify
+// One warp per touched chunk, grid-stride over the chunks of all instances:
+// lane L classifies cells 32L .. 32L+31 of the chunk from their own flag
+// bytes (two 16-byte loads) and their parents' (32 >> D consecutive bytes),
+// and writes the 32 class bytes with two 16-byte stores.  A chunk of a level
+// above J_min that nothing touched has no refined parent: its class bytes
+// stay 0.
 template <int D>
 __global__ void __launch_bounds__(256) k_classify(const InstDev* __restrict__ IB,
-                                                  const int* __restrict__ chunk_pre, int n) {
-  __shared__ InstDev si;
-  int chunk, have = -1;
-  mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
-  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
-  const Geo& g = si.g;
-  const uint8_t* flags = si.flags;
-  uint8_t* cls = si.cls;
-  MR_DENSE_CHUNK_BEGIN(g, chunk, l, c, gi)
-    const bool inR = (l == g.Jmin) || (flags[g.base[l - 1] + (c >> D)] & (MR_F_H | MR_F_G));
-    const bool ref = (l < g.J) && (flags[gi] & (MR_F_H | MR_F_G));
-    cls[gi] = inR ? (ref ? MR_C_INT : MR_C_LEAF) : 0;
-  MR_DENSE_CHUNK_END
+                                                  const int* __restrict__ chunk_pre, int n, int nchunks) {
+  mr_grid_dep();
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < nchunks; t += nw) {
+    int chunk;
+    const InstDev& I = IB[mr_group_chunk_of(chunk_pre, n, t, chunk)];
+    const Geo& g = I.g;
+    const uint32_t c0 = (uint32_t)chunk * MR_DENSE_ALIGN;
+    const int l = mr_level_of(g, c0);
+    const bool top = l == g.Jmin;
+    if (!top && !__shfl_sync(0xffffffffu, (int)I.act[chunk], 0)) continue;
+    if (top && lane == 0) I.act[chunk] = 1;  // the counts and the scatter visit it
+    const uint32_t first = c0 - g.base[l] + 32u * (uint32_t)lane, ncode = g.ncode[l];
+    uint32_t fw[8] = {0, 0, 0, 0, 0, 0, 0, 0}, pw[4] = {0, 0, 0, 0};
+    if (l < g.J) {
+      const uint4* fp = (const uint4*)(I.flags + c0) + 2 * lane;
+      const uint4 a = fp[0], b = fp[1];
+      fw[0] = a.x; fw[1] = a.y; fw[2] = a.z; fw[3] = a.w;
+      fw[4] = b.x; fw[5] = b.y; fw[6] = b.z; fw[7] = b.w;
+    }
+    if (!top) {
+      const uint8_t* pp = I.flags + g.base[l - 1] + (first >> D);  // 32 >> D bytes, aligned to their size
+      if constexpr (D == 1) {
+        const uint4 a = *(const uint4*)pp;
+        pw[0] = a.x; pw[1] = a.y; pw[2] = a.z; pw[3] = a.w;
+      } else if constexpr (D == 2) {
+        const uint2 a = *(const uint2*)pp;
+        pw[0] = a.x; pw[1] = a.y;
+      } else {
+        pw[0] = *(const uint32_t*)pp;
+      }
+    }
+    uint32_t ow[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      uint32_t o = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = 4 * w + k, pj = j >> D;
+        const uint32_t pb = (pw[pj >> 2] >> (8 * (pj & 3))) & 0xFFu, fb = (fw[w] >> (8 * k)) & 0xFFu;
+        const bool inR = top || (pb & (MR_F_H | MR_F_G));
+        const uint32_t v = !inR || first + (uint32_t)j >= ncode ? 0u : ((fb & (MR_F_H | MR_F_G)) ? MR_C_INT : MR_C_LEAF);
+        o |= v << (8 * k);
+      }
+      ow[w] = o;
+    }
+    uint4* cp = (uint4*)(I.cls + c0) + 2 * lane;
+    cp[0] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+    cp[1] = make_uint4(ow[4], ow[5], ow[6], ow[7]);
+  }
 }
 
-__global__ void __launch_bounds__(256) k_full_mesh(Geo g, uint8_t* cls) {
+__global__ void __launch_bounds__(256) k_full_mesh(Geo g, uint8_t* cls, uint8_t* act) {
+  if (threadIdx.x == 0) act[blockIdx.x] = 1;
   MR_DENSE_CHUNK_BEGIN(g, blockIdx.x, l, c, gi)
     (void)c;
     cls[gi] = l == g.J ? MR_C_LEAF : MR_C_INT;
@@ -286,7 +358,7 @@ __device__ __forceinline__ uint32_t ghost_need3(const Geo& g, const uint8_t* cls
 // towards J_min, depth first; only the thread that marks a cell first walks
 // on from it.
 template <int D>
-__device__ void ghost_cascade(const Geo& g, uint8_t* cls, int L0, const int* c0) {
+__device__ void ghost_cascade(const Geo& g, uint8_t* cls, uint8_t* act, int L0, const int* c0) {
   int sl[MR_MAXL], sc[MR_MAXL][3];
   uint32_t sm[MR_MAXL];
   sl[0] = L0;
@@ -307,7 +379,9 @@ __device__ void ghost_cascade(const Geo& g, uint8_t* cls, int L0, const int* c0)
     const int L = sl[t];
     int ac[3] = {sc[t][0] + k % 3 - 1, D >= 2 ? sc[t][1] + (k / 3) % 3 - 1 : 0, D == 3 ? sc[t][2] + k / 9 - 1 : 0};
     mr_nbr_mesh_d<D>(g, L, ac);  // inside: only such cells enter the mask
-    const uint32_t o2 = mr_atomic_or_byte(cls, g.base[L] + mr_encode_d<D>(g, L, ac), MR_C_GHOST);
+    const uint32_t ga = g.base[L] + mr_encode_d<D>(g, L, ac);
+    const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
+    if (!o2) mr_touch(act, ga);
     if ((o2 & MR_C_GHOST) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
     sl[sp] = L - 1;
     for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? ac[a] >> 1 : 0;
@@ -319,106 +393,117 @@ __device__ void ghost_cascade(const Geo& g, uint8_t* cls, int L0, const int* c0)
   }
 }
 
+// A block per touched chunk at a time, grid-stride over the chunks of all
+// instances (a chunk nothing touched holds no leaf).
 template <int D>
 __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__ IB,
-                                                     const int* __restrict__ chunk_pre, int n) {
+                                                     const int* __restrict__ chunk_pre, int n, int nchunks) {
   __shared__ InstDev si;
   __shared__ uint16_t queue[MR_DENSE_ALIGN];  // the chunk's leaves (offsets in the chunk)
   __shared__ int qn;
-  int chunk, have = -1;
-  mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
-  mr_grid_dep();  // after the copy of the descriptor, which no step kernel writes
-  const Geo& g = si.g;
-  uint8_t* cls = si.cls;
-  const bool block = D == 2 && g.diag;
-  const uint32_t c0 = (uint32_t)chunk * MR_DENSE_ALIGN;
-  const int l = mr_level_of(g, c0);
-  const uint32_t cb = c0 - g.base[l];
-  if (threadIdx.x == 0) qn = 0;
-  __syncthreads();
-  // Leaves are a few per cent of the dense cells: gather them first, so that
-  // the marking below runs on full warps instead of one lane in 32.  The
-  // marks are a union (atomic ORs; only the thread that sets a ghost walks
-  // its parent stencil), so the result does not depend on the order.
-  {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < (int)(MR_DENSE_ALIGN / 256u); ++k) {
-      const uint32_t off = (uint32_t)k * 256u + threadIdx.x;
-      const bool leaf = cb + off < g.ncode[l] && (cls[c0 + off] & 3u) == MR_C_LEAF;
-      const uint32_t bal = __ballot_sync(0xffffffffu, leaf);
-      int at = 0;
-      if (lane == 0 && bal) at = atomicAdd(&qn, __popc(bal));
-      at = __shfl_sync(0xffffffffu, at, 0);
-      if (leaf) queue[at + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)off;
+  int have = -1;
+  mr_grid_dep();
+  for (int t = blockIdx.x; t < nchunks; t += gridDim.x) {
+    int chunk;
+    const int ib = mr_group_chunk_of(chunk_pre, n, t, chunk);
+    // one read for the block (other blocks may touch the byte meanwhile)
+    if (!__syncthreads_or(threadIdx.x == 0 && IB[ib].act[chunk])) continue;
+    mr_inst_use(si, have, IB, ib);
+    const Geo& g = si.g;
+    uint8_t* cls = si.cls;
+    const bool block = D == 2 && g.diag;
+    const uint32_t c0 = (uint32_t)chunk * MR_DENSE_ALIGN;
+    const int l = mr_level_of(g, c0);
+    const uint32_t cb = c0 - g.base[l];
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+    // Leaves are a few per cent of the dense cells: gather them first, so that
+    // the marking below runs on full warps instead of one lane in 32.  The
+    // marks are a union (atomic ORs; only the thread that sets a ghost walks
+    // its parent stencil), so the result does not depend on the order.
+    {
+      const int lane = threadIdx.x & 31;
+  #pragma unroll
+      for (int k = 0; k < (int)(MR_DENSE_ALIGN / 256u); ++k) {
+        const uint32_t off = (uint32_t)k * 256u + threadIdx.x;
+        const bool leaf = cb + off < g.ncode[l] && (cls[c0 + off] & 3u) == MR_C_LEAF;
+        const uint32_t bal = __ballot_sync(0xffffffffu, leaf);
+        int at = 0;
+        if (lane == 0 && bal) at = atomicAdd(&qn, __popc(bal));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (leaf) queue[at + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)off;
+      }
     }
-  }
-  __syncthreads();
-  const int nq = qn;
-  if constexpr (D == 3) {
-    // (leaf, window cell) pairs over the whole block: the 12 axis window
-    // cells of a leaf are independent, and most are in the tree already
-    for (int it = threadIdx.x; it < nq * 12; it += blockDim.x) {
-      const int w = it % 12, k = w & 3;
-      int nb[3];
-      mr_decode_d<3>(g, l, cb + queue[it / 12], nb);
-      nb[w >> 2] += k < 2 ? k - 2 : k - 1;  // -2, -1, +1, +2 along axis w / 4
-      if (!mr_nbr_mesh_d<3>(g, l, nb)) continue;
-      const uint32_t gw = g.base[l] + mr_encode_d<3>(g, l, nb);
-      if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
-      const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
-      if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
-      const int pc[3] = {nb[0] >> 1, nb[1] >> 1, nb[2] >> 1};
-      ghost_cascade<3>(g, cls, l - 1, pc);
-    }
-  } else {
-  for (int qi = threadIdx.x; qi < nq; qi += blockDim.x) {
-    const uint32_t c = cb + queue[qi];
-    int x, y;
-    mr_decode(g, l, c, x, y);
-    uint32_t need = 0;
-    const uint8_t* cl = cls + g.base[l];
-    if constexpr (D == 2) {
-      MortonBox<2> bx;
-      bx.init(g, l, x, y);
-      if (block) {
-#pragma unroll
-        for (int w = 0; w < 25; ++w) {
-          if (w == 12) continue;  // the leaf itself
-          if (bx.in(w % 5, w / 5) && !(cl[bx.code(w % 5, w / 5)] & (3u | MR_C_GHOST))) need |= 1u << w;
-        }
-      } else {
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-          const int axis = w >> 2, k = w & 3;
-          const int off = k < 2 ? k - 2 : k - 1;
-          const int a = axis == 0 ? 2 + off : 2, b = axis == 1 ? 2 + off : 2;
-          if (bx.in(a, b) && !(cl[bx.code(a, b)] & (3u | MR_C_GHOST))) need |= 1u << w;
-        }
+    __syncthreads();
+    const int nq = qn;
+    if constexpr (D == 3) {
+      // (leaf, window cell) pairs over the whole block: the 12 axis window
+      // cells of a leaf are independent, and most are in the tree already
+      for (int it = threadIdx.x; it < nq * 12; it += blockDim.x) {
+        const int w = it % 12, k = w & 3;
+        int nb[3];
+        mr_decode_d<3>(g, l, cb + queue[it / 12], nb);
+        nb[w >> 2] += k < 2 ? k - 2 : k - 1;  // -2, -1, +1, +2 along axis w / 4
+        if (!mr_nbr_mesh_d<3>(g, l, nb)) continue;
+        const uint32_t gw = g.base[l] + mr_encode_d<3>(g, l, nb);
+        if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
+        const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
+        if (!old) mr_touch(si.act, gw);
+        if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
+        const int pc[3] = {nb[0] >> 1, nb[1] >> 1, nb[2] >> 1};
+        ghost_cascade<3>(g, cls, si.act, l - 1, pc);
       }
     } else {
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
+    for (int qi = threadIdx.x; qi < nq; qi += blockDim.x) {
+      const uint32_t c = cb + queue[qi];
+      int x, y;
+      mr_decode(g, l, c, x, y);
+      uint32_t need = 0;
+      const uint8_t* cl = cls + g.base[l];
+      if constexpr (D == 2) {
+        MortonBox<2> bx;
+        bx.init(g, l, x, y);
+        if (block) {
+  #pragma unroll
+          for (int w = 0; w < 25; ++w) {
+            if (w == 12) continue;  // the leaf itself
+            if (bx.in(w % 5, w / 5) && !(cl[bx.code(w % 5, w / 5)] & (3u | MR_C_GHOST))) need |= 1u << w;
+          }
+        } else {
+  #pragma unroll
+          for (int w = 0; w < 8; ++w) {
+            const int axis = w >> 2, k = w & 3;
+            const int off = k < 2 ? k - 2 : k - 1;
+            const int a = axis == 0 ? 2 + off : 2, b = axis == 1 ? 2 + off : 2;
+            if (bx.in(a, b) && !(cl[bx.code(a, b)] & (3u | MR_C_GHOST))) need |= 1u << w;
+          }
+        }
+      } else {
+  #pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          int nx, ny;
+          ghost_window_cell(false, w, x, y, nx, ny);
+          if (!mr_nbr_mesh(g, l, nx, ny)) continue;
+          if (!(cl[mr_encode(g, l, nx, ny)] & (3u | MR_C_GHOST))) need |= 1u << w;
+        }
+      }
+      while (need) {
+        const int w = __ffs(need) - 1;
+        need &= need - 1u;
         int nx, ny;
-        ghost_window_cell(false, w, x, y, nx, ny);
-        if (!mr_nbr_mesh(g, l, nx, ny)) continue;
-        if (!(cl[mr_encode(g, l, nx, ny)] & (3u | MR_C_GHOST))) need |= 1u << w;
+        ghost_window_cell(block, w, x, y, nx, ny);
+        mr_nbr_mesh(g, l, nx, ny);  // inside: only such cells enter the mask
+        const uint32_t gw = g.base[l] + mr_encode(g, l, nx, ny);
+        const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
+        if (!old) mr_touch(si.act, gw);
+        if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
+        // cascade: the stencil of the ghost's parent, towards coarser levels
+        const int pc[3] = {nx >> 1, ny >> 1, 0};
+        ghost_cascade<D>(g, cls, si.act, l - 1, pc);
       }
     }
-    while (need) {
-      const int w = __ffs(need) - 1;
-      need &= need - 1u;
-      int nx, ny;
-      ghost_window_cell(block, w, x, y, nx, ny);
-      mr_nbr_mesh(g, l, nx, ny);  // inside: only such cells enter the mask
-      const uint32_t old = mr_atomic_or_byte(cls, g.base[l] + mr_encode(g, l, nx, ny), MR_C_GHOST);
-      if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
-      // cascade: the stencil of the ghost's parent, towards coarser levels
-      const int pc[3] = {nx >> 1, ny >> 1, 0};
-      ghost_cascade<D>(g, cls, l - 1, pc);
     }
-  }
-  }
+  }  // the barrier at the top of the next chunk ends this chunk's use of the queue
 }
 
 // ---------------------------------------------------------------- compaction
@@ -455,6 +540,13 @@ __global__ void __launch_bounds__(256) k_count(const InstDev* __restrict__ IB, c
   for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < nchunks; t += nw) {
     int chunk;
     const int b = mr_group_chunk_of(chunk_pre, n, t, chunk);
+    if (!IB[b].act[chunk]) {  // nothing classified or marked in it
+      if (lane == 0) {
+        int* bc = IB[b].bcounts + 3 * chunk;
+        bc[0] = bc[1] = bc[2] = 0;
+      }
+      continue;
+    }
     const uint4* src = (const uint4*)(IB[b].cls + (size_t)chunk * MR_DENSE_ALIGN) + 2 * lane;
     const uint4 v0 = src[0], v1 = src[1];
     int nl = 0, ni = 0, ng = 0;
@@ -586,6 +678,17 @@ __global__ void __launch_bounds__(256) k_scatter(const InstDev* __restrict__ IB,
     const Geo& g = I.g;
     const MeshDev& B = I.mesh[dst];
     const uint32_t c0 = (uint32_t)chunk * MR_DENSE_ALIGN;
+    const bool touched = I.act[chunk], held = B.mact[chunk];
+    if (!touched) {
+      if (held) {  // entries of the mesh last written here: clear them
+        const int4 none = make_int4(MR_MAP_NONE, MR_MAP_NONE, MR_MAP_NONE, MR_MAP_NONE);
+        int4* mp = (int4*)(B.map + c0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) mp[32 * k + lane] = none;
+        if (lane == 0) B.mact[chunk] = 0;
+      }
+      continue;
+    }
     const uint8_t* cl = I.cls + c0;
     uint8_t v[32];
 #pragma unroll
@@ -621,6 +724,11 @@ __global__ void __launch_bounds__(256) k_scatter(const InstDev* __restrict__ IB,
     clp[1] = zero;
     flp[0] = zero;
     flp[1] = zero;
+    if (lane == 0) {
+      B.mact[chunk] = 1;
+      I.act[chunk] = 0;
+      I.acth[chunk] = 0;
+    }
   }
 }
 
@@ -628,7 +736,7 @@ __global__ void __launch_bounds__(256) k_scatter(const InstDev* __restrict__ IB,
 template <int D>
 __global__ void __launch_bounds__(256) k_leaves_in(Geo g, long long n, const unsigned long long* keys,
                                                    const signed char* levels, int32_t* inidx,
-                                                   uint8_t* cls, MeshCounts* cnt,
+                                                   uint8_t* cls, uint8_t* act, MeshCounts* cnt,
                                                    unsigned long long* vol) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -640,6 +748,7 @@ __global__ void __launch_bounds__(256) k_leaves_in(Geo g, long long n, const uns
     }
     const uint32_t c = (uint32_t)key;
     const uint32_t old = mr_atomic_or_byte(cls, g.base[l] + c, MR_C_LEAF);
+    mr_touch(act, g.base[l] + c);
     if (old & MR_C_LEAF) mr_set_err(cnt, MR_DERR_INPUT);
     inidx[g.base[l] + c] = (int32_t)i;
     atomicAdd(vol, 1ull << (D * (g.J - l)));
@@ -648,6 +757,7 @@ __global__ void __launch_bounds__(256) k_leaves_in(Geo g, long long n, const uns
       a >>= D;
       const uint32_t o = mr_atomic_or_byte(cls, g.base[la] + a, MR_C_INT);
       if (o & MR_C_INT) break;
+      mr_touch(act, g.base[la] + a);
     }
   }
 }
@@ -696,31 +806,37 @@ void mr_launch_grade(const Group& G, cudaStream_t st) {
     MR_DISPATCH_D_PDL(k_grade, mr_tile_grid(G, (long long)G.chunks * MR_DENSE_ALIGN, 256, G.bps[MR_PH_FLAGS]), 256, mr_pre_bytes(G), st,
                   G.dev, G.n);
 }
-// dense kernels: one block per 1024-cell chunk of every instance
+// dense kernels: grid-stride over the 1024-cell chunks of every instance,
+// visiting the touched ones
+int mr_chunk_warps_grid(const Group& G) {  // one warp per chunk, 8 warps per block
+  return std::max(1, std::min((G.chunks + 7) / 8, G.bps[MR_PH_COMPACT] * G.nsm));
+}
 void mr_launch_classify(const Group& G, cudaStream_t st) {
   const int D_ = G.d;
-  MR_DISPATCH_D_PDL(k_classify, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+  MR_DISPATCH_D_PDL(k_classify, mr_chunk_warps_grid(G), 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
 }
-void mr_launch_full_mesh(const Geo& g, uint8_t* cls, cudaStream_t st, int) {
-  k_full_mesh<<<(int)(g.base[g.J + 1] / MR_DENSE_ALIGN), 256, 0, st>>>(g, cls);
+void mr_launch_full_mesh(const Geo& g, uint8_t* cls, uint8_t* act, cudaStream_t st, int) {
+  k_full_mesh<<<(int)(g.base[g.J + 1] / MR_DENSE_ALIGN), 256, 0, st>>>(g, cls, act);
+}
+int mr_chunk_blocks_grid(const Group& G) {  // one block per chunk at a time
+  return std::max(1, std::min(G.chunks, G.bps[MR_PH_COMPACT] * G.nsm));
 }
 void mr_launch_mark_ghosts(const Group& G, cudaStream_t st) {
   if (G.s > 1) return mr_launch_mark_ghosts_w(G, st);
   const int D_ = G.d;
-  MR_DISPATCH_D_PDL(k_mark_ghosts, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+  MR_DISPATCH_D_PDL(k_mark_ghosts, mr_chunk_blocks_grid(G), 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
 }
 void mr_launch_compact(const Group& G, int dst, cudaStream_t st) {
-  // one warp per chunk, 8 warps per block, at most 8 blocks per SM
-  const int grid = std::min((G.chunks + 7) / 8, G.bps[MR_PH_COMPACT] * G.nsm);
+  const int grid = mr_chunk_warps_grid(G);
   mr_launch_pdl(k_count, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
   mr_launch_pdl(k_scan_blocks, G.n, 1024, 0, st, G.dev, dst);
   mr_launch_pdl(k_scatter, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, dst, G.chunks);
 }
 void mr_launch_leaves_in(const Geo& g, long long n, const unsigned long long* keys,
-                         const signed char* levels, int32_t* inidx, uint8_t* cls, MeshCounts* cnt,
+                         const signed char* levels, int32_t* inidx, uint8_t* cls, uint8_t* act, MeshCounts* cnt,
                          unsigned long long* vol, cudaStream_t st, int grid) {
   const int D_ = g.d;
-  MR_DISPATCH_D(k_leaves_in, grid, 256, 0, st, g, n, keys, levels, inidx, cls, cnt, vol);
+  MR_DISPATCH_D(k_leaves_in, grid, 256, 0, st, g, n, keys, levels, inidx, cls, act, cnt, vol);
 }
 void mr_launch_leaves_check(const Geo& g, uint8_t* cls, MeshCounts* cnt, cudaStream_t st, int grid) {
   k_leaves_check<<<grid, 256, 0, st>>>(g, cls, cnt);

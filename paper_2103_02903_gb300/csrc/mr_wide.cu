@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(256) k_grade_w(const InstDev* __restrict__ IB,
     mr_inst_use(si, have, IB, b);
     const Geo& g = si.g;
     uint8_t* flags = si.flags;
-    const uint32_t gi = g.base[g.Jmin + 1] + (uint32_t)(t - pre[b]) * 256u + threadIdx.x;
+    const uint32_t t0 = g.base[g.Jmin + 1] + (uint32_t)(t - pre[b]) * 256u, gi = t0 + threadIdx.x;
+    if (!si.acth[t0 / MR_DENSE_ALIGN]) continue;  // no H flag in this tile's chunk
     if (gi >= g.base[g.J]) continue;
     if (!(flags[gi] & MR_F_H)) continue;
     const int l0 = mr_level_of(g, gi);
@@ -179,9 +180,13 @@ __global__ void __launch_bounds__(256) k_grade_w(const InstDev* __restrict__ IB,
       if (!mr_nbr_mesh_d<D>(g, L, nb)) continue;
       for (int a = 0; a < D; ++a) nb[a] >>= 1;
       const int tl = L - 1;
-      const uint32_t pi = g.base[tl] + mr_encode_d<D>(g, tl, nb);
+      const uint32_t pc = mr_encode_d<D>(g, tl, nb), pi = g.base[tl] + pc;
       if (flags[pi] & (MR_F_H | MR_F_G)) continue;  // plain load first
       const uint32_t old = mr_atomic_or_byte(flags, pi, MR_F_G);
+      if (!(old & (MR_F_H | MR_F_G))) {  // the cell and its children's chunk hold cells of the new tree
+        mr_touch(si.act, pi);
+        mr_touch(si.act, g.base[tl + 1] + (pc << D));
+      }
       if (!(old & (MR_F_H | MR_F_G)) && tl > g.Jmin && sp < MR_MAXL) {
         sl[sp] = tl;
         sk[sp] = 0;
@@ -200,86 +205,94 @@ __global__ void __launch_bounds__(256) k_grade_w(const InstDev* __restrict__ IB,
 // marked the same way (cells outside the tree become ghosts), towards J_min.
 template <int D, int S>
 __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict__ IB,
-                                                       const int* __restrict__ chunk_pre, int n) {
+                                                       const int* __restrict__ chunk_pre, int n, int nchunks) {
   using B = WBox<D, S>;
   constexpr int W = 2 * S;
   __shared__ InstDev si;
   __shared__ uint16_t queue[MR_DENSE_ALIGN];  // the chunk's leaves (offsets in the chunk)
   __shared__ int qn;
-  int chunk, have = -1;
-  mr_inst_use(si, have, IB, mr_group_chunk(chunk_pre, n, chunk));
+  int have = -1;
   mr_grid_dep();
-  const Geo& g = si.g;
-  uint8_t* cls = si.cls;
-  const uint32_t c0 = (uint32_t)chunk * MR_DENSE_ALIGN;
-  const int l = mr_level_of(g, c0);
-  const uint32_t cb = c0 - g.base[l];
-  if (threadIdx.x == 0) qn = 0;
-  __syncthreads();
-  // the leaves are a few per cent of the cells: gather them, then spread the
-  // (leaf, window cell) pairs over the whole block (the marks are a union of
-  // atomic ORs, so the order does not matter)
-  {
-    const int lane = threadIdx.x & 31;
-    for (int k = 0; k < (int)(MR_DENSE_ALIGN / 256u); ++k) {
-      const uint32_t off = (uint32_t)k * 256u + threadIdx.x;
-      const bool leaf = cb + off < g.ncode[l] && (cls[c0 + off] & 3u) == MR_C_LEAF;
-      const uint32_t bal = __ballot_sync(0xffffffffu, leaf);
-      int at = 0;
-      if (lane == 0 && bal) at = atomicAdd(&qn, __popc(bal));
-      at = __shfl_sync(0xffffffffu, at, 0);
-      if (leaf) queue[at + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)off;
-    }
-  }
-  __syncthreads();
-  const bool block = D == 2 && g.diag;
-  const int nw = block ? (2 * W + 1) * (2 * W + 1) : D * 2 * W;
-  const int items = qn * nw;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int w = it % nw;
-    if (block && w == (2 * W + 1) * W + W) continue;  // the leaf itself
-    const uint32_t c = cb + queue[it / nw];
-    int nb[3] = {0, 0, 0};
-    mr_decode_d<D>(g, l, c, nb);
-    if (block) {
-      nb[0] += w % (2 * W + 1) - W;
-      nb[1] += w / (2 * W + 1) - W;
-    } else {
-      const int axis = w / (2 * W), o = w % (2 * W);
-      nb[axis] += o < W ? o - W : o - W + 1;  // -W..-1, 1..W
-    }
-    if (!mr_nbr_mesh_d<D>(g, l, nb)) continue;
-    const uint32_t gw = g.base[l] + mr_encode_d<D>(g, l, nb);
-    if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
-    const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
-    if ((old & (3u | MR_C_GHOST)) || l - 1 < g.Jmin) continue;
-    // cascade over the stencils of the ghosts' parents
-    int sl[MR_MAXL], sc[MR_MAXL][3], sk[MR_MAXL];
-    int sp = 1;
-    sl[0] = l - 1;
-    sk[0] = 0;
-    for (int a = 0; a < 3; ++a) sc[0][a] = a < D ? nb[a] >> 1 : 0;
-    while (sp > 0) {
-      const int f = sp - 1;
-      if (sk[f] == B::N) {
-        --sp;
-        continue;
+  // a block per touched chunk at a time (a chunk nothing touched holds no leaf)
+  for (int t = blockIdx.x; t < nchunks; t += gridDim.x) {
+    int chunk;
+    const int ib = mr_group_chunk_of(chunk_pre, n, t, chunk);
+    if (!__syncthreads_or(threadIdx.x == 0 && IB[ib].act[chunk])) continue;  // one read for the block
+    mr_inst_use(si, have, IB, ib);
+    const Geo& g = si.g;
+    uint8_t* cls = si.cls;
+    const uint32_t c0 = (uint32_t)chunk * MR_DENSE_ALIGN;
+    const int l = mr_level_of(g, c0);
+    const uint32_t cb = c0 - g.base[l];
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+    // the leaves are a few per cent of the cells: gather them, then spread the
+    // (leaf, window cell) pairs over the whole block (the marks are a union of
+    // atomic ORs, so the order does not matter)
+    {
+      const int lane = threadIdx.x & 31;
+      for (int k = 0; k < (int)(MR_DENSE_ALIGN / 256u); ++k) {
+        const uint32_t off = (uint32_t)k * 256u + threadIdx.x;
+        const bool leaf = cb + off < g.ncode[l] && (cls[c0 + off] & 3u) == MR_C_LEAF;
+        const uint32_t bal = __ballot_sync(0xffffffffu, leaf);
+        int at = 0;
+        if (lane == 0 && bal) at = atomicAdd(&qn, __popc(bal));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (leaf) queue[at + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)off;
       }
-      const int kk = sk[f]++;
-      const int L = sl[f];
-      int ac[3] = {sc[f][0] + kk % B::W1 - S, D >= 2 ? sc[f][1] + (kk / B::W1) % B::W1 - S : 0,
-                   D == 3 ? sc[f][2] + kk / (B::W1 * B::W1) - S : 0};
-      if (!mr_nbr_mesh_d<D>(g, L, ac)) continue;  // outside: the stencil clamps to a cell of the box
-      const uint32_t ga = g.base[L] + mr_encode_d<D>(g, L, ac);
-      if (cls[ga] & (3u | MR_C_GHOST)) continue;
-      const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
-      if ((o2 & (3u | MR_C_GHOST)) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
-      sl[sp] = L - 1;
-      sk[sp] = 0;
-      for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? ac[a] >> 1 : 0;
-      ++sp;
     }
-  }
+    __syncthreads();
+    const bool block = D == 2 && g.diag;
+    const int nw = block ? (2 * W + 1) * (2 * W + 1) : D * 2 * W;
+    const int items = qn * nw;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int w = it % nw;
+      if (block && w == (2 * W + 1) * W + W) continue;  // the leaf itself
+      const uint32_t c = cb + queue[it / nw];
+      int nb[3] = {0, 0, 0};
+      mr_decode_d<D>(g, l, c, nb);
+      if (block) {
+        nb[0] += w % (2 * W + 1) - W;
+        nb[1] += w / (2 * W + 1) - W;
+      } else {
+        const int axis = w / (2 * W), o = w % (2 * W);
+        nb[axis] += o < W ? o - W : o - W + 1;  // -W..-1, 1..W
+      }
+      if (!mr_nbr_mesh_d<D>(g, l, nb)) continue;
+      const uint32_t gw = g.base[l] + mr_encode_d<D>(g, l, nb);
+      if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
+      const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
+      if (!old) mr_touch(si.act, gw);
+      if ((old & (3u | MR_C_GHOST)) || l - 1 < g.Jmin) continue;
+      // cascade over the stencils of the ghosts' parents
+      int sl[MR_MAXL], sc[MR_MAXL][3], sk[MR_MAXL];
+      int sp = 1;
+      sl[0] = l - 1;
+      sk[0] = 0;
+      for (int a = 0; a < 3; ++a) sc[0][a] = a < D ? nb[a] >> 1 : 0;
+      while (sp > 0) {
+        const int f = sp - 1;
+        if (sk[f] == B::N) {
+          --sp;
+          continue;
+        }
+        const int kk = sk[f]++;
+        const int L = sl[f];
+        int ac[3] = {sc[f][0] + kk % B::W1 - S, D >= 2 ? sc[f][1] + (kk / B::W1) % B::W1 - S : 0,
+                     D == 3 ? sc[f][2] + kk / (B::W1 * B::W1) - S : 0};
+        if (!mr_nbr_mesh_d<D>(g, L, ac)) continue;  // outside: the stencil clamps to a cell of the box
+        const uint32_t ga = g.base[L] + mr_encode_d<D>(g, L, ac);
+        if (cls[ga] & (3u | MR_C_GHOST)) continue;
+        const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
+        if (!o2) mr_touch(si.act, ga);
+        if ((o2 & (3u | MR_C_GHOST)) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
+        sl[sp] = L - 1;
+        sk[sp] = 0;
+        for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? ac[a] >> 1 : 0;
+        ++sp;
+      }
+    }
+  }  // the barrier at the top of the next chunk ends this chunk's use of the queue
 }
 
 // ------------------------------------------------------------------ prediction of ghosts and new leaves
@@ -828,15 +841,16 @@ void mr_launch_grade_w(const Group& G, cudaStream_t st) {
 }
 
 void mr_launch_mark_ghosts_w(const Group& G, cudaStream_t st) {
+  const int grid = mr_chunk_blocks_grid(G);
   if (G.d == 1) {
-    if (G.s == 2) mr_launch_pdl(k_mark_ghosts_w<1, 2>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
-    else mr_launch_pdl(k_mark_ghosts_w<1, 3>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+    if (G.s == 2) mr_launch_pdl(k_mark_ghosts_w<1, 2>, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
+    else mr_launch_pdl(k_mark_ghosts_w<1, 3>, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
   } else if (G.d == 2) {
-    if (G.s == 2) mr_launch_pdl(k_mark_ghosts_w<2, 2>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
-    else mr_launch_pdl(k_mark_ghosts_w<2, 3>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+    if (G.s == 2) mr_launch_pdl(k_mark_ghosts_w<2, 2>, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
+    else mr_launch_pdl(k_mark_ghosts_w<2, 3>, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
   } else {
-    if (G.s == 2) mr_launch_pdl(k_mark_ghosts_w<3, 2>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
-    else mr_launch_pdl(k_mark_ghosts_w<3, 3>, G.chunks, 256, 0, st, G.dev, G.chunk_pre, G.n);
+    if (G.s == 2) mr_launch_pdl(k_mark_ghosts_w<3, 2>, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
+    else mr_launch_pdl(k_mark_ghosts_w<3, 3>, grid, 256, 0, st, G.dev, G.chunk_pre, G.n, G.chunks);
   }
 }
 
