@@ -147,6 +147,16 @@ __device__ __forceinline__ void mr_set_err(MeshCounts* c, int bits) { atomicOr(&
 // passes of this step visit its 1024-cell chunk (every writer stores 1).
 __device__ __forceinline__ void mr_touch(uint8_t* act, uint32_t gi) { act[gi / MR_DENSE_ALIGN] = 1; }
 
+// Ghost marking: the stencil around the cell of dense index gi (the parent of
+// a new ghost) is walked by the one thread that claims it first, so that
+// sibling ghosts and overlapping cascades walk each stencil once.
+__device__ __forceinline__ bool mr_claim_stencil(uint8_t* cls, uint8_t* act, uint32_t gi) {
+  if (cls[gi] & MR_C_STEN) return false;  // a plain load first
+  if (mr_atomic_or_byte(cls, gi, MR_C_STEN) & MR_C_STEN) return false;
+  mr_touch(act, gi);
+  return true;
+}
+
 // level of a dense index (levels J_min..J)
 __device__ __forceinline__ int mr_level_of(const Geo& g, uint32_t gi) {
   int l = g.Jmin;

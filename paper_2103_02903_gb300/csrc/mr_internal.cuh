@@ -25,6 +25,7 @@
 #define MR_C_INT 2u
 #define MR_C_GHOST 4u
 #define MR_C_INPUT 8u
+#define MR_C_STEN 16u  // ghost marking: the prediction stencil around this cell is claimed
 
 // device error bits
 #define MR_DERR_CAPACITY 1

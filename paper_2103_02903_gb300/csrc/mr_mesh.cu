@@ -356,9 +356,10 @@ __device__ __forceinline__ uint32_t ghost_need3(const Geo& g, const uint8_t* cls
 // A cell of level L + 1 became a ghost: mark its parent's 3^D stencil
 // (cell c of level L), cells outside the tree becoming ghosts, and so on
 // towards J_min, depth first; only the thread that marks a cell first walks
-// on from it.
+// on from it, and only the thread that claims a stencil first walks it.
 template <int D>
 __device__ void ghost_cascade(const Geo& g, uint8_t* cls, uint8_t* act, int L0, const int* c0) {
+  if (!mr_claim_stencil(cls, act, g.base[L0] + mr_encode_d<D>(g, L0, c0))) return;
   int sl[MR_MAXL], sc[MR_MAXL][3];
   uint32_t sm[MR_MAXL];
   sl[0] = L0;
@@ -381,10 +382,12 @@ __device__ void ghost_cascade(const Geo& g, uint8_t* cls, uint8_t* act, int L0, 
     mr_nbr_mesh_d<D>(g, L, ac);  // inside: only such cells enter the mask
     const uint32_t ga = g.base[L] + mr_encode_d<D>(g, L, ac);
     const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
-    if (!o2) mr_touch(act, ga);
-    if ((o2 & MR_C_GHOST) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
-    sl[sp] = L - 1;
+    if (o2 & MR_C_GHOST) continue;
+    mr_touch(act, ga);
+    if (L - 1 < g.Jmin || sp >= MR_MAXL) continue;
     for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? ac[a] >> 1 : 0;
+    if (!mr_claim_stencil(cls, act, g.base[L - 1] + mr_encode_d<D>(g, L - 1, sc[sp]))) continue;
+    sl[sp] = L - 1;
     if constexpr (D == 3)
       sm[sp] = ghost_need3(g, cls, L - 1, sc[sp]);
     else
@@ -448,8 +451,9 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
         const uint32_t gw = g.base[l] + mr_encode_d<3>(g, l, nb);
         if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
         const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
-        if (!old) mr_touch(si.act, gw);
-        if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
+        if (old & MR_C_GHOST) continue;
+        mr_touch(si.act, gw);
+        if (l - 1 < g.Jmin) continue;
         const int pc[3] = {nb[0] >> 1, nb[1] >> 1, nb[2] >> 1};
         ghost_cascade<3>(g, cls, si.act, l - 1, pc);
       }
@@ -495,8 +499,9 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
         mr_nbr_mesh(g, l, nx, ny);  // inside: only such cells enter the mask
         const uint32_t gw = g.base[l] + mr_encode(g, l, nx, ny);
         const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
-        if (!old) mr_touch(si.act, gw);
-        if ((old & MR_C_GHOST) || l - 1 < g.Jmin) continue;
+        if (old & MR_C_GHOST) continue;
+        mr_touch(si.act, gw);
+        if (l - 1 < g.Jmin) continue;
         // cascade: the stencil of the ghost's parent, towards coarser levels
         const int pc[3] = {nx >> 1, ny >> 1, 0};
         ghost_cascade<D>(g, cls, si.act, l - 1, pc);

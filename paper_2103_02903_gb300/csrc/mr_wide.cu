@@ -262,14 +262,17 @@ __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict
       const uint32_t gw = g.base[l] + mr_encode_d<D>(g, l, nb);
       if (cls[gw] & (3u | MR_C_GHOST)) continue;  // in the tree or marked
       const uint32_t old = mr_atomic_or_byte(cls, gw, MR_C_GHOST);
-      if (!old) mr_touch(si.act, gw);
-      if ((old & (3u | MR_C_GHOST)) || l - 1 < g.Jmin) continue;
-      // cascade over the stencils of the ghosts' parents
+      if (old & (3u | MR_C_GHOST)) continue;
+      mr_touch(si.act, gw);
+      if (l - 1 < g.Jmin) continue;
+      // cascade over the stencils of the ghosts' parents, each stencil
+      // walked by the thread that claims it first
       int sl[MR_MAXL], sc[MR_MAXL][3], sk[MR_MAXL];
       int sp = 1;
       sl[0] = l - 1;
       sk[0] = 0;
       for (int a = 0; a < 3; ++a) sc[0][a] = a < D ? nb[a] >> 1 : 0;
+      if (!mr_claim_stencil(cls, si.act, g.base[l - 1] + mr_encode_d<D>(g, l - 1, sc[0]))) continue;
       while (sp > 0) {
         const int f = sp - 1;
         if (sk[f] == B::N) {
@@ -284,11 +287,13 @@ __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict
         const uint32_t ga = g.base[L] + mr_encode_d<D>(g, L, ac);
         if (cls[ga] & (3u | MR_C_GHOST)) continue;
         const uint32_t o2 = mr_atomic_or_byte(cls, ga, MR_C_GHOST);
-        if (!o2) mr_touch(si.act, ga);
-        if ((o2 & (3u | MR_C_GHOST)) || L - 1 < g.Jmin || sp >= MR_MAXL) continue;
+        if (o2 & (3u | MR_C_GHOST)) continue;
+        mr_touch(si.act, ga);
+        if (L - 1 < g.Jmin || sp >= MR_MAXL) continue;
+        for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? ac[a] >> 1 : 0;
+        if (!mr_claim_stencil(cls, si.act, g.base[L - 1] + mr_encode_d<D>(g, L - 1, sc[sp]))) continue;
         sl[sp] = L - 1;
         sk[sp] = 0;
-        for (int a = 0; a < 3; ++a) sc[sp][a] = a < D ? ac[a] >> 1 : 0;
         ++sp;
       }
     }
