@@ -595,14 +595,35 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict_
   __syncthreads();
   for (int b0 = 0; b0 < nblocks; b0 += 1024 * MR_SCAN_VPT) {
     const int first = b0 + threadIdx.x * MR_SCAN_VPT;
+    // the thread's 3 MR_SCAN_VPT counts are consecutive (96 bytes, 16-byte
+    // aligned): six 16-byte loads where the chunks are all there
+    const bool whole = first + MR_SCAN_VPT <= nblocks;
     int v[MR_SCAN_VPT][3], x[3], tot[3] = {0, 0, 0};
+    if (whole) {
+      const int4* src = (const int4*)(bc + first * 3);
+      int w[3 * MR_SCAN_VPT];
+#pragma unroll
+      for (int k = 0; k < 3 * MR_SCAN_VPT / 4; ++k) {
+        const int4 q = src[k];
+        w[4 * k] = q.x;
+        w[4 * k + 1] = q.y;
+        w[4 * k + 2] = q.z;
+        w[4 * k + 3] = q.w;
+      }
+#pragma unroll
+      for (int j = 0; j < MR_SCAN_VPT; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[j][c] = w[3 * j + c];
+    } else {
+#pragma unroll
+      for (int j = 0; j < MR_SCAN_VPT; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[j][c] = first + j < nblocks ? bc[(first + j) * 3 + c] : 0;
+    }
 #pragma unroll
     for (int j = 0; j < MR_SCAN_VPT; ++j)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        v[j][c] = first + j < nblocks ? bc[(first + j) * 3 + c] : 0;
-        tot[c] += v[j][c];
-      }
+      for (int c = 0; c < 3; ++c) tot[c] += v[j][c];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       x[c] = tot[c];
@@ -630,13 +651,25 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const InstDev* __restrict_
     int run[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) run[c] = carry[c] + (wid > 0 ? warp_sums[wid - 1][c] : 0) + x[c] - tot[c];
+    int w[3 * MR_SCAN_VPT];
 #pragma unroll
     for (int j = 0; j < MR_SCAN_VPT; ++j)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        if (first + j < nblocks) bc[(first + j) * 3 + c] = run[c];
+        w[3 * j + c] = run[c];
         run[c] += v[j][c];
       }
+    if (whole) {
+      int4* dst4 = (int4*)(bc + first * 3);
+#pragma unroll
+      for (int k = 0; k < 3 * MR_SCAN_VPT / 4; ++k) dst4[k] = make_int4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < MR_SCAN_VPT; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (first + j < nblocks) bc[(first + j) * 3 + c] = w[3 * j + c];
+    }
     __syncthreads();  // every thread has read carry
     if (threadIdx.x == 1023)
 #pragma unroll
