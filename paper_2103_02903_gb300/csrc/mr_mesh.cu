@@ -856,8 +856,8 @@ void mr_launch_classify(const Group& G, cudaStream_t st) {
 void mr_launch_full_mesh(const Geo& g, uint8_t* cls, uint8_t* act, cudaStream_t st, int) {
   k_full_mesh<<<(int)(g.base[g.J + 1] / MR_DENSE_ALIGN), 256, 0, st>>>(g, cls, act);
 }
-int mr_chunk_blocks_grid(const Group& G) {  // one block per chunk at a time
-  return std::max(1, std::min(G.chunks, G.bps[MR_PH_COMPACT] * G.nsm));
+int mr_chunk_blocks_grid(const Group& G) {  // one block per chunk: an untouched one ends at once
+  return std::max(1, G.chunks);
 }
 void mr_launch_mark_ghosts(const Group& G, cudaStream_t st) {
   if (G.s > 1) return mr_launch_mark_ghosts_w(G, st);
