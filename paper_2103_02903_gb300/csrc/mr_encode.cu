@@ -134,8 +134,10 @@ __device__ __forceinline__ bool half_details(const ValPtr<__half>* sv, const Val
   return true;
 }
 
+// 2D and 1D: at most 80 registers, 3 blocks per SM (the stencil-sharing
+// barriers of one block are covered by the others); 3D would spill
 template <int D, int Q, int F>
-__global__ void __launch_bounds__(256) k_details(const InstDev* __restrict__ IB, int n, int cur) {
+__global__ void __launch_bounds__(256, D == 3 ? 1 : 3) k_details(const InstDev* __restrict__ IB, int n, int cur) {
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];
