@@ -135,9 +135,10 @@ __device__ __forceinline__ bool half_details(const ValPtr<__half>* sv, const Val
 }
 
 // 2D and 1D: at most 80 registers, 3 blocks per SM (the stencil-sharing
-// barriers of one block are covered by the others); 3D would spill
+// barriers of one block are covered by the others); 3D: 2 blocks, 128
+// registers (with a minimum of one block the compiler takes 150)
 template <int D, int Q, int F>
-__global__ void __launch_bounds__(256, D == 3 ? 1 : 3) k_details(const InstDev* __restrict__ IB, int n, int cur) {
+__global__ void __launch_bounds__(256, D == 3 ? 2 : 3) k_details(const InstDev* __restrict__ IB, int n, int cur) {
   using S = typename FormT<F>::S;
   constexpr int PY = PopRows<Q>::value;
   extern __shared__ int pre[];

@@ -74,9 +74,10 @@ __global__ void __launch_bounds__(256) k_remesh_copy(const InstDev* __restrict__
 
 // Ghosts and newly created leaves of one level: the prediction operator
 // applied to level-1 values of the new mesh (all present by construction).
-// 2D and 1D: at most 64 registers, 4 blocks per SM; 3D would spill
+// 2D and 1D: at most 64 registers, 4 blocks per SM; 3D: 2 blocks, 128
+// registers
 template <int D, int Q, int F>
-__global__ void __launch_bounds__(256, D == 3 ? 1 : 4) k_predict_level(const InstDev* __restrict__ IB, int ngrp, int dst,
+__global__ void __launch_bounds__(256, D == 3 ? 2 : 4) k_predict_level(const InstDev* __restrict__ IB, int ngrp, int dst,
                                                                        int kl) {
   using S = typename FormT<F>::S;
   using C = typename FormT<F>::C;
