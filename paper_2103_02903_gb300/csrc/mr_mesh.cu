@@ -403,6 +403,7 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
                                                      const int* __restrict__ chunk_pre, int n, int nchunks) {
   __shared__ InstDev si;
   __shared__ uint16_t queue[MR_DENSE_ALIGN];  // the chunk's leaves (offsets in the chunk)
+  __shared__ int32_t qc[D == 3 ? 3 : 1][D == 3 ? MR_DENSE_ALIGN : 1];  // 3D: their coordinates, decoded once
   __shared__ int qn;
   int have = -1;
   mr_grid_dep();
@@ -434,7 +435,17 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
         int at = 0;
         if (lane == 0 && bal) at = atomicAdd(&qn, __popc(bal));
         at = __shfl_sync(0xffffffffu, at, 0);
-        if (leaf) queue[at + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)off;
+        if (leaf) {
+          const int q = at + __popc(bal & ((1u << lane) - 1u));
+          queue[q] = (uint16_t)off;
+          if constexpr (D == 3) {
+            int c[3];
+            mr_decode_d<3>(g, l, cb + off, c);
+            qc[0][q] = c[0];
+            qc[1][q] = c[1];
+            qc[2][q] = c[2];
+          }
+        }
       }
     }
     __syncthreads();
@@ -444,8 +455,8 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
       // cells of a leaf are independent, and most are in the tree already
       for (int it = threadIdx.x; it < nq * 12; it += blockDim.x) {
         const int w = it % 12, k = w & 3;
-        int nb[3];
-        mr_decode_d<3>(g, l, cb + queue[it / 12], nb);
+        const int q = it / 12;
+        int nb[3] = {qc[0][q], qc[1][q], qc[2][q]};
         nb[w >> 2] += k < 2 ? k - 2 : k - 1;  // -2, -1, +1, +2 along axis w / 4
         if (!mr_nbr_mesh_d<3>(g, l, nb)) continue;
         const uint32_t gw = g.base[l] + mr_encode_d<3>(g, l, nb);

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict
   using B = WBox<D, S>;
   constexpr int W = 2 * S;
   __shared__ InstDev si;
-  __shared__ uint16_t queue[MR_DENSE_ALIGN];  // the chunk's leaves (offsets in the chunk)
+  __shared__ int32_t qc[D][MR_DENSE_ALIGN];  // the chunk's leaves: their coordinates, decoded once
   __shared__ int qn;
   int have = -1;
   mr_grid_dep();
@@ -238,7 +238,12 @@ __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict
         int at = 0;
         if (lane == 0 && bal) at = atomicAdd(&qn, __popc(bal));
         at = __shfl_sync(0xffffffffu, at, 0);
-        if (leaf) queue[at + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)off;
+        if (leaf) {
+          const int q = at + __popc(bal & ((1u << lane) - 1u));
+          int c[3] = {0, 0, 0};
+          mr_decode_d<D>(g, l, cb + off, c);
+          for (int a = 0; a < D; ++a) qc[a][q] = c[a];
+        }
       }
     }
     __syncthreads();
@@ -248,9 +253,9 @@ __global__ void __launch_bounds__(256) k_mark_ghosts_w(const InstDev* __restrict
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       const int w = it % nw;
       if (block && w == (2 * W + 1) * W + W) continue;  // the leaf itself
-      const uint32_t c = cb + queue[it / nw];
+      const int q = it / nw;
       int nb[3] = {0, 0, 0};
-      mr_decode_d<D>(g, l, c, nb);
+      for (int a = 0; a < D; ++a) nb[a] = qc[a][q];
       if (block) {
         nb[0] += w % (2 * W + 1) - W;
         nb[1] += w / (2 * W + 1) - W;
