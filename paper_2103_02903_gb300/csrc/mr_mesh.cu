@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
     // its parent stencil), so the result does not depend on the order.
     {
       const int lane = threadIdx.x & 31;
-  #pragma unroll
+#pragma unroll
       for (int k = 0; k < (int)(MR_DENSE_ALIGN / 256u); ++k) {
         const uint32_t off = (uint32_t)k * 256u + threadIdx.x;
         const bool leaf = cb + off < g.ncode[l] && (cls[c0 + off] & 3u) == MR_C_LEAF;
@@ -479,13 +479,13 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
         MortonBox<2> bx;
         bx.init(g, l, x, y);
         if (block) {
-  #pragma unroll
+#pragma unroll
           for (int w = 0; w < 25; ++w) {
             if (w == 12) continue;  // the leaf itself
             if (bx.in(w % 5, w / 5) && !(cl[bx.code(w % 5, w / 5)] & (3u | MR_C_GHOST))) need |= 1u << w;
           }
         } else {
-  #pragma unroll
+#pragma unroll
           for (int w = 0; w < 8; ++w) {
             const int axis = w >> 2, k = w & 3;
             const int off = k < 2 ? k - 2 : k - 1;
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(256) k_mark_ghosts(const InstDev* __restrict__
           }
         }
       } else {
-  #pragma unroll
+#pragma unroll
         for (int w = 0; w < 4; ++w) {
           int nx, ny;
           ghost_window_cell(false, w, x, y, nx, ny);
